@@ -1,0 +1,211 @@
+/*
+ * sdpgb.h -- C ABI of libsdpgb, a GB300 (sm_103a) implementation of the
+ * preconditioned-CG Hessian solve inside the modified interior-point method of
+ * Zhang & Lavaei, "Modified Interior-Point Method for Large-and-Sparse Low-Rank
+ * Semidefinite Programs" (arXiv 1703.10973).
+ *
+ * Problem (eq. SDP / SDD):  min C.X  s.t.  A_i.X = b_i (i < m), X psd;
+ *                           max b^T y s.t.  sum_i y_i A_i + S = C, S psd.
+ *
+ * Conventions shared by every call
+ *  - Symmetric matrices are passed as triplets (i, j, v) with i <= j meaning
+ *    M[i][j] = M[j][i] = v; repeated positions add.  Indices are 0-based int32.
+ *  - Dense n x n matrices are row-major double (equal to column-major for the
+ *    symmetric ones).
+ *  - Host arrays are copied during the call; the caller keeps ownership.
+ *  - "_dev" pointers are device pointers owned by the caller; they must be
+ *    valid on the handle's stream and must not alias each other.
+ *  - The handle owns all other device memory and frees it in sdp_destroy.
+ *  - Every call returns an sdp_status; nothing is thrown across the ABI.  After
+ *    any status the handle may still be destroyed; sdp_last_error() gives text.
+ *  - One handle is used by one host thread at a time.  All work is issued on the
+ *    stream given to sdp_setup (NULL = the legacy default stream).
+ *  - Precision argument `prec`: SDP_FP64 computes in double.  SDP_FP32 and
+ *    SDP_BF16 store the operator data (W, Z, U, the core inverse) in float or
+ *    bfloat16 and accumulate in float; vectors crossing the ABI stay double.
+ */
+#ifndef SDPGB_H
+#define SDPGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdp_problem sdp_problem;
+
+typedef enum {
+  SDP_OK = 0,
+  SDP_ERR_ARG = 1,          /* invalid argument (sizes, null pointers, indices)   */
+  SDP_ERR_OOM = 2,          /* device or host allocation failed                  */
+  SDP_ERR_NOT_PD = 3,       /* Cholesky met a non-positive pivot                  */
+  SDP_ERR_MAXIT = 4,        /* iteration cap reached; best iterate is kept        */
+  SDP_ERR_UNSUPPORTED = 5,  /* A^T A is not diagonal (Assumption 2 not met here)  */
+  SDP_ERR_NUMERIC = 6,      /* NaN or Inf detected                                 */
+  SDP_ERR_TIMEOUT = 7,      /* a bounded device-side wait expired                 */
+  SDP_ERR_CUDA = 8          /* a CUDA runtime call failed                          */
+} sdp_status;
+
+typedef enum { SDP_FP64 = 0, SDP_FP32 = 1, SDP_BF16 = 2 } sdp_prec;
+
+typedef enum {
+  SDP_PRECOND_DIAG = 0,     /* tau^2 A^T A only (U = 0)                            */
+  SDP_PRECOND_WOODBURY = 1  /* Ht = tau^2 A^T A + UU UU^T, eq. (AtIUUtAt)/(SMW2)   */
+} sdp_precond_kind;
+
+typedef struct {
+  double gap_tol;      /* relative duality gap |C.X-b^Ty|/(1+|C.X|+|b^Ty|); 1e-6 */
+  double infeas_tol;   /* ||b-A X||/(1+||b||) and ||C-S-A^T y||_F/(1+||C||_F);  1e-6 */
+  double pcg_rtol;     /* PCG stop: ||H dy - r|| <= pcg_rtol ||r||;  1e-8          */
+  int ipm_maxit;       /* 100 */
+  int pcg_maxit;       /* 1000 */
+  int refine_maxit;    /* outer FP64 refinement sweeps for prec != FP64; 8         */
+  int k;               /* rank k of the W split (eq. Wsplit2); 0 = value of sdp_setup */
+  double step_frac;    /* fraction of the step to the boundary; 0.9                */
+  int prec;            /* sdp_prec used inside PCG by sdp_ipm_step / sdp_solve     */
+  int precond;         /* sdp_precond_kind; SDP_PRECOND_WOODBURY                   */
+  double inner_rtol;   /* PCG tolerance of a reduced-precision inner solve; 1e-4   */
+  int verbose;         /* 1 = one line per IPM iteration on stderr                 */
+} sdp_params;
+
+typedef struct {
+  int iter;                 /* IPM iteration index that produced this record      */
+  double mu;                /* X.S / n                                             */
+  double obj_p, obj_d;      /* C.X and b^T y                                       */
+  double relgap, pinf, dinf;
+  double alpha_p, alpha_d, sigma;
+  double tau;               /* lambda_min(W) of the split                          */
+  int pcg_iters_pred, pcg_iters_corr;
+  double pcg_relres_pred, pcg_relres_corr;   /* true FP64 residuals              */
+  int converged;            /* 1 when the stopping test held at entry              */
+} sdp_ipm_info;
+
+typedef struct {
+  double obj_p, obj_d, relgap, pinf, dinf;
+  int iters;                /* IPM iterations taken                                */
+  int pcg_iters_total;
+  int converged;
+  double seconds;           /* host wall time of the solve                         */
+} sdp_result;
+
+/* Fill *prm with the defaults listed above. */
+void sdp_default_params(sdp_params* prm);
+
+/*
+ * sdp_setup -- eq. (SDP): copy C, the A_i and b to the device and build the
+ * sparse constraint operator: the CSR pattern of V = sum_i v_i A_i (union of all
+ * supports, both triangles), the gather map slot -> (constraint, coefficient),
+ * the per-constraint entry list used by the Hessian gather, and
+ * (A^T A)^{-1} = diag(1/||A_i||_F^2).  Assumption 2 is required in the form
+ * "A^T A diagonal": SDP_ERR_UNSUPPORTED if two constraints have a nonzero inner
+ * product.  Sets the start point X = S = xi I, y = 0.
+ *   n >= 1, m >= 1, 1 <= k <= n.  C triplets: nnzC >= 0 (Ci, Cj, Cv may be
+ *   NULL when nnzC == 0).  A triplets: (Ak[t], Ai[t], Aj[t], Av[t]) adds Av[t]
+ *   at (Ai,Aj) and (Aj,Ai) of A_{Ak[t]}.  b has m entries.  prm may be NULL
+ *   (defaults).  cuda_stream is a cudaStream_t or NULL.  On success *out owns
+ *   the problem; on failure *out is NULL.
+ */
+sdp_status sdp_setup(int n, int m,
+                     int64_t nnzC, const int32_t* Ci, const int32_t* Cj, const double* Cv,
+                     int64_t nnzA, const int32_t* Ak, const int32_t* Ai, const int32_t* Aj,
+                     const double* Av, const double* b, int k, const sdp_params* prm,
+                     void* cuda_stream, sdp_problem** out);
+
+/*
+ * sdp_hessian_matvec -- eq. (hesseqn2): Hv_dev[i] = A_i . (W (sum_j v_dev[j] A_j) W)
+ * for the handle's current scaling matrix W (set by sdp_ipm_step or sdp_set_W).
+ * Matrix-free: V = sum v_j A_j on the CSR pattern, T = W V (sparse gather
+ * SpMM), then one dot W[p,:] . T[q,:] per stored constraint entry.
+ * v_dev, Hv_dev: device double[m].  prec: sdp_prec.
+ */
+sdp_status sdp_hessian_matvec(sdp_problem* h, const double* v_dev, double* Hv_dev, int prec);
+
+/*
+ * sdp_precond_build -- Algorithm 1 steps 1-2 for the current W:
+ * tau = lambda_min(W), U = V_l (Lambda_l - tau I)^{1/2} from the k largest
+ * eigenpairs (eq. Wsplit2), Z = chol(2 W0 + U U^T) (eq. hessExp2), the core
+ * S = tau^2 I + UU^T (A^T A)^{-1} UU with UU = A^T (U kron Z) (eq. SMW2, using
+ * tau^2), its Cholesky factor L and L^{-1}.  SDP_ERR_NOT_PD if a factor fails.
+ */
+sdp_status sdp_precond_build(sdp_problem* h);
+
+/*
+ * sdp_precond_apply -- eq. (SMW2): z = (tau^2 G)^{-1} (r - UU S^{-1} UU^T G^{-1} r)
+ * with G = A^T A, UU^T y = Z^T (sum y_i A_i) U and (UU X)_i = A_i . (Z X U^T)
+ * (eq. Umv).  r_dev, z_dev: device double[m].  Needs sdp_precond_build first.
+ */
+sdp_status sdp_precond_apply(sdp_problem* h, const double* r_dev, double* z_dev, int prec);
+
+/*
+ * sdp_pcg_solve -- Algorithm 1 step 3: PCG for H y = r from y = 0 with the
+ * built preconditioner, stopping when ||r - H y|| <= rtol ||r|| (recursive
+ * residual) or after maxit iterations (SDP_ERR_MAXIT, y = last iterate).
+ * prec selects the matvec/preconditioner precision; for prec != FP64 the solve
+ * is an FP64 iterative refinement whose true residual is recomputed in FP64.
+ * r_dev, y_dev: device double[m].  iters, relres (true FP64 relative residual)
+ * may be NULL.
+ */
+sdp_status sdp_pcg_solve(sdp_problem* h, const double* r_dev, double* y_dev, double rtol,
+                         int maxit, int prec, int* iters, double* relres);
+
+/*
+ * sdp_ipm_step -- one iteration of the infeasible NT predictor-corrector:
+ * residuals; NT scaling W = L Q Lambda^{-1/2} Q^T L^T (X = L L^T, L^T S L = Q Lambda Q^T);
+ * sdp_precond_build; predictor (sigma = 0) and corrector (sigma = (mu_aff/mu)^3)
+ * Newton directions, each from H dy = Rp - A(Rc) + A(W Rd W) solved by PCG;
+ * step to step_frac of the boundary; update.  info may be NULL.  Returns
+ * SDP_OK also when the point already satisfies the stopping test
+ * (info->converged = 1, nothing changed).
+ */
+sdp_status sdp_ipm_step(sdp_problem* h, sdp_ipm_info* info);
+
+/* sdp_solve -- repeat sdp_ipm_step until converged or ipm_maxit.  res may be NULL. */
+sdp_status sdp_solve(sdp_problem* h, sdp_result* res);
+
+/* Replace the scaling matrix W by W_dev (device double[n*n], symmetric positive definite). */
+sdp_status sdp_set_W(sdp_problem* h, const double* W_dev);
+
+/* Copy the current W to device memory W_dev (double[n*n]). */
+sdp_status sdp_get_W(sdp_problem* h, double* W_dev);
+
+/* Copy the current iterate to host arrays (each may be NULL): X, S n*n; y m. */
+sdp_status sdp_get_solution(sdp_problem* h, double* X_host, double* y_host, double* S_host);
+
+/* Replace the current iterate by host arrays X, S (n*n) and y (m); iter sets the counter. */
+sdp_status sdp_set_state(sdp_problem* h, const double* X_host, const double* y_host,
+                         const double* S_host, int iter);
+
+/* tau and the split rank used by the last sdp_precond_build. */
+sdp_status sdp_precond_info(sdp_problem* h, double* tau, int* k);
+
+/* Problem sizes: n, m, k, nnz of the V pattern. */
+sdp_status sdp_sizes(const sdp_problem* h, int* n, int* m, int* k, int64_t* nnzV);
+
+/* Reset the iterate to the start point X = S = xi I, y = 0 on the device (no host
+ * transfer); the preconditioner and W are invalidated. */
+sdp_status sdp_reset(sdp_problem* h);
+
+/*
+ * Per-kernel-class timing for measurement.  sdp_timing_enable(h, cls) records a
+ * pair of CUDA events on the handle's stream around every later launch of the
+ * kernel class `cls` ("gemm_f64", "sytrd", "matvec", "potrf", "trsm", "stein",
+ * "ormtr", "precond_apply"); NULL turns recording off.  sdp_timing_read
+ * synchronises the stream and returns the accumulated device milliseconds,
+ * launch count, and algorithmic flops and bytes of the recorded launches, then
+ * clears the accumulators.  Any pointer may be NULL.
+ */
+sdp_status sdp_timing_enable(sdp_problem* h, const char* cls);
+sdp_status sdp_timing_read(sdp_problem* h, double* ms, int64_t* launches, double* flops, double* bytes);
+
+/* Number of kernel launches issued by this handle since setup (for accounting). */
+int64_t sdp_launch_count(const sdp_problem* h);
+
+void sdp_destroy(sdp_problem* h);
+const char* sdp_status_str(sdp_status s);
+const char* sdp_last_error(const sdp_problem* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDPGB_H */

@@ -1,0 +1,8 @@
+"""GB300 (sm_103a) implementation of the PCG Hessian solve of the modified
+interior-point method (Zhang & Lavaei, arXiv 1703.10973), behind the libsdpgb
+C ABI declared in include/sdpgb.h."""
+from ._build import LIB, build  # noqa: F401
+from ._lib import SDPError, load  # noqa: F401
+from .api import SDPProblem, default_params  # noqa: F401
+
+__all__ = ["SDPProblem", "default_params", "SDPError", "build", "load", "LIB"]

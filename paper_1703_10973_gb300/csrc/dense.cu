@@ -1,0 +1,540 @@
+// Dense FP64 building blocks: tiled GEMM, blocked Cholesky, blocked triangular
+// solves, reductions and elementwise kernels.  All matrices are row-major.
+//
+// On GB300 the FP64 pipe runs at about 1/60 of the FP32 rate, so every FP64
+// kernel here is arithmetic-bound long before it is memory-bound: the GEMM keeps
+// a 64 x 64 tile per CTA (4 x 4 per thread) and does 16 FMAs per shared-memory
+// operand pair, far above the ratio the FP64 pipe needs.
+#include "internal.cuh"
+
+#include <algorithm>
+
+namespace sdpgb {
+
+int64_t g_launches = 0;
+
+static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// GEMM:  C = alpha op(A) op(B) + beta C
+// ---------------------------------------------------------------------------
+template <typename T, int BM, int BN, bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A,
+                                              int lda, const T* __restrict__ B, int ldb, T beta,
+                                              T* __restrict__ C, int ldc, int lower_only,
+                                              long long sA, long long sB, long long sC) {
+  constexpr int BK = 16;
+  constexpr int TM = BM / 16, TN = BN / 16;
+  const int bm = blockIdx.y * BM, bn = blockIdx.x * BN;
+  if (lower_only && bn > bm + BM - 1) return;
+  A += (long long)blockIdx.z * sA;
+  B += (long long)blockIdx.z * sB;
+  C += (long long)blockIdx.z * sC;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int t = threadIdx.x; t < BM * BK; t += 256) {
+      int r, c;
+      if (!TA) { r = t / BK; c = t % BK; } else { c = t / BM; r = t % BM; }
+      const int gr = bm + r, gc = k0 + c;
+      T v = T(0);
+      if (gr < M && gc < K) v = TA ? A[(size_t)gc * lda + gr] : A[(size_t)gr * lda + gc];
+      As[c][r] = v;
+    }
+    for (int t = threadIdx.x; t < BK * BN; t += 256) {
+      int r, c;
+      if (!TB) { r = t / BN; c = t % BN; } else { c = t / BK; r = t % BK; }
+      const int gr = k0 + r, gc = bn + c;
+      T v = T(0);
+      if (gr < K && gc < N) v = TB ? B[(size_t)gc * ldb + gr] : B[(size_t)gr * ldb + gc];
+      Bs[r][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int r = bm + ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int c = bn + tx + 16 * j;
+      if (c >= N) continue;
+      T v = alpha * acc[i][j];
+      if (beta != T(0)) v = fma(beta, C[(size_t)r * ldc + c], v);
+      C[(size_t)r * ldc + c] = v;
+    }
+  }
+}
+
+template <typename T, int BM, int BN>
+static void gemm_launch(cudaStream_t st, bool tA, bool tB, int M, int N, int K, T alpha, const T* A,
+                        int lda, const T* B, int ldb, T beta, T* C, int ldc, int lower_only,
+                        int batch, long long sA, long long sB, long long sC) {
+  dim3 grid(cdiv(N, BN), cdiv(M, BM), batch);
+  count_launch();
+  if (!tA && !tB)
+    k_gemm<T, BM, BN, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, sA, sB, sC);
+  else if (!tA && tB)
+    k_gemm<T, BM, BN, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, sA, sB, sC);
+  else if (tA && !tB)
+    k_gemm<T, BM, BN, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, sA, sB, sC);
+  else
+    k_gemm<T, BM, BN, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, sA, sB, sC);
+}
+
+void gemm(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
+          int lda, const double* B, int ldb, double beta, double* C, int ldc, int lower_only,
+          int batch, long long sA, long long sB, long long sC) {
+  if (M <= 0 || N <= 0) return;
+  if (K <= 0) {  // C = beta C
+    if (beta == 0.0) {
+      for (int b = 0; b < batch; ++b) copy2d(st, M, N, nullptr, 0, C + b * sC, ldc);
+    } else {
+      gemm_launch<double, 32, 32>(st, false, false, M, N, 1, 0.0, C, ldc, C, ldc, beta, C, ldc,
+                                  lower_only, batch, sC, sC, sC);
+    }
+    return;
+  }
+  const long long tiles64 = (long long)cdiv(M, 64) * cdiv(N, 64) * batch;
+  const bool timed = ktimer_on("gemm_f64");
+  if (timed) ktimer_begin(st, "gemm_f64");
+  if (tiles64 >= 2 * 152)
+    gemm_launch<double, 64, 64>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, batch, sA, sB, sC);
+  else
+    gemm_launch<double, 32, 32>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, batch, sA, sB, sC);
+  if (timed) {
+    const double f = 2.0 * M * N * (double)K * batch * (lower_only ? 0.5 : 1.0);
+    const double by = 8.0 * ((double)M * K + (double)K * N + 2.0 * M * N) * batch;
+    ktimer_end(st, "gemm_f64", f, by);
+  }
+}
+
+void gemm_f32(cudaStream_t st, bool tA, bool tB, int M, int N, int K, float alpha, const float* A,
+              int lda, const float* B, int ldb, float beta, float* C, int ldc) {
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  gemm_launch<float, 64, 64>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, 1, 0, 0, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise helpers
+// ---------------------------------------------------------------------------
+__global__ void k_fill(double* x, size_t count, double v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) x[i] = v;
+}
+void fill(cudaStream_t st, double* x, size_t count, double v) {
+  if (!count) return;
+  count_launch();
+  k_fill<<<std::min<unsigned>(cdiv(count, 256), 4096), 256, 0, st>>>(x, count, v);
+}
+
+__global__ void k_copy2d(int rows, int cols, const double* __restrict__ s, int lds, double* __restrict__ d, int ldd) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / cols), c = (int)(t % cols);
+    d[(size_t)r * ldd + c] = s ? s[(size_t)r * lds + c] : 0.0;
+  }
+}
+void copy2d(cudaStream_t st, int rows, int cols, const double* src, int lds, double* dst, int ldd) {
+  if (rows <= 0 || cols <= 0) return;
+  count_launch();
+  k_copy2d<<<std::min<unsigned>(cdiv((size_t)rows * cols, 256), 8192), 256, 0, st>>>(rows, cols, src, lds, dst, ldd);
+}
+
+__global__ void k_transpose(int rows, int cols, const double* __restrict__ s, int lds, double* __restrict__ d, int ldd) {
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = s[(size_t)r * lds + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) d[(size_t)c * ldd + r] = tile[threadIdx.x][i];
+  }
+}
+void transpose(cudaStream_t st, int rows, int cols, const double* src, int lds, double* dst, int ldd) {
+  if (rows <= 0 || cols <= 0) return;
+  count_launch();
+  k_transpose<<<dim3(cdiv(cols, 32), cdiv(rows, 32)), dim3(32, 8), 0, st>>>(rows, cols, src, lds, dst, ldd);
+}
+
+// A_ij = A_ji for i < j (copy the lower triangle into the upper one) or average.
+template <int MODE>
+__global__ void k_sym(int n, double* A, int lda) {
+  __shared__ double tl[32][33], tu[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  const int r0 = bi * 32, c0 = bj * 32;  // lower tile (r0, c0), mirror tile (c0, r0)
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    int r = r0 + i, c = c0 + threadIdx.x;
+    tl[i][threadIdx.x] = (r < n && c < n) ? A[(size_t)r * lda + c] : 0.0;
+    r = c0 + i; c = r0 + threadIdx.x;
+    tu[i][threadIdx.x] = (r < n && c < n) ? A[(size_t)r * lda + c] : 0.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    // element (c0+i, r0+tx) of the upper tile mirrors (r0+tx, c0+i) of the lower tile
+    const int ru = c0 + i, cu = r0 + threadIdx.x;
+    const int rl = r0 + i, cl = c0 + threadIdx.x;
+    const double lo_m = tl[threadIdx.x][i];  // A[r0+tx][c0+i]
+    const double up_m = tu[threadIdx.x][i];  // A[c0+tx][r0+i]
+    if (MODE == 0) {
+      if (ru < n && cu < n && cu > ru) A[(size_t)ru * lda + cu] = lo_m;
+    } else {
+      const double lo = tl[i][threadIdx.x];  // A[rl][cl]
+      const double avg = 0.5 * (lo + up_m);
+      if (rl < n && cl < n) A[(size_t)rl * lda + cl] = avg;
+      if (ru < n && cu < n && ru != cu) A[(size_t)ru * lda + cu] = 0.5 * (tu[i][threadIdx.x] + lo_m);
+    }
+  }
+}
+void symmetrize_lower(cudaStream_t st, int n, double* A, int lda) {
+  count_launch();
+  k_sym<0><<<dim3(cdiv(n, 32), cdiv(n, 32)), dim3(32, 8), 0, st>>>(n, A, lda);
+}
+void symmetrize_avg(cudaStream_t st, int n, double* A, int lda) {
+  count_launch();
+  k_sym<1><<<dim3(cdiv(n, 32), cdiv(n, 32)), dim3(32, 8), 0, st>>>(n, A, lda);
+}
+
+__global__ void k_add_diag(int n, double* A, int lda, double v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) A[(size_t)i * lda + i] += v;
+}
+void add_diag(cudaStream_t st, int n, double* A, int lda, double v) {
+  count_launch();
+  k_add_diag<<<cdiv(n, 256), 256, 0, st>>>(n, A, lda, v);
+}
+
+__global__ void k_scale_cols(int rows, int cols, const double* __restrict__ A, int lda,
+                             const double* __restrict__ s, double pw, double* __restrict__ B, int ldb) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / cols), c = (int)(t % cols);
+    const double f = (pw == 1.0) ? s[c] : (pw == -1.0) ? 1.0 / s[c] : pow(s[c], pw);
+    B[(size_t)r * ldb + c] = A[(size_t)r * lda + c] * f;
+  }
+}
+void scale_cols(cudaStream_t st, int rows, int cols, const double* A, int lda, const double* s,
+                double pw, double* B, int ldb) {
+  count_launch();
+  k_scale_cols<<<std::min<unsigned>(cdiv((size_t)rows * cols, 256), 8192), 256, 0, st>>>(rows, cols, A, lda, s, pw, B, ldb);
+}
+
+__global__ void k_zero_upper(int n, double* A, int lda) {
+  const size_t total = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / n), c = (int)(t % n);
+    if (c > r) A[(size_t)r * lda + c] = 0.0;
+  }
+}
+void zero_upper(cudaStream_t st, int n, double* A, int lda) {
+  count_launch();
+  k_zero_upper<<<std::min<unsigned>(cdiv((size_t)n * n, 256), 8192), 256, 0, st>>>(n, A, lda);
+}
+
+__global__ void k_axpby(size_t count, double a, const double* x, double b, const double* y, double* z) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    z[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+void axpby(cudaStream_t st, size_t count, double a, const double* x, double b, const double* y, double* z) {
+  if (!count) return;
+  count_launch();
+  k_axpby<<<std::min<unsigned>(cdiv(count, 256), 8192), 256, 0, st>>>(count, a, x, b, y, z);
+}
+
+__global__ void k_to_f32(size_t count, const double* x, float* y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) y[i] = (float)x[i];
+}
+void to_f32(cudaStream_t st, size_t count, const double* x, float* y) {
+  count_launch();
+  k_to_f32<<<std::min<unsigned>(cdiv(count, 256), 8192), 256, 0, st>>>(count, x, y);
+}
+__global__ void k_to_bf16(size_t count, const double* x, __nv_bfloat16* y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn((float)x[i]);
+}
+void to_bf16(cudaStream_t st, size_t count, const double* x, __nv_bfloat16* y) {
+  count_launch();
+  k_to_bf16<<<std::min<unsigned>(cdiv(count, 256), 8192), 256, 0, st>>>(count, x, y);
+}
+
+// ---------------------------------------------------------------------------
+// Reductions (deterministic: fixed partition, fixed summation order)
+// ---------------------------------------------------------------------------
+constexpr int DOT_BLOCKS = 512;
+size_t dot_part_doubles() { return DOT_BLOCKS; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (l < (int)(blockDim.x / 32)) ? sh[l] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;  // valid in thread 0
+}
+
+__global__ void k_dot_part(size_t count, const double* __restrict__ x, const double* __restrict__ y, double* part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    s = fma(x[i], y[i], s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+__global__ void k_sum_part(int np, const double* part, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[0] = s;
+}
+void dot(cudaStream_t st, size_t count, const double* x, const double* y, double* out, double* part) {
+  count_launch(2);
+  k_dot_part<<<DOT_BLOCKS, 256, 0, st>>>(count, x, y, part);
+  k_sum_part<<<1, 512, 0, st>>>(DOT_BLOCKS, part, out);
+}
+
+// ---------------------------------------------------------------------------
+// Triangular matrix-vector products with a lower-triangular L
+// ---------------------------------------------------------------------------
+constexpr int TRMV_CHUNKS = 64;
+size_t trmv_part_doubles(int n) { return (size_t)n * TRMV_CHUNKS; }
+
+__global__ void k_trmv_n(int n, const double* __restrict__ L, int ldl, const double* __restrict__ x, double* __restrict__ y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  if (warp >= n) return;
+  const double* row = L + (size_t)warp * ldl;
+  double s = 0.0;
+  for (int j = lane; j <= warp; j += 32) s = fma(row[j], x[j], s);
+  s = warp_sum(s);
+  if (lane == 0) y[warp] = s;
+}
+// part[c][j] = sum_{i in chunk c, i >= j} L[i][j] x[i]
+__global__ void k_trmv_t_part(int n, const double* __restrict__ L, int ldl, const double* __restrict__ x, double* __restrict__ part) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  const int rows = (n + TRMV_CHUNKS - 1) / TRMV_CHUNKS;
+  const int i0 = c * rows, i1 = min(n, i0 + rows);
+  if (j >= n) return;
+  double s = 0.0;
+  for (int i = max(i0, j); i < i1; ++i) s = fma(L[(size_t)i * ldl + j], x[i], s);
+  part[(size_t)c * n + j] = s;
+}
+__global__ void k_trmv_t_sum(int n, const double* __restrict__ part, double* __restrict__ y) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < TRMV_CHUNKS; ++c) s += part[(size_t)c * n + j];
+  y[j] = s;
+}
+void trmv_lower(cudaStream_t st, bool trans, int n, const double* L, int ldl, const double* x, double* y, double* part) {
+  if (!trans) {
+    count_launch();
+    k_trmv_n<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, L, ldl, x, y);
+  } else {
+    count_launch(2);
+    k_trmv_t_part<<<dim3(cdiv(n, 128), TRMV_CHUNKS), 128, 0, st>>>(n, L, ldl, x, part);
+    k_trmv_t_sum<<<cdiv(n, 256), 256, 0, st>>>(n, part, y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked Cholesky and triangular solves
+// ---------------------------------------------------------------------------
+constexpr int NB = 64;
+
+// Factor the nbs x nbs diagonal block in place (lower) and write its inverse to Dinv (ld NB).
+__global__ void __launch_bounds__(256) k_potrf_diag(int nbs, double* A, int lda, double* Dinv, int* info, int base) {
+  extern __shared__ double sm[];
+  double* a = sm;                  // NB x (NB+1)
+  double* x = sm + NB * (NB + 1);  // NB x (NB+1)
+  constexpr int LD = NB + 1;
+  for (int t = threadIdx.x; t < nbs * nbs; t += blockDim.x) {
+    const int i = t / nbs, j = t % nbs;
+    a[i * LD + j] = (j <= i) ? A[(size_t)i * lda + j] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < nbs; ++j) {
+    if (threadIdx.x == 0) {
+      double p = a[j * LD + j];
+      if (!(p > 0.0)) {
+        if (info && *info == 0) *info = base + j + 1;
+        p = 1.0;
+      }
+      a[j * LD + j] = sqrt(p);
+    }
+    __syncthreads();
+    const double ljj = a[j * LD + j];
+    for (int i = j + 1 + threadIdx.x; i < nbs; i += blockDim.x) a[i * LD + j] /= ljj;
+    __syncthreads();
+    const int w = nbs - j - 1;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      const int i = j + 1 + t / w, l = j + 1 + t % w;
+      if (l <= i) a[i * LD + l] -= a[i * LD + j] * a[l * LD + j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nbs * nbs; t += blockDim.x) {
+    const int i = t / nbs, j = t % nbs;
+    A[(size_t)i * lda + j] = (j <= i) ? a[i * LD + j] : 0.0;
+  }
+  if (Dinv) {
+    if (threadIdx.x < nbs) {
+      const int c = threadIdx.x;
+      for (int i = 0; i < nbs; ++i) {
+        double v = 0.0;
+        if (i >= c) {
+          double s = (i == c) ? 1.0 : 0.0;
+          for (int l = c; l < i; ++l) s -= a[i * LD + l] * x[l * LD + c];
+          v = s / a[i * LD + i];
+        }
+        x[i * LD + c] = v;
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+      const int i = t / NB, j = t % NB;
+      Dinv[(size_t)i * NB + j] = (i < nbs && j < nbs) ? x[i * LD + j] : 0.0;
+    }
+  }
+}
+
+// Inverse of each lower-triangular diagonal block of L (one CTA per block).
+__global__ void __launch_bounds__(64) k_inv_diag(int n, const double* L, int ldl, double* Dinv) {
+  extern __shared__ double sm[];
+  constexpr int LD = NB + 1;
+  double* a = sm;             // NB x LD
+  double* x = sm + NB * LD;   // NB x LD
+  const int b = blockIdx.x, k0 = b * NB, nbs = min(NB, n - k0);
+  for (int t = threadIdx.x; t < nbs * nbs; t += blockDim.x) {
+    const int i = t / nbs, j = t % nbs;
+    a[i * LD + j] = (j <= i) ? L[(size_t)(k0 + i) * ldl + k0 + j] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < nbs) {
+    const int c = threadIdx.x;
+    for (int i = 0; i < nbs; ++i) {
+      double v = 0.0;
+      if (i >= c) {
+        double s = (i == c) ? 1.0 : 0.0;
+        for (int l = c; l < i; ++l) s -= a[i * LD + l] * x[l * LD + c];
+        v = s / a[i * LD + i];
+      }
+      x[i * LD + c] = v;
+    }
+  }
+  __syncthreads();
+  double* D = Dinv + (size_t)b * NB * NB;
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    const int i = t / NB, j = t % NB;
+    D[t] = (i < nbs && j < nbs) ? x[i * LD + j] : 0.0;
+  }
+}
+
+size_t potrf_work_doubles(int n) { return (size_t)NB * NB + (size_t)n * NB; }
+
+void potrf(cudaStream_t st, int n, double* A, int lda, int* info_dev, double* work) {
+  static bool attr = false;
+  const size_t smem = 2 * NB * (NB + 1) * sizeof(double);
+  if (!attr) {
+    cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  double* Dinv = work;
+  double* tmp = work + NB * NB;   // (n) x NB panel
+  ktimer_begin(st, "potrf");
+  cudaMemsetAsync(info_dev, 0, sizeof(int), st);
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kbs = std::min(NB, n - k0);
+    double* Akk = A + (size_t)k0 * lda + k0;
+    count_launch();
+    k_potrf_diag<<<1, 256, smem, st>>>(kbs, Akk, lda, Dinv, info_dev, k0);
+    const int r0 = k0 + kbs;
+    const int rows = n - r0;
+    if (rows <= 0) break;
+    double* P = A + (size_t)r0 * lda + k0;
+    // panel: P <- P L_kk^{-T}
+    gemm(st, false, true, rows, kbs, kbs, 1.0, P, lda, Dinv, NB, 0.0, tmp, NB);
+    copy2d(st, rows, kbs, tmp, NB, P, lda);
+    // trailing: A22 -= P P^T (lower tiles only)
+    gemm(st, false, true, rows, rows, kbs, -1.0, P, lda, P, lda, 1.0, A + (size_t)r0 * lda + r0, lda, 1);
+  }
+  zero_upper(st, n, A, lda);
+  ktimer_end(st, "potrf", (double)n * n * n / 3.0, 8.0 * n * n);
+}
+
+size_t trsm_work_doubles(int n, int nrhs) {
+  const int nblk = (n + NB - 1) / NB;
+  return (size_t)nblk * NB * NB + (size_t)NB * nrhs;
+}
+
+void trsm_left_lower(cudaStream_t st, bool trans, int n, int nrhs, const double* L, int ldl, double* B,
+                     int ldb, double* work) {
+  const int nblk = (n + NB - 1) / NB;
+  double* Dinv = work;
+  double* tmp = work + (size_t)nblk * NB * NB;
+  ktimer_begin(st, "trsm");
+  const size_t smem = 2 * NB * (NB + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_inv_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  count_launch();
+  k_inv_diag<<<nblk, 64, smem, st>>>(n, L, ldl, Dinv);
+  if (!trans) {
+    for (int b = 0; b < nblk; ++b) {
+      const int k0 = b * NB, kbs = std::min(NB, n - k0);
+      double* Bk = B + (size_t)k0 * ldb;
+      gemm(st, false, false, kbs, nrhs, kbs, 1.0, Dinv + (size_t)b * NB * NB, NB, Bk, ldb, 0.0, tmp, nrhs);
+      copy2d(st, kbs, nrhs, tmp, nrhs, Bk, ldb);
+      const int r0 = k0 + kbs;
+      if (r0 < n)
+        gemm(st, false, false, n - r0, nrhs, kbs, -1.0, L + (size_t)r0 * ldl + k0, ldl, Bk, ldb, 1.0,
+             B + (size_t)r0 * ldb, ldb);
+    }
+  } else {
+    for (int b = nblk - 1; b >= 0; --b) {
+      const int k0 = b * NB, kbs = std::min(NB, n - k0);
+      double* Bk = B + (size_t)k0 * ldb;
+      gemm(st, true, false, kbs, nrhs, kbs, 1.0, Dinv + (size_t)b * NB * NB, NB, Bk, ldb, 0.0, tmp, nrhs);
+      copy2d(st, kbs, nrhs, tmp, nrhs, Bk, ldb);
+      if (k0 > 0)
+        gemm(st, true, false, k0, nrhs, kbs, -1.0, L + (size_t)k0 * ldl, ldl, Bk, ldb, 1.0, B, ldb);
+    }
+  }
+  ktimer_end(st, "trsm", (double)n * n * nrhs, 8.0 * ((double)n * n / 2 + 2.0 * n * nrhs));
+}
+
+}  // namespace sdpgb

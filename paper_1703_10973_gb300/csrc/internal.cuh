@@ -1,0 +1,273 @@
+// Internal declarations shared by the translation units of libsdpgb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sdpgb.h"
+
+namespace sdpgb {
+
+// ---------------------------------------------------------------------------
+// Error plumbing: every CUDA call inside the library goes through CK(), which
+// records the failing call on the handle and returns SDP_ERR_CUDA.
+// ---------------------------------------------------------------------------
+struct Err {
+  sdp_status st = SDP_OK;
+  std::string msg;
+};
+
+#define SDP_CK(h, call)                                                          \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      (h)->set_error(SDP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+      return SDP_ERR_CUDA;                                                       \
+    }                                                                            \
+  } while (0)
+
+#define SDP_TRY(expr)                                                            \
+  do {                                                                           \
+    sdp_status s_ = (expr);                                                      \
+    if (s_ != SDP_OK) return s_;                                                 \
+  } while (0)
+
+// Launch accounting: every kernel launch in the library increments this counter
+// (per process); sdp_launch_count() reports it per handle via a snapshot.
+extern int64_t g_launches;
+inline void count_launch(int k = 1) { g_launches += k; }
+
+// Optional event timing of one kernel class (sdp_timing_enable / sdp_timing_read).
+// ktimer_begin/ktimer_end bracket a launch; they do nothing unless `cls` is the
+// class currently enabled.
+bool ktimer_on(const char* cls);
+void ktimer_begin(cudaStream_t st, const char* cls);
+void ktimer_end(cudaStream_t st, const char* cls, double flops, double bytes);
+void ktimer_set(const char* cls);
+void ktimer_read(double* ms, int64_t* launches, double* flops, double* bytes);
+
+// Device buffer owned by a handle.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Dense FP64 linear algebra (dense.cu).  Row-major storage; ld = row stride.
+// ---------------------------------------------------------------------------
+// C[M x N] = alpha * op(A) * op(B) + beta * C.  op(A) is M x K.  When
+// lower_only != 0 tiles strictly above the diagonal of C are skipped.
+// Batched over `batch` with element strides sA, sB, sC.
+void gemm(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha,
+          const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+          int lower_only = 0, int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0);
+void gemm_f32(cudaStream_t st, bool tA, bool tB, int M, int N, int K, float alpha,
+              const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc);
+
+// In-place lower Cholesky A = L L^T of an n x n matrix (strict upper part set to 0).
+// info_dev receives 0 on success or (index + 1) of the first non-positive pivot.
+// work: at least potrf_work_doubles(n) doubles.
+size_t potrf_work_doubles(int n);
+void potrf(cudaStream_t st, int n, double* A, int lda, int* info_dev, double* work);
+
+// Triangular solves with a lower-triangular L (n x n), in place on B (n x nrhs):
+// trans == false: B <- L^{-1} B;  trans == true: B <- L^{-T} B.
+size_t trsm_work_doubles(int n, int nrhs);
+void trsm_left_lower(cudaStream_t st, bool trans, int n, int nrhs, const double* L, int ldl,
+                     double* B, int ldb, double* work);
+
+// Elementwise helpers.
+void fill(cudaStream_t st, double* x, size_t count, double v);
+void copy2d(cudaStream_t st, int rows, int cols, const double* src, int lds, double* dst, int ldd);
+void transpose(cudaStream_t st, int rows, int cols, const double* src, int lds, double* dst, int ldd);
+void symmetrize_lower(cudaStream_t st, int n, double* A, int lda);     // A_ij (i<j) = A_ji
+void symmetrize_avg(cudaStream_t st, int n, double* A, int lda);       // A = (A + A^T)/2
+void add_diag(cudaStream_t st, int n, double* A, int lda, double v);
+void scale_cols(cudaStream_t st, int rows, int cols, const double* A, int lda, const double* s,
+                double pw, double* B, int ldb);                        // B = A diag(s^pw)
+void zero_upper(cudaStream_t st, int n, double* A, int lda);
+void axpby(cudaStream_t st, size_t count, double a, const double* x, double b, const double* y,
+           double* z);                                                 // z = a x + b y
+void to_f32(cudaStream_t st, size_t count, const double* x, float* y);
+void to_bf16(cudaStream_t st, size_t count, const double* x, __nv_bfloat16* y);
+
+// Deterministic reductions into device memory (two stages, fixed order).
+// out[0] = sum_i x_i y_i.
+void dot(cudaStream_t st, size_t count, const double* x, const double* y, double* out, double* part);
+size_t dot_part_doubles();
+
+// Lower-triangular GEMV y = L x and y = L^T x (L n x n row-major).  part: n * TRMV_CHUNKS doubles.
+void trmv_lower(cudaStream_t st, bool trans, int n, const double* L, int ldl, const double* x,
+                double* y, double* part);
+size_t trmv_part_doubles(int n);
+
+// ---------------------------------------------------------------------------
+// Symmetric eigensolver (eig.cu).  A is n x n row-major symmetric and is
+// overwritten (it receives the Householder vectors of the tridiagonalisation).
+// ---------------------------------------------------------------------------
+struct EigWork {
+  double* d = nullptr;      // n   diagonal of T
+  double* e = nullptr;      // n   off-diagonal of T
+  double* tauh = nullptr;   // n   Householder scalars
+  double* p = nullptr;      // n   symv result
+  double* part = nullptr;   // 4096 block partials
+  unsigned int* bar = nullptr;  // 2 barrier words
+  int* flag = nullptr;      // 1 error flag (barrier timeout)
+  double* ws = nullptr;     // inverse-iteration workspace: 6 * n * batch doubles
+  int batch = 0;
+  double* G = nullptr;      // n x n Gram matrix for the re-orthogonalisation
+  double* aux = nullptr;    // trsm / potrf work
+  int* info = nullptr;      // potrf info
+  double* wsel = nullptr;   // selected eigenvalues
+};
+size_t eig_work_bytes(int n, bool full);
+void eig_work_carve(EigWork* w, void* base, int n, bool full);
+
+// Full eigendecomposition: w ascending, E row t = unit eigenvector of w[t].
+sdp_status eig_full(cudaStream_t st, int n, double* A, double* w, double* E, EigWork* ws);
+// Smallest eigenvalue only (result in *lmin_dev, device).
+sdp_status eig_min(cudaStream_t st, int n, double* A, double* lmin_dev, EigWork* ws);
+// Smallest eigenvalue and the top-k eigenpairs: wtop[0..k) ascending (= lambda_{n-k..n-1}),
+// Etop rows = eigenvectors; *lmin_dev = lambda_0.
+sdp_status eig_extremes(cudaStream_t st, int n, double* A, int k, double* lmin_dev, double* wtop,
+                        double* Etop, EigWork* ws);
+// Reads the barrier-timeout flag; nonzero -> SDP_ERR_TIMEOUT.
+int eig_flag(cudaStream_t st, EigWork* ws);
+
+}  // namespace sdpgb
+
+// ---------------------------------------------------------------------------
+// The handle.
+// ---------------------------------------------------------------------------
+struct sdp_problem {
+  int n = 0, m = 0, k = 0;
+  sdp_params prm{};
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  int64_t launches_at_setup = 0;
+
+  // ---- sparse constraint operator (device) ----
+  int nnzV = 0;            // CSR pattern of V = sum v_i A_i (both triangles)
+  int* rowptr = nullptr;   // n+1
+  int* colidx = nullptr;   // nnzV
+  int* sptr = nullptr;     // nnzV+1  slot -> contributors
+  int* scon = nullptr;     // contributors: constraint
+  double* scoef = nullptr; // contributors: coefficient
+  int ncontrib = 0;
+  int nent = 0;            // stored upper entries over all constraints
+  int* eptr = nullptr;     // m+1   constraint -> entries
+  int* ep = nullptr;       // entry row (p <= q)
+  int* eq = nullptr;       // entry col
+  double* ecoef = nullptr; // entry value
+  double* ginv = nullptr;  // m   1/||A_i||_F^2
+  // K-pattern for the core formation (pairs of support rows of each constraint)
+  int ncr = 0;             // constraint-row slots
+  int* crptr = nullptr;    // m+1   constraint -> support rows
+  int* crrow = nullptr;    // ncr   support row index
+  int* crlist_ptr = nullptr;  // ncr+1  (constraint,row) -> entries (col, coef) of A_i in that row
+  int* crlist_col = nullptr;
+  double* crlist_coef = nullptr;
+  int nnzK = 0;
+  int* krowptr = nullptr;  // n+1
+  int* kcol = nullptr;     // nnzK
+  int* kptr = nullptr;     // nnzK+1  K slot -> contributor triples
+  int* kcon = nullptr;     // constraint
+  int* kcra = nullptr;     // cr slot of row a
+  int* kcrb = nullptr;     // cr slot of row b
+  int nkc = 0;
+
+  // ---- data (device) ----
+  double* C = nullptr;     // n*n dense
+  double* b = nullptr;     // m
+  double normb = 0, normC = 0;
+
+  // ---- IPM state (device) ----
+  double *X = nullptr, *y = nullptr, *S = nullptr, *W = nullptr;
+  int iter = 0;
+  bool have_W = false;
+  double xi = 0;
+
+  // ---- matvec work ----
+  double* Vval = nullptr;  // nnzV
+  double* T = nullptr;     // n*n
+  float* W32 = nullptr;    // n*n (reduced-precision copies, lazily allocated)
+  float* T32 = nullptr;
+  __nv_bfloat16* W16 = nullptr;
+  bool W32_valid = false, W16_valid = false;
+
+  // ---- preconditioner ----
+  bool pc_valid = false;
+  double tau = 0;
+  double core_shift = 0;   // diagonal of the factored core (tau^2, or more after a retry)
+  int kpc = 0;             // split rank used
+  double* U = nullptr;     // n*k
+  double* Z = nullptr;     // n*n
+  double* Sc = nullptr;    // nk*nk core, then its Cholesky factor
+  double* Linv = nullptr;  // nk*nk inverse of the factor
+  double* tau_dev = nullptr;  // device scalars: [0] tau, [1] lmin scratch
+  double* wtop = nullptr;  // k
+  double* Etop = nullptr;  // k*n
+  double* au = nullptr;    // ncr*k   (A_i u_l) restricted to support rows
+  double* Kval = nullptr;  // nnzK
+  double* KZ = nullptr;    // n*n
+  double* pvec = nullptr;  // scratch vectors for the apply
+  double* Bn = nullptr;    // n*k
+  double* uvec = nullptr;  // nk
+  double* uvec2 = nullptr; // nk
+  double* trpart = nullptr;
+
+  // ---- dense IPM work ----
+  double *L = nullptr, *Rs = nullptr, *M1 = nullptr, *M2 = nullptr, *M3 = nullptr;
+  double *Gt = nullptr, *Sinv = nullptr, *Rd = nullptr, *Rc = nullptr, *dX = nullptr,
+         *dS = nullptr, *E = nullptr, *lam = nullptr;
+  double *Rp = nullptr, *rhs = nullptr, *dy = nullptr;
+  double* work = nullptr;  // trsm / potrf work
+  size_t work_doubles = 0;
+  int* info = nullptr;
+  double* scal = nullptr;  // device scalar scratch (64)
+  double* part = nullptr;  // reduction partials
+  sdpgb::EigWork eig;
+  void* eig_base = nullptr;
+
+  // ---- PCG vectors ----
+  double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr, *px = nullptr,
+         *pbest = nullptr, *pcorr = nullptr;
+
+  std::vector<void*> owned;   // every cudaMalloc made for this handle
+
+  void set_error(sdp_status s, const std::string& msg) {
+    (void)s;
+    last_error = msg;
+  }
+  sdp_status alloc(void** p, size_t bytes);
+  template <typename T>
+  sdp_status allocT(T** p, size_t count) {
+    return alloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  }
+};
+
+namespace sdpgb {
+// matvec.cu
+sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec);
+sdp_status ensure_lowprec_W(sdp_problem* h, int prec);
+// sparse helpers used by the IPM and the preconditioner (matvec.cu)
+void assemble_V(sdp_problem* h, const double* v, const double* scale, double* Vval);
+void op_A_dense(sdp_problem* h, const double* X, double* out, double alpha, const double* add,
+                double beta);   // out = alpha * A(X) + beta * add
+void scatter_V_dense(sdp_problem* h, const double* Vval, double alpha, double* D);  // D += alpha*V
+void spmm_rows(sdp_problem* h, const double* Vval, const double* B, int ldb, int ncols, double* out,
+               int ldo);   // out[a, :ncols] = sum_{s in row a} Vval[s] B[col(s), :ncols]
+// precond.cu
+sdp_status precond_build_impl(sdp_problem* h);
+sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int prec);
+// pcg.cu
+sdp_status pcg_impl(sdp_problem* h, const double* r, double* y, double rtol, int maxit, int prec,
+                    int* iters, double* relres);
+// ipm.cu
+sdp_status ipm_alloc(sdp_problem* h);
+sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info);
+}  // namespace sdpgb

@@ -1,0 +1,279 @@
+// One iteration of the infeasible NT predictor-corrector around the PCG
+// Hessian solve, and sdp_solve.
+//
+// Per iteration (all FP64 on the device; the host reads a few scalars):
+//   residuals   Rp = b - A(X),  Rd = C - S - A^T y,  mu = X.S / n
+//   NT scaling  X = L L^T,  L^T S L = Q Lambda Q^T,  Gt = L Q,
+//               W = Gt Lambda^{-1/2} Gt^T (so W S W = X),  S^{-1} = Gt Lambda^{-1} Gt^T
+//   precond     sdp_precond_build (Algorithm 1 steps 1-2)
+//   Newton      H dy = Rp - A(Rc) + A(W Rd W)  (eq. hesseqn2), by PCG;
+//               dS = Rd - A^T dy,  dX = Rc - W dS W
+//   predictor   Rc = -X;  corrector Rc = sigma mu S^{-1} - X, sigma = (mu_aff / mu)^3
+//   step        alpha = min(1, step_frac / max(0, -lambda_min(L^{-1} dX L^{-T}))) per side.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+
+namespace sdpgb {
+
+enum { R_RP = 8, R_RD, R_CX, R_BY, R_XS, R_XDS, R_DXS, R_DXDS, R_LMIN };
+
+sdp_status ipm_alloc(sdp_problem* h) {
+  if (h->L) return SDP_OK;
+  const int n = h->n, m = h->m;
+  const size_t nn = (size_t)n * n;
+  SDP_TRY(h->allocT(&h->L, nn));
+  SDP_TRY(h->allocT(&h->Rs, nn));
+  if (!h->M1) SDP_TRY(h->allocT(&h->M1, nn));
+  SDP_TRY(h->allocT(&h->M2, nn));
+  SDP_TRY(h->allocT(&h->M3, nn));
+  SDP_TRY(h->allocT(&h->Gt, nn));
+  SDP_TRY(h->allocT(&h->Sinv, nn));
+  SDP_TRY(h->allocT(&h->Rd, nn));
+  SDP_TRY(h->allocT(&h->Rc, nn));
+  SDP_TRY(h->allocT(&h->dX, nn));
+  SDP_TRY(h->allocT(&h->dS, nn));
+  SDP_TRY(h->allocT(&h->E, nn));
+  SDP_TRY(h->allocT(&h->lam, n));
+  SDP_TRY(h->allocT(&h->Rp, m));
+  SDP_TRY(h->allocT(&h->rhs, m));
+  SDP_TRY(h->allocT(&h->dy, m));
+  if (!h->scal) SDP_TRY(h->allocT(&h->scal, 64));
+  if (!h->part) SDP_TRY(h->allocT(&h->part, dot_part_doubles()));
+  if (!h->info) SDP_TRY(h->allocT(&h->info, 8));
+  const size_t wneed = std::max(potrf_work_doubles(n), trsm_work_doubles(n, n));
+  if (wneed > h->work_doubles) {
+    SDP_TRY(h->allocT(&h->work, wneed));
+    h->work_doubles = wneed;
+  }
+  if (!h->eig_base) {
+    SDP_TRY(h->alloc(&h->eig_base, eig_work_bytes(n, true)));
+    eig_work_carve(&h->eig, h->eig_base, n, true);
+  }
+  return SDP_OK;
+}
+
+static sdp_status chol_checked(sdp_problem* h, const double* src, double* L, const char* what) {
+  const int n = h->n;
+  copy2d(h->stream, n, n, src, n, L, n);
+  potrf(h->stream, n, L, n, h->info, h->work);
+  int info = 0;
+  SDP_CK(h, cudaMemcpyAsync(&info, h->info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  SDP_CK(h, cudaStreamSynchronize(h->stream));
+  if (info) {
+    h->last_error = std::string(what) + ": not positive definite (pivot " + std::to_string(info - 1) + ")";
+    return SDP_ERR_NOT_PD;
+  }
+  return SDP_OK;
+}
+
+// Largest alpha with (Lf Lf^T) + alpha D psd, from lambda_min(Lf^{-1} D Lf^{-T}).
+static sdp_status max_step(sdp_problem* h, const double* Lf, const double* D, double* alpha) {
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  copy2d(st, n, n, D, n, h->M1, n);
+  trsm_left_lower(st, false, n, n, Lf, n, h->M1, n, h->work);   // Lf^{-1} D
+  transpose(st, n, n, h->M1, n, h->M2, n);                      // D Lf^{-T}
+  trsm_left_lower(st, false, n, n, Lf, n, h->M2, n, h->work);   // Lf^{-1} D Lf^{-T}
+  symmetrize_avg(st, n, h->M2, n);
+  SDP_TRY(eig_min(st, n, h->M2, h->scal + R_LMIN, &h->eig));
+  double lmin = 0.0;
+  SDP_CK(h, cudaMemcpyAsync(&lmin, h->scal + R_LMIN, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaStreamSynchronize(st));
+  if (eig_flag(st, &h->eig)) {
+    h->last_error = "step length: grid barrier timeout";
+    return SDP_ERR_TIMEOUT;
+  }
+  if (!std::isfinite(lmin)) {
+    h->last_error = "step length: non-finite eigenvalue";
+    return SDP_ERR_NUMERIC;
+  }
+  *alpha = (lmin >= 0.0) ? INFINITY : -1.0 / lmin;
+  return SDP_OK;
+}
+
+// dy from H dy = rhs0 - A(Rc); then dS, dX.  Returns PCG stats.
+static sdp_status newton(sdp_problem* h, const double* rhs0, int* its, double* relres) {
+  cudaStream_t st = h->stream;
+  const int n = h->n, m = h->m;
+  const size_t nn = (size_t)n * n;
+  op_A_dense(h, h->Rc, h->rhs, -1.0, rhs0, 1.0);
+  sdp_status s = pcg_impl(h, h->rhs, h->dy, h->prm.pcg_rtol, h->prm.pcg_maxit, h->prm.prec, its, relres);
+  if (s != SDP_OK && s != SDP_ERR_MAXIT) return s;
+  // dS = Rd - A^T dy
+  SDP_CK(h, cudaMemcpyAsync(h->dS, h->Rd, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  assemble_V(h, h->dy, nullptr, h->Vval);
+  scatter_V_dense(h, h->Vval, -1.0, h->dS);
+  // dX = Rc - W dS W
+  gemm(st, false, false, n, n, n, 1.0, h->W, n, h->dS, n, 0.0, h->M1, n);
+  gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->M2, n);
+  axpby(st, nn, 1.0, h->Rc, -1.0, h->M2, h->dX);
+  symmetrize_avg(st, n, h->dX, n);
+  (void)m;
+  return SDP_OK;
+}
+
+sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
+  SDP_TRY(ipm_alloc(h));
+  cudaStream_t st = h->stream;
+  const int n = h->n, m = h->m;
+  const size_t nn = (size_t)n * n;
+  double* sc = h->scal;
+  sdp_ipm_info inf{};
+  inf.iter = h->iter;
+
+  // ---- residuals and scalars
+  op_A_dense(h, h->X, h->Rp, -1.0, h->b, 1.0);
+  axpby(st, nn, 1.0, h->C, -1.0, h->S, h->Rd);
+  assemble_V(h, h->y, nullptr, h->Vval);
+  scatter_V_dense(h, h->Vval, -1.0, h->Rd);
+  dot(st, m, h->Rp, h->Rp, sc + R_RP, h->part);
+  dot(st, nn, h->Rd, h->Rd, sc + R_RD, h->part);
+  dot(st, nn, h->C, h->X, sc + R_CX, h->part);
+  dot(st, m, h->b, h->y, sc + R_BY, h->part);
+  dot(st, nn, h->X, h->S, sc + R_XS, h->part);
+  double v[5];
+  SDP_CK(h, cudaMemcpyAsync(v, sc + R_RP, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaStreamSynchronize(st));
+  const double cx = v[2], by = v[3], xs = v[4];
+  const double mu = xs / n;
+  inf.mu = mu;
+  inf.obj_p = cx;
+  inf.obj_d = by;
+  inf.relgap = std::fabs(cx - by) / (1.0 + std::fabs(cx) + std::fabs(by));
+  inf.pinf = std::sqrt(v[0]) / (1.0 + h->normb);
+  inf.dinf = std::sqrt(v[1]) / (1.0 + h->normC);
+  if (!std::isfinite(cx) || !std::isfinite(by) || !std::isfinite(xs)) {
+    h->last_error = "ipm_step: non-finite iterate";
+    if (info) *info = inf;
+    return SDP_ERR_NUMERIC;
+  }
+  if (inf.relgap <= h->prm.gap_tol && inf.pinf <= h->prm.infeas_tol && inf.dinf <= h->prm.infeas_tol) {
+    inf.converged = 1;
+    if (info) *info = inf;
+    return SDP_OK;
+  }
+
+  // ---- NT scaling
+  SDP_TRY(chol_checked(h, h->X, h->L, "ipm_step: chol(X)"));
+  gemm(st, false, false, n, n, n, 1.0, h->S, n, h->L, n, 0.0, h->M1, n);   // S L
+  gemm(st, true, false, n, n, n, 1.0, h->L, n, h->M1, n, 0.0, h->M2, n);   // L^T S L
+  symmetrize_avg(st, n, h->M2, n);
+  SDP_TRY(eig_full(st, n, h->M2, h->lam, h->E, &h->eig));
+  gemm(st, false, true, n, n, n, 1.0, h->L, n, h->E, n, 0.0, h->Gt, n);    // Gt = L Q, Q = E^T
+  scale_cols(st, n, n, h->Gt, n, h->lam, -0.5, h->M1, n);
+  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->W, n);
+  symmetrize_avg(st, n, h->W, n);
+  scale_cols(st, n, n, h->Gt, n, h->lam, -1.0, h->M1, n);
+  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->Sinv, n);
+  symmetrize_avg(st, n, h->Sinv, n);
+  double lam0 = 0.0;
+  SDP_CK(h, cudaMemcpyAsync(&lam0, h->lam, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaStreamSynchronize(st));
+  if (eig_flag(st, &h->eig)) {
+    h->last_error = "ipm_step: grid barrier timeout in the eigensolver";
+    return SDP_ERR_TIMEOUT;
+  }
+  if (!(lam0 > 0.0)) {
+    h->last_error = "ipm_step: L^T S L has a non-positive eigenvalue " + std::to_string(lam0);
+    return SDP_ERR_NUMERIC;
+  }
+  h->have_W = true;
+  h->W32_valid = h->W16_valid = false;
+  h->pc_valid = false;
+
+  // ---- preconditioner (Algorithm 1 steps 1-2)
+  SDP_TRY(precond_build_impl(h));
+  inf.tau = h->tau;
+  SDP_TRY(chol_checked(h, h->S, h->Rs, "ipm_step: chol(S)"));
+
+  // ---- common part of the right-hand side: Rp <- Rp + A(W Rd W)
+  gemm(st, false, false, n, n, n, 1.0, h->W, n, h->Rd, n, 0.0, h->M1, n);
+  gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->M3, n);
+  symmetrize_avg(st, n, h->M3, n);
+  op_A_dense(h, h->M3, h->Rp, 1.0, h->Rp, 1.0);   // Rp <- Rp + A(W Rd W)
+
+  // ---- predictor
+  axpby(st, nn, -1.0, h->X, 0.0, nullptr, h->Rc);
+  int its = 0;
+  double rr = 0.0;
+  SDP_TRY(newton(h, h->Rp, &its, &rr));
+  inf.pcg_iters_pred = its;
+  inf.pcg_relres_pred = rr;
+  double ap = 0.0, ad = 0.0;
+  SDP_TRY(max_step(h, h->L, h->dX, &ap));
+  SDP_TRY(max_step(h, h->Rs, h->dS, &ad));
+  ap = std::min(1.0, h->prm.step_frac * ap);
+  ad = std::min(1.0, h->prm.step_frac * ad);
+  dot(st, nn, h->X, h->dS, sc + R_XDS, h->part);
+  dot(st, nn, h->dX, h->S, sc + R_DXS, h->part);
+  dot(st, nn, h->dX, h->dS, sc + R_DXDS, h->part);
+  double w3[3];
+  SDP_CK(h, cudaMemcpyAsync(w3, sc + R_XDS, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaStreamSynchronize(st));
+  const double mu_aff = (xs + ad * w3[0] + ap * w3[1] + ap * ad * w3[2]) / n;
+  const double ratio = std::min(1.0, std::max(0.0, mu_aff / mu));
+  const double sigma = ratio * ratio * ratio;
+  inf.sigma = sigma;
+
+  // ---- corrector
+  axpby(st, nn, sigma * mu, h->Sinv, -1.0, h->X, h->Rc);
+  SDP_TRY(newton(h, h->Rp, &its, &rr));
+  inf.pcg_iters_corr = its;
+  inf.pcg_relres_corr = rr;
+  SDP_TRY(max_step(h, h->L, h->dX, &ap));
+  SDP_TRY(max_step(h, h->Rs, h->dS, &ad));
+  ap = std::min(1.0, h->prm.step_frac * ap);
+  ad = std::min(1.0, h->prm.step_frac * ad);
+  inf.alpha_p = ap;
+  inf.alpha_d = ad;
+
+  // ---- update
+  axpby(st, nn, 1.0, h->X, ap, h->dX, h->X);
+  axpby(st, m, 1.0, h->y, ad, h->dy, h->y);
+  axpby(st, nn, 1.0, h->S, ad, h->dS, h->S);
+  symmetrize_avg(st, n, h->X, n);
+  symmetrize_avg(st, n, h->S, n);
+  SDP_CK(h, cudaGetLastError());
+  h->iter++;
+  if (h->prm.verbose)
+    fprintf(stderr, "ipm %3d mu %.3e gap %.3e pinf %.3e dinf %.3e ap %.3f ad %.3f sig %.3e pcg %d/%d rel %.1e/%.1e\n",
+            inf.iter, inf.mu, inf.relgap, inf.pinf, inf.dinf, ap, ad, sigma, inf.pcg_iters_pred,
+            inf.pcg_iters_corr, inf.pcg_relres_pred, inf.pcg_relres_corr);
+  if (info) *info = inf;
+  return SDP_OK;
+}
+
+}  // namespace sdpgb
+
+extern "C" sdp_status sdp_solve(sdp_problem* h, sdp_result* res) {
+  if (!h) return SDP_ERR_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  sdp_result r{};
+  sdp_status s = SDP_OK;
+  int pcg_total = 0;
+  for (int it = 0; it <= h->prm.ipm_maxit; ++it) {
+    sdp_ipm_info inf{};
+    s = sdpgb::ipm_step_impl(h, &inf);
+    r.obj_p = inf.obj_p;
+    r.obj_d = inf.obj_d;
+    r.relgap = inf.relgap;
+    r.pinf = inf.pinf;
+    r.dinf = inf.dinf;
+    if (s != SDP_OK) break;
+    if (inf.converged) {
+      r.converged = 1;
+      break;
+    }
+    pcg_total += inf.pcg_iters_pred + inf.pcg_iters_corr;
+  }
+  r.iters = h->iter;
+  r.pcg_iters_total = pcg_total;
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (res) *res = r;
+  if (s == SDP_OK && !r.converged) return SDP_ERR_MAXIT;
+  return s;
+}

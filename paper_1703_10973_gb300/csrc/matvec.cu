@@ -1,0 +1,307 @@
+// The Hessian operator of eq. (hesseqn2), applied matrix-free:
+//   V  = sum_j v_j A_j          (gather over the CSR slots of the V pattern)
+//   T  = W V                    (sparse-times-dense: T[r, l] = sum_{s in row l} V_ls W[r, s])
+//   Hv_i = sum_{(p,q) in A_i} a_pq mult_pq W[p, :] . T[q, :]
+// because (W V W)_pq = sum_l W_pl (V W)_lq = W[p, :] . (W V)[q, :] (V, W symmetric).
+// T is produced row by row in its final layout, so no transpose is needed, and
+// the per-entry dot products read two contiguous rows.
+//
+// The same CSR machinery serves the IPM: A(X) (op_A_dense), A^T y scattered into
+// a dense matrix (scatter_V_dense) and sparse-times-dense products with U or Z.
+#include "internal.cuh"
+
+#include <algorithm>
+
+namespace sdpgb {
+
+static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+template <typename T> __device__ __forceinline__ float tof(T x);
+template <> __device__ __forceinline__ float tof<float>(float x) { return x; }
+template <> __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+__device__ __forceinline__ double wsum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float wsum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// K0: V values from v (gather form, no atomics)
+// ---------------------------------------------------------------------------
+__global__ void k_assemble(int nnzV, const int* __restrict__ sptr, const int* __restrict__ scon,
+                           const double* __restrict__ scoef, const double* __restrict__ v,
+                           const double* __restrict__ scale, double* __restrict__ Vval) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nnzV) return;
+  double acc = 0.0;
+  for (int c = sptr[s]; c < sptr[s + 1]; ++c) {
+    const int k = scon[c];
+    const double f = scale ? scale[k] : 1.0;
+    acc = fma(scoef[c] * f, v[k], acc);
+  }
+  Vval[s] = acc;
+}
+
+void assemble_V(sdp_problem* h, const double* v, const double* scale, double* Vval) {
+  count_launch();
+  k_assemble<<<cdiv(h->nnzV, 256), 256, 0, h->stream>>>(h->nnzV, h->sptr, h->scon, h->scoef, v, scale, Vval);
+}
+
+// ---------------------------------------------------------------------------
+// K1: T = W V, R rows of W per CTA staged in shared memory
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(256) k_spmm_wv_f64(int n, const int* __restrict__ rowptr,
+                                                     const int* __restrict__ colidx,
+                                                     const double* __restrict__ Vval,
+                                                     const double* __restrict__ W, double* __restrict__ T) {
+  extern __shared__ double wsh[];  // R x n
+  const int r0 = blockIdx.x * R;
+  for (int t = threadIdx.x; t < R * n; t += blockDim.x) {
+    const int rr = t / n, c = t % n;
+    wsh[t] = (r0 + rr < n) ? W[(size_t)(r0 + rr) * n + c] : 0.0;
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    double acc[R];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) acc[rr] = 0.0;
+    const int s1 = rowptr[l + 1];
+    for (int s = rowptr[l]; s < s1; ++s) {
+      const double val = Vval[s];
+      const int col = colidx[s];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc[rr] = fma(val, wsh[rr * n + col], acc[rr]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr)
+      if (r0 + rr < n) T[(size_t)(r0 + rr) * n + l] = acc[rr];
+  }
+}
+
+template <typename TW, int R>
+__global__ void __launch_bounds__(256) k_spmm_wv_lp(int n, const int* __restrict__ rowptr,
+                                                    const int* __restrict__ colidx,
+                                                    const double* __restrict__ Vval,
+                                                    const TW* __restrict__ W, float* __restrict__ T) {
+  extern __shared__ float fsh[];  // R x n
+  const int r0 = blockIdx.x * R;
+  for (int t = threadIdx.x; t < R * n; t += blockDim.x) {
+    const int rr = t / n, c = t % n;
+    fsh[t] = (r0 + rr < n) ? tof<TW>(W[(size_t)(r0 + rr) * n + c]) : 0.f;
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    float acc[R];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) acc[rr] = 0.f;
+    const int s1 = rowptr[l + 1];
+    for (int s = rowptr[l]; s < s1; ++s) {
+      const float val = (float)Vval[s];
+      const int col = colidx[s];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc[rr] = fmaf(val, fsh[rr * n + col], acc[rr]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr)
+      if (r0 + rr < n) T[(size_t)(r0 + rr) * n + l] = acc[rr];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: per-constraint gather of W[p,:] . T[q,:]
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sddmm_f64(int n, int m, const int* __restrict__ eptr,
+                                                   const int* __restrict__ ep, const int* __restrict__ eq,
+                                                   const double* __restrict__ ecoef,
+                                                   const double* __restrict__ W, const double* __restrict__ T,
+                                                   double* __restrict__ Hv) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  if (i >= m) return;
+  double acc = 0.0;
+  for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
+    const double* wp = W + (size_t)ep[e] * n;
+    const double* tq = T + (size_t)eq[e] * n;
+    double s = 0.0;
+    for (int l = lane; l < n; l += 32) s = fma(wp[l], tq[l], s);
+    acc = fma(ecoef[e], s, acc);
+  }
+  acc = wsum_d(acc);
+  if (lane == 0) Hv[i] = acc;
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(256) k_sddmm_lp(int n, int m, const int* __restrict__ eptr,
+                                                  const int* __restrict__ ep, const int* __restrict__ eq,
+                                                  const double* __restrict__ ecoef, const TW* __restrict__ W,
+                                                  const float* __restrict__ T, double* __restrict__ Hv) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  if (i >= m) return;
+  float acc = 0.f;
+  for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
+    const TW* wp = W + (size_t)ep[e] * n;
+    const float* tq = T + (size_t)eq[e] * n;
+    float s = 0.f;
+    for (int l = lane; l < n; l += 32) s = fmaf(tof<TW>(wp[l]), tq[l], s);
+    acc = fmaf((float)ecoef[e], s, acc);
+  }
+  acc = wsum_f(acc);
+  if (lane == 0) Hv[i] = (double)acc;
+}
+
+sdp_status ensure_lowprec_W(sdp_problem* h, int prec) {
+  const size_t nn = (size_t)h->n * h->n;
+  if (prec == SDP_FP32 || prec == SDP_BF16) {
+    if (!h->T32) SDP_TRY(h->allocT(&h->T32, nn));
+  }
+  if (prec == SDP_FP32 && !h->W32_valid) {
+    if (!h->W32) SDP_TRY(h->allocT(&h->W32, nn));
+    to_f32(h->stream, nn, h->W, h->W32);
+    h->W32_valid = true;
+  }
+  if (prec == SDP_BF16 && !h->W16_valid) {
+    if (!h->W16) SDP_TRY(h->allocT(&h->W16, nn));
+    to_bf16(h->stream, nn, h->W, h->W16);
+    h->W16_valid = true;
+  }
+  return SDP_OK;
+}
+
+static int rows_per_cta(int n, size_t elem) {
+  const size_t budget = 96 * 1024;
+  int r = (int)std::min<size_t>(8, budget / (elem * (size_t)n));
+  if (r >= 8) return 8;
+  if (r >= 4) return 4;
+  if (r >= 2) return 2;
+  return 1;
+}
+
+template <int R>
+static void launch_spmm_f64(sdp_problem* h, const double* Vval) {
+  const size_t smem = (size_t)R * h->n * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_spmm_wv_f64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  count_launch();
+  k_spmm_wv_f64<R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->colidx, Vval, h->W, h->T);
+}
+template <typename TW, int R>
+static void launch_spmm_lp(sdp_problem* h, const double* Vval, const TW* W) {
+  const size_t smem = (size_t)R * h->n * sizeof(float);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_spmm_wv_lp<TW, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  count_launch();
+  k_spmm_wv_lp<TW, R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->colidx, Vval, W, h->T32);
+}
+
+sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec) {
+  if (!h->have_W) {
+    h->last_error = "hessian_matvec: no scaling matrix W (call sdp_set_W or sdp_ipm_step)";
+    return SDP_ERR_ARG;
+  }
+  const int n = h->n;
+  const bool timed = ktimer_on("matvec");
+  if (timed) ktimer_begin(h->stream, "matvec");
+  assemble_V(h, v, nullptr, h->Vval);
+  if (prec == SDP_FP64) {
+    switch (rows_per_cta(n, sizeof(double))) {
+      case 8: launch_spmm_f64<8>(h, h->Vval); break;
+      case 4: launch_spmm_f64<4>(h, h->Vval); break;
+      case 2: launch_spmm_f64<2>(h, h->Vval); break;
+      default: launch_spmm_f64<1>(h, h->Vval); break;
+    }
+    count_launch();
+    k_sddmm_f64<<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(n, h->m, h->eptr, h->ep, h->eq, h->ecoef,
+                                                                     h->W, h->T, Hv);
+  } else if (prec == SDP_FP32) {
+    SDP_TRY(ensure_lowprec_W(h, prec));
+    switch (rows_per_cta(n, sizeof(float))) {
+      case 8: launch_spmm_lp<float, 8>(h, h->Vval, h->W32); break;
+      case 4: launch_spmm_lp<float, 4>(h, h->Vval, h->W32); break;
+      case 2: launch_spmm_lp<float, 2>(h, h->Vval, h->W32); break;
+      default: launch_spmm_lp<float, 1>(h, h->Vval, h->W32); break;
+    }
+    count_launch();
+    k_sddmm_lp<float><<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(n, h->m, h->eptr, h->ep, h->eq,
+                                                                           h->ecoef, h->W32, h->T32, Hv);
+  } else if (prec == SDP_BF16) {
+    SDP_TRY(ensure_lowprec_W(h, prec));
+    switch (rows_per_cta(n, sizeof(float))) {
+      case 8: launch_spmm_lp<__nv_bfloat16, 8>(h, h->Vval, h->W16); break;
+      case 4: launch_spmm_lp<__nv_bfloat16, 4>(h, h->Vval, h->W16); break;
+      case 2: launch_spmm_lp<__nv_bfloat16, 2>(h, h->Vval, h->W16); break;
+      default: launch_spmm_lp<__nv_bfloat16, 1>(h, h->Vval, h->W16); break;
+    }
+    count_launch();
+    k_sddmm_lp<__nv_bfloat16><<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(
+        n, h->m, h->eptr, h->ep, h->eq, h->ecoef, h->W16, h->T32, Hv);
+  } else {
+    h->last_error = "hessian_matvec: unknown precision";
+    return SDP_ERR_ARG;
+  }
+  if (timed) {
+    // algorithmic work: T = W V (2 nnzV n flops), one length-n dot per stored entry;
+    // bytes: W read for T, T written, W and T rows read by the gather (4 n^2 s) + sparse data
+    const double s = (prec == SDP_FP64) ? 8.0 : (prec == SDP_FP32 ? 4.0 : 3.0);
+    const double f = 2.0 * h->nnzV * (double)n + 2.0 * h->nent * (double)n;
+    const double by = 4.0 * s * n * (double)n + 12.0 * h->nnzV + 16.0 * h->m;
+    ktimer_end(h->stream, "matvec", f, by);
+  }
+  return SDP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sparse helpers for the IPM and the preconditioner
+// ---------------------------------------------------------------------------
+// out[i] = alpha * A_i . X + beta * add[i]   (X symmetric)
+__global__ void k_opA(int m, const int* __restrict__ eptr, const int* __restrict__ ep,
+                      const int* __restrict__ eq, const double* __restrict__ ecoef, int n,
+                      const double* __restrict__ X, double* __restrict__ out, double alpha,
+                      const double* __restrict__ add, double beta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int e = eptr[i]; e < eptr[i + 1]; ++e) s = fma(ecoef[e], X[(size_t)ep[e] * n + eq[e]], s);
+  out[i] = alpha * s + (add ? beta * add[i] : 0.0);
+}
+void op_A_dense(sdp_problem* h, const double* X, double* out, double alpha, const double* add, double beta) {
+  count_launch();
+  k_opA<<<cdiv(h->m, 256), 256, 0, h->stream>>>(h->m, h->eptr, h->ep, h->eq, h->ecoef, h->n, X, out, alpha,
+                                                add, beta);
+}
+
+// D[row][col] += alpha * Vval[s]  over every slot of the V pattern
+__global__ void k_scatter(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                          const double* __restrict__ Vval, double alpha, double* __restrict__ D) {
+  const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (r >= n) return;
+  for (int s = rowptr[r] + lane; s < rowptr[r + 1]; s += 32) D[(size_t)r * n + colidx[s]] += alpha * Vval[s];
+}
+void scatter_V_dense(sdp_problem* h, const double* Vval, double alpha, double* D) {
+  count_launch();
+  k_scatter<<<cdiv((size_t)h->n * 32, 256), 256, 0, h->stream>>>(h->n, h->rowptr, h->colidx, Vval, alpha, D);
+}
+
+// out[a, c] = sum_{s in row a} val[s] B[col(s), c]   (c < ncols)
+__global__ void k_spmm_rows(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                            const double* __restrict__ val, const double* __restrict__ B, int ldb, int ncols,
+                            double* __restrict__ out, int ldo) {
+  const int a = blockIdx.y;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = rowptr[a]; s < rowptr[a + 1]; ++s) acc = fma(val[s], B[(size_t)colidx[s] * ldb + c], acc);
+    out[(size_t)a * ldo + c] = acc;
+  }
+}
+void spmm_rows(sdp_problem* h, const double* Vval, const double* B, int ldb, int ncols, double* out, int ldo) {
+  count_launch();
+  const unsigned gx = std::max(1u, std::min(cdiv(ncols, 128), 64u));
+  k_spmm_rows<<<dim3(gx, h->n), 128, 0, h->stream>>>(h->n, h->rowptr, h->colidx, Vval, B, ldb, ncols, out, ldo);
+}
+
+}  // namespace sdpgb

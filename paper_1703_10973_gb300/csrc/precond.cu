@@ -1,0 +1,279 @@
+// The preconditioner of Section III (Algorithm 1 steps 1-2, eq. SMW2).
+//
+// Build, for the current scaling matrix W:
+//   tau = lambda_min(W);  U = V_l (Lambda_l - tau I)^{1/2}    (eq. Wsplit2)
+//   Z   = chol(2 W0 + U U^T) = chol(2 W - U U^T)             (eq. hessExp2)
+//   core S = tau^2 I + UU^T G^{-1} UU,  UU = A^T (U kron Z), G = A^T A diagonal
+// Block (l, l') of S (n x n, columns of UU ordered l*n + c) is
+//   tau^2 delta_ll' I + Z^T K_ll' Z,   K_ll' = sum_i g_i (A_i u_l)(A_i u_l')^T,
+// so the formation is a sparse K_ll' Z product followed by a dense Z^T (K Z)
+// GEMM per block -- k(k+1)/2 GEMMs of n^3 instead of an m x nk Gram matrix.
+// The core is factored L L^T = S and L^{-1} is formed once, so every apply
+// costs two triangular matrix-vector products instead of two dependent
+// triangular solves.
+//
+// Apply (eq. SMW2):  t = G^{-1} r;  u = UU^T t = Z^T (sum t_i A_i) U;
+//   s = L^{-T} L^{-1} u;  z = tau^{-2} G^{-1} (r - UU s),  (UU s)_i = A_i . (Z S U^T).
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace sdpgb {
+
+static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// U[a][l] = Etop[l][a] * sqrt(max(wtop[l] - tau, 0))
+__global__ void k_make_U(int n, int k, const double* __restrict__ Etop, const double* __restrict__ wtop,
+                         const double* __restrict__ tau_dev, double* __restrict__ U) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int a = t / k, l = t % k;
+  const double s = sqrt(fmax(wtop[l] - tau_dev[0], 0.0));
+  U[t] = Etop[(size_t)l * n + a] * s;
+}
+
+// au[cr][l] = (A_i u_l)[row(cr)] = sum_{(b, coef) in row(cr) of A_i} coef U[b][l]
+__global__ void k_au(int ncr, int k, const int* __restrict__ clptr, const int* __restrict__ clcol,
+                     const double* __restrict__ clcoef, const double* __restrict__ U, double* __restrict__ au) {
+  const int cr = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cr >= ncr) return;
+  for (int l = 0; l < k; ++l) {
+    double s = 0.0;
+    for (int t = clptr[cr]; t < clptr[cr + 1]; ++t) s = fma(clcoef[t], U[(size_t)clcol[t] * k + l], s);
+    au[(size_t)cr * k + l] = s;
+  }
+}
+
+// Kval[s] = sum_{(i, cra, crb) in slot s} g_i au[cra][l] au[crb][l2]
+__global__ void k_kvals(int nnzK, const int* __restrict__ kptr, const int* __restrict__ kcon,
+                        const int* __restrict__ kcra, const int* __restrict__ kcrb, const double* __restrict__ ginv,
+                        const double* __restrict__ au, int k, int l, int l2, double* __restrict__ Kval) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nnzK) return;
+  double acc = 0.0;
+  for (int t = kptr[s]; t < kptr[s + 1]; ++t)
+    acc = fma(ginv[kcon[t]] * au[(size_t)kcra[t] * k + l], au[(size_t)kcrb[t] * k + l2], acc);
+  Kval[s] = acc;
+}
+
+// out[a, c] = sum_{s in row a} val[s] B[col(s), c]   (generic CSR)
+__global__ void k_csr_mm(int rows, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                         const double* __restrict__ val, const double* __restrict__ B, int ldb, int ncols,
+                         double* __restrict__ out, int ldo) {
+  const int a = blockIdx.y;
+  if (a >= rows) return;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = rowptr[a]; s < rowptr[a + 1]; ++s) acc = fma(val[s], B[(size_t)colidx[s] * ldb + c], acc);
+    out[(size_t)a * ldo + c] = acc;
+  }
+}
+
+// z_i = (ginv_i / tau^2) (r_i - (UU s)_i),  (UU s)_i = A_i . (ZS U^T)
+__global__ void k_apply_tail(int m, int k, const int* __restrict__ eptr, const int* __restrict__ ep,
+                             const int* __restrict__ eq, const double* __restrict__ ecoef,
+                             const double* __restrict__ ZS, const double* __restrict__ U,
+                             const double* __restrict__ ginv, const double* __restrict__ r, double inv_tau2,
+                             double* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double us = 0.0;
+  for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
+    const int p = ep[e], q = eq[e];
+    double s = 0.0;
+    if (p == q) {
+      for (int l = 0; l < k; ++l) s = fma(ZS[(size_t)p * k + l], U[(size_t)p * k + l], s);
+      us = fma(ecoef[e], s, us);
+    } else {
+      for (int l = 0; l < k; ++l) {
+        s = fma(ZS[(size_t)p * k + l], U[(size_t)q * k + l], s);
+        s = fma(ZS[(size_t)q * k + l], U[(size_t)p * k + l], s);
+      }
+      us = fma(0.5 * ecoef[e], s, us);
+    }
+  }
+  z[i] = ginv[i] * inv_tau2 * (r[i] - us);
+}
+
+__global__ void k_scale_ginv(int m, const double* __restrict__ ginv, const double* __restrict__ r, double s,
+                             double* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) z[i] = ginv[i] * s * r[i];
+}
+
+static sdp_status precond_alloc(sdp_problem* h) {
+  if (h->U) return SDP_OK;
+  const int n = h->n, k = std::max(h->k, 1);
+  const size_t nk = (size_t)n * k;
+  SDP_TRY(h->allocT(&h->U, nk));
+  SDP_TRY(h->allocT(&h->Z, (size_t)n * n));
+  SDP_TRY(h->allocT(&h->Sc, nk * nk));
+  SDP_TRY(h->allocT(&h->Linv, nk * nk));
+  SDP_TRY(h->allocT(&h->tau_dev, 8));
+  SDP_TRY(h->allocT(&h->wtop, 32));
+  SDP_TRY(h->allocT(&h->Etop, (size_t)32 * n));
+  SDP_TRY(h->allocT(&h->au, (size_t)std::max(h->ncr, 1) * k));
+  SDP_TRY(h->allocT(&h->Kval, std::max(h->nnzK, 1)));
+  SDP_TRY(h->allocT(&h->KZ, (size_t)n * n));
+  SDP_TRY(h->allocT(&h->Bn, nk));
+  SDP_TRY(h->allocT(&h->uvec, nk));
+  SDP_TRY(h->allocT(&h->uvec2, nk));
+  SDP_TRY(h->allocT(&h->pvec, std::max<size_t>(nk, (size_t)h->nnzV)));
+  SDP_TRY(h->allocT(&h->trpart, trmv_part_doubles((int)nk)));
+  SDP_TRY(h->allocT(&h->info, 8));
+  const size_t wneed = std::max(std::max(potrf_work_doubles((int)nk), trsm_work_doubles((int)nk, (int)nk)),
+                                std::max(potrf_work_doubles(n), trsm_work_doubles(n, n)));
+  if (wneed > h->work_doubles) {
+    SDP_TRY(h->allocT(&h->work, wneed));
+    h->work_doubles = wneed;
+  }
+  if (!h->M1) SDP_TRY(h->allocT(&h->M1, (size_t)n * n));
+  if (!h->eig_base) {
+    SDP_TRY(h->alloc(&h->eig_base, eig_work_bytes(n, true)));
+    eig_work_carve(&h->eig, h->eig_base, n, true);
+  }
+  return SDP_OK;
+}
+
+static sdp_status read_info(sdp_problem* h, const char* what) {
+  int info = 0;
+  SDP_CK(h, cudaMemcpyAsync(&info, h->info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  SDP_CK(h, cudaStreamSynchronize(h->stream));
+  if (info != 0) {
+    h->last_error = std::string(what) + ": non-positive pivot at " + std::to_string(info - 1);
+    return SDP_ERR_NOT_PD;
+  }
+  return SDP_OK;
+}
+
+// Sc = Z^T K_ll' Z block by block, plus shift on the diagonal.
+static void form_core(sdp_problem* h, int k, double shift) {
+  cudaStream_t st = h->stream;
+  const int n = h->n, nk = n * k;
+  for (int l = 0; l < k; ++l) {
+    for (int l2 = l; l2 < k; ++l2) {
+      count_launch(2);
+      k_kvals<<<cdiv(h->nnzK, 256), 256, 0, st>>>(h->nnzK, h->kptr, h->kcon, h->kcra, h->kcrb, h->ginv, h->au,
+                                                 k, l, l2, h->Kval);
+      const unsigned gx = std::max(1u, std::min(cdiv(n, 128), 64u));
+      k_csr_mm<<<dim3(gx, n), 128, 0, st>>>(n, h->krowptr, h->kcol, h->Kval, h->Z, n, n, h->KZ, n);
+      double* blk = h->Sc + (size_t)l * n * nk + (size_t)l2 * n;
+      gemm(st, true, false, n, n, n, 1.0, h->Z, n, h->KZ, n, 0.0, blk, nk);
+      if (l2 != l) transpose(st, n, n, blk, nk, h->Sc + (size_t)l2 * n * nk + (size_t)l * n, nk);
+    }
+  }
+  if (shift != 0.0) add_diag(st, nk, h->Sc, nk, shift);
+}
+
+__global__ void k_max_diag(int n, const double* A, int lda, double* out) {
+  __shared__ double sh[256];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v = fmax(v, fabs(A[(size_t)i * lda + i]));
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+static sdp_status max_diag(sdp_problem* h, const double* A, int n, double* out) {
+  count_launch();
+  k_max_diag<<<1, 256, 0, h->stream>>>(n, A, n, h->tau_dev + 4);
+  SDP_CK(h, cudaMemcpyAsync(out, h->tau_dev + 4, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  SDP_CK(h, cudaStreamSynchronize(h->stream));
+  return SDP_OK;
+}
+
+sdp_status precond_build_impl(sdp_problem* h) {
+  SDP_TRY(precond_alloc(h));
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  const int k = (h->prm.precond == SDP_PRECOND_DIAG) ? 0 : std::min(h->k, n - 1 > 0 ? n - 1 : 0);
+  const int nk = n * k;
+  // ---- step 1a: eigenvalues of W (smallest and top k with vectors)
+  copy2d(st, n, n, h->W, n, h->M1, n);
+  SDP_TRY(eig_extremes(st, n, h->M1, k, h->tau_dev, h->wtop, h->Etop, &h->eig));
+  double tau = 0.0;
+  SDP_CK(h, cudaMemcpyAsync(&tau, h->tau_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaStreamSynchronize(st));
+  if (eig_flag(st, &h->eig)) {
+    h->last_error = "precond_build: grid barrier timeout in the tridiagonalisation";
+    return SDP_ERR_TIMEOUT;
+  }
+  if (!(tau > 0.0) || !std::isfinite(tau)) {
+    h->last_error = "precond_build: lambda_min(W) = " + std::to_string(tau) + " is not positive";
+    return SDP_ERR_NUMERIC;
+  }
+  h->tau = tau;
+  h->kpc = k;
+  if (k == 0) {
+    h->pc_valid = true;
+    return SDP_OK;
+  }
+  // ---- step 1b: U and Z = chol(2W - U U^T)
+  count_launch();
+  k_make_U<<<cdiv((size_t)n * k, 256), 256, 0, st>>>(n, k, h->Etop, h->wtop, h->tau_dev, h->U);
+  axpby(st, (size_t)n * n, 2.0, h->W, 0.0, nullptr, h->Z);
+  gemm(st, false, true, n, n, k, -1.0, h->U, k, h->U, k, 1.0, h->Z, n);
+  potrf(st, n, h->Z, n, h->info, h->work);
+  SDP_TRY(read_info(h, "precond_build: chol(2 W0 + U U^T)"));
+  // ---- step 2: core S = tau^2 I + Z^T K Z (block l, l'), Cholesky, inverse
+  count_launch();
+  k_au<<<cdiv(h->ncr, 256), 256, 0, st>>>(h->ncr, k, h->crlist_ptr, h->crlist_col, h->crlist_coef, h->U, h->au);
+  // When nk > m (or near the optimum) UU^T G^{-1} UU is singular or nearly so and
+  // the core's smallest eigenvalue is tau^2 itself; if the FP64 Cholesky then
+  // meets a non-positive pivot, the core is rebuilt with tau^2 + delta on the
+  // diagonal.  S + delta I is the Woodbury core of tau^2 G + c UU UU^T with
+  // c = tau^2 / (tau^2 + delta) < 1, still a symmetric positive definite
+  // preconditioner, so PCG still converges to the exact Newton direction.
+  double shift = tau * tau;
+  sdp_status fs = SDP_OK;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    form_core(h, k, shift);
+    potrf(st, nk, h->Sc, nk, h->info, h->work);
+    fs = read_info(h, "precond_build: chol(core)");
+    if (fs == SDP_OK) break;
+    if (fs != SDP_ERR_NOT_PD) return fs;
+    form_core(h, k, 0.0);
+    double dmax = 0.0;
+    SDP_TRY(max_diag(h, h->Sc, nk, &dmax));
+    shift = std::max(shift * 100.0, tau * tau + 1e-14 * dmax * std::pow(100.0, attempt));
+  }
+  SDP_TRY(fs);
+  h->core_shift = shift;
+  fill(st, h->Linv, (size_t)nk * nk, 0.0);
+  add_diag(st, nk, h->Linv, nk, 1.0);
+  trsm_left_lower(st, false, nk, nk, h->Sc, nk, h->Linv, nk, h->work);
+  h->pc_valid = true;
+  return SDP_OK;
+}
+
+sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int prec) {
+  (void)prec;  // the apply runs in FP64; reduced precision is confined to the matvec
+  cudaStream_t st = h->stream;
+  const int n = h->n, m = h->m, k = h->kpc, nk = n * k;
+  const double inv_tau2 = 1.0 / (h->tau * h->tau);
+  if (k == 0) {
+    count_launch();
+    k_scale_ginv<<<cdiv(m, 256), 256, 0, st>>>(m, h->ginv, r, inv_tau2, z);
+    return SDP_OK;
+  }
+  // u = Z^T (sum g_i r_i A_i) U, stored as k x n (row l = column l of u)
+  assemble_V(h, r, h->ginv, h->pvec);
+  spmm_rows(h, h->pvec, h->U, k, k, h->Bn, k);
+  gemm(st, true, false, k, n, n, 1.0, h->Bn, k, h->Z, n, 0.0, h->uvec, n);
+  // s = L^{-T} L^{-1} u
+  trmv_lower(st, false, nk, h->Linv, nk, h->uvec, h->uvec2, h->trpart);
+  trmv_lower(st, true, nk, h->Linv, nk, h->uvec2, h->uvec, h->trpart);
+  // ZS = Z S_mat with S_mat[c][l] = s[l n + c]
+  gemm(st, false, true, n, k, n, 1.0, h->Z, n, h->uvec, n, 0.0, h->Bn, k);
+  count_launch();
+  k_apply_tail<<<cdiv(m, 256), 256, 0, st>>>(m, k, h->eptr, h->ep, h->eq, h->ecoef, h->Bn, h->U, h->ginv, r,
+                                             inv_tau2, z);
+  return SDP_OK;
+}
+
+}  // namespace sdpgb

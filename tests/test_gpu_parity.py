@@ -1,0 +1,276 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every input is seeded and synthetic; expected values come from ``oracle/`` run
+on the same inputs.  Tolerances: FP64 matvec 1e-12 relative (2-norm);
+preconditioner apply 1e-9; PCG to the requested true residual; the IPM end
+point within 1e-6 relative objective error and 1e-5 relative Frobenius error
+of the recovered matrix.
+"""
+import numpy as np
+import pytest
+
+import sdp_inputs as si
+from oracle import sdp_oracle as o
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_10973_gb300 import _build, load
+    _build.build()
+    load()
+
+
+def _prob(d, **kw):
+    from paper_1703_10973_gb300 import SDPProblem, default_params
+    return SDPProblem.from_data(d, params=default_params(**kw))
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def _ipm_like_W(n, k, mu, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.concatenate([rng.uniform(1.0, 3.0, n - k), rng.uniform(1.0, 2.0, k) / mu])
+    return (Q * ev) @ Q.T
+
+
+# --------------------------------------------------------------------------
+# hessian_matvec
+# --------------------------------------------------------------------------
+
+MATVEC_CASES = {
+    "mc_tiny": lambda: si.mc_instance(5, 7, 1, 20, 3),
+    "mc_C1": lambda: si.config_instance("C1"),
+    "mc_ragged": lambda: si.mc_instance(37, 61, 2, 900, 5),   # n = 98: ragged tails everywhere
+    "general": lambda: si.random_general(23, 40, 3, 2),
+    "diag": lambda: si.diag_constraint_instance(17, 1),
+    "unit_diag": lambda: si.unit_diag_instance(9),
+}
+
+
+@pytest.mark.parametrize("case", sorted(MATVEC_CASES))
+def test_matvec_fp64_matches_oracle(case):
+    d = MATVEC_CASES[case]()
+    P = o.Problem.from_data(d)
+    W = _ipm_like_W(d.n, min(2, d.n - 1), 1e-3, 11)
+    with _prob(d) as prob:
+        prob.set_W(_dev(W))
+        for seed in (1, 2):
+            v = si.random_vec(d.m, seed)
+            hv = prob.hessian_matvec(_dev(v)).cpu().numpy()
+            assert _rel(hv, o.hessian_matvec(P, W, v)) <= 1e-12
+
+
+def test_matvec_fp64_C2_full_size():
+    """Full C2 size (n = 1000, m = 8000) with W from a real oracle NT scaling."""
+    d = si.config_instance("C2")
+    P = o.Problem.from_data(d)
+    X = si.random_spd(d.n, 5, cond=1e4)
+    S = si.random_spd(d.n, 6, cond=1e4)
+    W = o.nt_scaling(X, S)
+    v = si.random_vec(d.m, 9)
+    with _prob(d) as prob:
+        prob.set_W(_dev(W))
+        hv = prob.hessian_matvec(_dev(v)).cpu().numpy()
+    assert _rel(hv, o.hessian_matvec(P, W, v)) <= 1e-12
+
+
+def test_matvec_explicit_hessian_columns():
+    """H e_j from the GPU equals column j of the explicit Hessian (closed form)."""
+    d = si.mc_instance(6, 8, 2, 30, 4)
+    P = o.Problem.from_data(d)
+    W = si.random_spd(d.n, 2, cond=50.0)
+    H = o.hessian_entries(P, W)
+    with _prob(d) as prob:
+        prob.set_W(_dev(W))
+        E = np.eye(d.m)
+        for j in (0, 7, d.m - 1):
+            col = prob.hessian_matvec(_dev(E[:, j])).cpu().numpy()
+            assert _rel(col, H[:, j]) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("bf16", 2e-2)])
+def test_matvec_reduced_precision(prec, tol):
+    d = si.mc_instance(40, 50, 2, 700, 8)
+    P = o.Problem.from_data(d)
+    W = si.random_spd(d.n, 3, cond=30.0)
+    v = si.random_vec(d.m, 1)
+    with _prob(d) as prob:
+        prob.set_W(_dev(W))
+        hv = prob.hessian_matvec(_dev(v), prec=prec).cpu().numpy()
+    assert _rel(hv, o.hessian_matvec(P, W, v)) <= tol
+
+
+# --------------------------------------------------------------------------
+# preconditioner
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mu", [1e-1, 1e-4, 1e-7])
+def test_precond_apply_matches_dense_inverse(mu):
+    """eq. (SMW2) on the GPU equals the oracle's dense solve with eq. (AtIUUtAt)."""
+    d = si.mc_instance(9, 11, 2, 60, 6)
+    P = o.Problem.from_data(d)
+    W = _ipm_like_W(d.n, 2, mu, 3)
+    pc = o.precond_build(P, W, 2)
+    Ht = o.precond_dense(P, pc)
+    r = si.random_vec(d.m, 2)
+    zref = np.linalg.solve(Ht, r)
+    with _prob(d) as prob:
+        prob.set_W(_dev(W))
+        prob.precond_build()
+        tau, k = prob.precond_info()
+        z = prob.precond_apply(_dev(r)).cpu().numpy()
+    assert k == 2
+    assert abs(tau - pc.tau) <= 1e-10 * abs(pc.tau) + 1e-14 * np.abs(W).max()
+    # eq. (SMW2) is forward-accurate to about kappa(Ht) eps (the instability the
+    # paper discusses in Section IV); the oracle's own SMW apply shows the same gap.
+    kap = np.linalg.cond(Ht)
+    tol = max(1e-12, 20.0 * kap * np.finfo(float).eps)
+    assert _rel(z, zref) <= tol
+    assert _rel(z, o.precond_apply(P, pc, r)) <= tol
+
+
+def test_precond_general_constraints():
+    d = si.random_general(14, 20, 2, 7)
+    P = o.Problem.from_data(d)
+    W = _ipm_like_W(d.n, 2, 1e-3, 5)
+    pc = o.precond_build(P, W, 2)
+    r = si.random_vec(d.m, 3)
+    with _prob(d) as prob:
+        prob.set_W(_dev(W))
+        prob.precond_build()
+        z = prob.precond_apply(_dev(r)).cpu().numpy()
+    assert _rel(z, o.precond_apply(P, pc, r)) <= 1e-9
+
+
+def test_precond_exact_for_low_rank_W():
+    """W = tau I + U U^T makes Ht = H: PCG converges in one iteration on the GPU."""
+    d = si.mc_instance(10, 10, 2, 50, 9)
+    rng = np.random.default_rng(5)
+    U0 = rng.standard_normal((d.n, 2)) * 3.0
+    W = 0.8 * np.eye(d.n) + U0 @ U0.T
+    r = si.random_vec(d.m, 3)
+    with _prob(d) as prob:
+        prob.set_W(_dev(W))
+        prob.precond_build()
+        y, its, rel, st = prob.pcg_solve(_dev(r), rtol=1e-10, maxit=50)
+    assert its == 1 and rel <= 1e-9
+
+
+# --------------------------------------------------------------------------
+# PCG
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mu", [1e-2, 1e-5])
+def test_pcg_matches_direct_solve(mu):
+    d = si.mc_instance(12, 14, 2, 100, 10)
+    P = o.Problem.from_data(d)
+    W = _ipm_like_W(d.n, 2, mu, 4)
+    H = o.hessian_entries(P, W)
+    # right-hand side with a solution of unit size, as for a Newton step
+    ystar = si.random_vec(d.m, 5)
+    ystar /= np.linalg.norm(ystar)
+    r = H @ ystar
+    with _prob(d) as prob:
+        prob.set_W(_dev(W))
+        prob.precond_build()
+        y, its, rel, st = prob.pcg_solve(_dev(r), rtol=1e-10, maxit=500)
+    y = y.cpu().numpy()
+    assert rel <= 1e-10
+    assert np.linalg.norm(H @ y - r) <= 1e-9 * np.linalg.norm(r)
+    assert _rel(y, ystar) <= 1e-10 * np.linalg.cond(H)
+    # the preconditioned iteration count stays small and independent of mu (Lemma Htilde)
+    assert its <= 60
+
+
+@pytest.mark.parametrize("prec,mu", [("fp32", 1e-3), ("bf16", 1e-1)])
+def test_pcg_reduced_precision_refined_to_fp64(prec, mu):
+    d = si.mc_instance(12, 14, 2, 100, 10)
+    P = o.Problem.from_data(d)
+    W = _ipm_like_W(d.n, 2, mu, 4)
+    H = o.hessian_entries(P, W)
+    r = si.random_vec(d.m, 5)
+    with _prob(d) as prob:
+        prob.set_W(_dev(W))
+        prob.precond_build()
+        y, its, rel, st = prob.pcg_solve(_dev(r), rtol=1e-8, maxit=2000, prec=prec)
+    y = y.cpu().numpy()
+    assert rel <= 1e-8
+    assert np.linalg.norm(H @ y - r) <= 1.01e-8 * np.linalg.norm(r)
+
+
+# --------------------------------------------------------------------------
+# interior-point method
+# --------------------------------------------------------------------------
+
+def test_first_ipm_step_matches_oracle():
+    """Same rules on both sides: after one step the iterates agree to PCG accuracy."""
+    d = si.config_instance("C1")
+    P = o.Problem.from_data(d)
+    ref = o.ipm_solve(P, o.IPMParams(maxit=1))
+    with _prob(d) as prob:
+        info = prob.ipm_step()
+        X, y, S = prob.get_solution()
+    assert abs(info["alpha_p"] - ref.log[0]["alpha_p"]) <= 1e-6
+    assert abs(info["alpha_d"] - ref.log[0]["alpha_d"]) <= 1e-6
+    assert _rel(X, ref.X) <= 1e-6 and _rel(S, ref.S) <= 1e-6 and _rel(y, ref.y) <= 1e-6
+
+
+def test_solve_C1_matches_oracle_and_recovers_M():
+    d = si.config_instance("C1")
+    P = o.Problem.from_data(d)
+    ref = o.ipm_solve(P)
+    with _prob(d) as prob:
+        res = prob.solve()
+        X, y, S = prob.get_solution()
+    assert res["converged"] and res["relgap"] <= 1e-6
+    assert abs(res["obj_p"] - ref.obj_p) <= 1e-6 * abs(ref.obj_p)
+    Z = o.mc_recovered(P, X)
+    assert _rel(Z, o.mc_recovered(P, ref.X)) <= 1e-5
+    assert _rel(Z, d.meta["M"]) <= 1e-5
+    cert = o.kkt_certificate(P, X, y, S)
+    assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6
+
+
+def test_solve_unit_diagonal_closed_form():
+    d = si.unit_diag_instance(12)
+    with _prob(d) as prob:
+        res = prob.solve()
+        X, y, S = prob.get_solution()
+    assert res["converged"]
+    assert np.abs(X - np.eye(12)).max() <= 1e-5
+    assert np.abs(y - 1.0).max() <= 1e-5
+
+
+def test_solve_maxcut_bipartite_closed_form():
+    d = si.maxcut_bipartite_instance(5, 6, 3, extra_edges=8)
+    with _prob(d, gap_tol=1e-8, infeas_tol=1e-8) as prob:
+        res = prob.solve()
+        X, _, _ = prob.get_solution()
+    z = d.meta["z"]
+    assert abs(res["obj_p"] + 2 * d.meta["n_edges"]) <= 1e-5 * 2 * d.meta["n_edges"]
+    assert np.abs(X - np.outer(z, z)).max() <= 1e-3
+
+
+def test_solve_general_sparse_kkt():
+    d = si.random_general(16, 24, 2, 21)
+    P = o.Problem.from_data(d)
+    ref = o.ipm_solve(P)
+    with _prob(d) as prob:
+        res = prob.solve()
+        X, y, S = prob.get_solution()
+    assert res["converged"]
+    assert abs(res["obj_p"] - ref.obj_p) <= 1e-6 * (1 + abs(ref.obj_p))
+    cert = o.kkt_certificate(P, X, y, S)
+    assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6 and cert["relgap"] <= 1e-6
