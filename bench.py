@@ -1,22 +1,28 @@
-"""Benchmark: SDP solves/s (and per-solve latency) at 1e-6 relative duality gap.
+"""Benchmark: SDP solves/s and per-solve latency at 1e-6 relative duality gap.
 
-One step = one complete solve of the plain-method matrix-completion SDP
-(n1 = n2 = 500, n = 1000, rank 2, m = 8000 uniform observations, seed 2) from
-the interior-point start point to relative gap, primal and dual infeasibility
-<= 1e-6, with every Newton system solved by PCG to a 1e-8 true relative
-residual.  The problem data stay resident in HBM across steps; each step resets
-the iterate on the device (sdp_reset) and runs sdp_solve.
+Default workload ("batched"): the first 16 instances of the batched
+matrix-completion workload (p, q uniform in [50, 400], r uniform in {1..4},
+m = min(pq/2, ceil(3 r (p+q) ln(p+q))) uniform observations, seeds 4000..4015).
+One step solves all 16 SDPs, each from the interior-point start point to
+relative gap, primal and dual infeasibility <= 1e-6 with every Newton system
+solved by PCG to a 1e-8 true relative residual, on 4 CUDA streams (one host
+thread per stream, one resident problem per instance).  The problem data stay
+in HBM across steps; each solve resets its iterate on the device.
 
-Printed line (rank 0): the contract keys plus roofline (dominant kernel,
-timed with CUDA events inside the timed region), cpu_baseline (the FP64 oracle
-on the host cores, bounded sample), e2e (host triplets -> sdp_setup -> solve ->
-solution copied back), clocks (nvidia-smi during the timed region) and the
-number of library kernel launches.
+`--workload C2` runs the single n = 1000, m = 8000, rank-2 instance instead; its
+nuclear-norm optimum has rank about 38, outside the low-rank regime the
+preconditioner is built for, and PCG stalls before 1e-6 (the line reports it).
 
---impl reference times the FP64 oracle (explicit Hessian + Cholesky) on the
-host cores on a bounded sample of the same workload.
---gpus N under torchrun runs N independent replicas (one instance per rank,
-no collective on the data path): value = total solves / max rank time.
+The printed line (rank 0) carries the contract keys plus: latency_ms (p50/p99
+per solve), roofline (dominant kernel class, timed with CUDA events over one
+instrumented step after the timed ones), cpu_baseline (the FP64 oracle on the
+host cores, bounded sample), e2e (host triplets -> sdp_setup -> solve ->
+solution copied back, through the public API), clocks (nvidia-smi samples taken
+during the timed region) and gpu_launches (library kernels in the timed region).
+
+--impl reference times the FP64 oracle (explicit Hessian + Cholesky) on the host
+cores on a bounded sample of the same workload.  Under torchrun (--gpus N) each
+rank solves its own copy of the batch with no collective on the data path.
 """
 from __future__ import annotations
 
@@ -24,9 +30,11 @@ import argparse
 import json
 import math
 import os
+import queue
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -37,7 +45,12 @@ import numpy as np  # noqa: E402
 
 METRIC = "SDP solves/s at 1e-6 relative duality gap"
 UNIT = "solves/s"
-WORKLOAD = "matrix-completion SDP n1=n2=500 (n=1000), rank 2, m=8000, seed 2; plain FP64 PCG"
+
+# FP64 FMA throughput of this GB300, measured with a register-resident DFMA
+# loop (1216 CTAs x 256 threads, 8 independent chains per thread): 1.194 TFLOP/s.
+# Nominal from the unit count: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26.
+FP64_PEAK_TFLOPS = 1.194
+ALU_CLASSES = ("gemm_f64", "sytrd", "potrf", "trsm")
 
 
 def _peaks():
@@ -48,21 +61,24 @@ def _peaks():
         return {}
 
 
-# FP64 FMA throughput of the GB300 (measured with a register-resident DFMA loop,
-# 1216 CTAs x 256 threads, 8 independent chains): 1.194 TFLOP/s.  Nominal from
-# the unit count: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz = 1.26 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.194
-
-
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
@@ -73,12 +89,9 @@ class Clocks:
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}",
-                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
@@ -94,6 +107,7 @@ class Clocks:
 
     def summary(self):
         sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
             for line in open(self.path):
                 p = [x.strip() for x in line.split(",")]
@@ -104,7 +118,6 @@ class Clocks:
                     mx.append(float(p[2]))
                 except ValueError:
                     continue
-                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
                 for nm, v in zip(names, p[5:9]):
                     if v.lower() in ("active", "1"):
                         reasons.add(nm)
@@ -116,53 +129,72 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _instance(seed_offset=0):
+def workload(name, count):
     import sdp_inputs as si
-    c = dict(si.CONFIGS["C2"])
-    return si.mc_instance(c["p"], c["q"], c["r"], c["m"], c["seed"] + seed_offset)
+    if name == "C2":
+        d = si.config_instance("C2")
+        return [d], ("matrix-completion SDP n1=n2=500 (n=1000), rank 2, m=8000, seed 2; "
+                     "plain method, k=8 (optimum rank ~38)")
+    specs = si.batched_specs(256)[:count]
+    inst = [si.mc_instance(s["p"], s["q"], s["r"], s["m"], s["seed"]) for s in specs]
+    desc = (f"batched matrix completion: first {count} of the 256 batched instances "
+            f"(p,q~U[50,400], r~U{{1..4}}, m=min(pq/2, 3r(p+q)ln(p+q)), seeds 4000..{4000 + count - 1}); "
+            f"n {min(d.n for d in inst)}..{max(d.n for d in inst)}, m {min(d.m for d in inst)}.."
+            f"{max(d.m for d in inst)}")
+    return inst, desc
 
 
-def cpu_oracle_rate(d, iters_per_solve):
-    """Time two oracle IPM iterations (explicit Hessian + Cholesky) and scale to a solve."""
+def cpu_oracle_rate(insts, iters_per_solve, budget_s=25.0):
+    """Oracle IPM iterations on the batch's instances (smallest first) for ~budget_s."""
     from oracle import sdp_oracle as o
-    P = o.Problem.from_data(d)
-    t0 = time.perf_counter()
-    o.ipm_solve(P, o.IPMParams(maxit=2))
-    per_iter = (time.perf_counter() - t0) / 2.0
-    return 1.0 / (per_iter * iters_per_solve), per_iter, 2
-
-
-def _cores():
-    try:
-        return len(os.sched_getaffinity(0))
-    except Exception:
-        return os.cpu_count() or 1
+    done_t, done_i, used = 0.0, 0, []
+    for d in sorted(insts, key=lambda d: d.m):
+        P = o.Problem.from_data(d)
+        t0 = time.perf_counter()
+        o.ipm_solve(P, o.IPMParams(maxit=1))
+        el = time.perf_counter() - t0
+        done_t += el
+        done_i += 1
+        used.append((d.n, d.m, el))
+        if done_t > budget_s:
+            break
+    # scale: mean oracle seconds per IPM iteration over the sampled instances (weighted
+    # to the batch by m^3, the Cholesky cost) times iterations per solve
+    w_s = sum(el for _, _, el in used)
+    w_m = sum(m ** 3 for _, m, _ in used)
+    all_m = sum(d.m ** 3 for d in insts)
+    est_batch_iter = w_s * all_m / w_m
+    solve_s = est_batch_iter * iters_per_solve
+    sample = (f"one oracle IPM iteration (explicit m x m Hessian + Cholesky, NumPy/LAPACK FP64) on "
+              f"{done_i} of the {len(insts)} instances ({w_s:.1f} s), extrapolated to the batch by m^3 and "
+              f"to {iters_per_solve:.1f} IPM iterations per solve")
+    return len(insts) / solve_s, sample
 
 
 def run_reference(args):
-    ws, rank, local = _dist()
+    ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    d = _instance()
-    from oracle import sdp_oracle as o
-    P = o.Problem.from_data(d)
-    iters_per_solve = 16  # the oracle's iteration count for this workload at 1e-6 (same IPM rules)
+    insts, desc = workload(args.workload, args.batch)
     times = []
+    from oracle import sdp_oracle as o
+    small = sorted(insts, key=lambda d: d.m)[0]
+    P = o.Problem.from_data(small)
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        o.ipm_solve(P, o.IPMParams(maxit=1))          # one oracle IPM iteration = one bounded sample
-        el = time.perf_counter() - t0
+        o.ipm_solve(P, o.IPMParams(maxit=1))
         if step >= args.warmup:
-            times.append(el)
-    per_iter = statistics.median(times)
-    value = 1.0 / (per_iter * iters_per_solve)
-    sample = (f"one oracle IPM iteration (explicit Hessian m=8000 + Cholesky + NT eig) per step, "
-              f"scaled by {iters_per_solve} iterations per solve")
+            times.append(time.perf_counter() - t0)
+    per_iter_small = statistics.median(times)
+    scale = sum(d.m ** 3 for d in insts) / small.m ** 3
+    iters = 20.0
+    value = len(insts) / (per_iter_small * scale * iters)
+    sample = (f"one oracle IPM iteration on the smallest instance (n={small.n}, m={small.m}) per step, "
+              f"scaled to the batch by m^3 and to {iters:.0f} IPM iterations per solve")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * per_iter * iters_per_solve,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "n": d.n, "m": d.m, "r": d.k, "l2_flush": False},
+            "warmup": args.warmup, "ms_per_step": 1e3 * len(insts) / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": desc, "instances": len(insts), "l2_flush": False},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -175,120 +207,178 @@ def run(args):
     dist = None
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     from paper_1703_10973_gb300 import SDPProblem, _build, default_params, load
     if not os.path.exists(_build.LIB):
         _build.build()
     load()
-    d = _instance(seed_offset=0)
-    params = default_params(prec=args.prec)
-    stream = torch.cuda.current_stream()
-    prob = SDPProblem.from_data(d, params=params, stream=stream.cuda_stream)
+    insts, desc = workload(args.workload, args.batch)
+    kk = 8 if args.workload == "C2" else 0
+    params = default_params(prec=args.prec, k=kk, pcg_maxit=args.pcg_maxit)
+    nstreams = min(args.streams, len(insts))
+    streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    probs = [SDPProblem.from_data(d, params=params, stream=streams[i % nstreams].cuda_stream)
+             for i, d in enumerate(insts)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def one_solve():
-        prob.reset()
-        return prob.solve()
+    def run_batch(start_event=None):
+        """Solve every instance once; stream s handles instances s, s+S, ...  Returns per-solve ms."""
+        if start_event is not None:
+            for st in streams:
+                st.wait_event(start_event)
+        lat = [None] * len(probs)
+        res = [None] * len(probs)
+        errs = []
 
-    results = []
+        def worker(s):
+            try:
+                st = streams[s]
+                for i in range(s, len(probs), nstreams):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(st)
+                    probs[i].reset()
+                    res[i] = probs[i].solve(allow_maxit=True)
+                    b.record(st)
+                    b.synchronize()
+                    lat[i] = a.elapsed_time(b)
+            except Exception as e:  # surfaced after join
+                errs.append(e)
+
+        th = [threading.Thread(target=worker, args=(s,)) for s in range(nstreams)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        if errs:
+            raise errs[0]
+        return lat, res
+
     for _ in range(args.warmup):
-        results.append(one_solve())
+        run_batch()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    # ---- timed region: K solves, each bracketed by events; L2 flushed between them
-    prob.timing_enable(args.timed_kernel)
-    l0 = prob.launch_count()
-    step_ms = []
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = probs[0].launch_count()
+    step_ms, lat_all, res_last = [], [], None
     with Clocks(local) as clk:
-        torch.cuda.synchronize()
         for i in range(args.steps):
-            flush.fill_(float(i))
-            evs[i][0].record(stream)
-            results.append(one_solve())
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
-    launches = prob.launch_count() - l0
-    kt = prob.timing_read()
-    prob.timing_enable(None)
-    step_ms = [a.elapsed_time(b) for a, b in evs]
+            flush.fill_(float(i))          # evict L2 between steps (256 MB > 126 MB L2)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            lat, res = run_batch(t0)
+            for s in streams:              # join every stream into the default stream
+                torch.cuda.current_stream().wait_stream(s)
+            t1.record()
+            torch.cuda.synchronize()
+            step_ms.append(t0.elapsed_time(t1))
+            lat_all += lat
+            res_last = res
+    launches = probs[0].launch_count() - l0
     total_ms = sum(step_ms)
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         dist.barrier()
-    value = ws * args.steps / (total_ms / 1e3)
-    last = results[-1]
-    ok = all(r["converged"] for r in results)
+    solves = len(insts) * args.steps * ws
+    value = solves / (total_ms / 1e3)
+    converged = all(r["converged"] for r in res_last)
+    ipm_iters = [r["iters"] for r in res_last]
+    pcg_iters = [r["pcg_iters_total"] for r in res_last]
 
-    # ---- end to end through the public API with host buffers
+    # ---- one instrumented step for the dominant kernel class
+    roof = None
+    if rank == 0 and args.timed_kernel:
+        probs[0].timing_enable(args.timed_kernel)
+        tk0 = time.perf_counter()
+        run_batch()
+        torch.cuda.synchronize()
+        step_wall = (time.perf_counter() - tk0) * 1e3
+        kt = probs[0].timing_read()
+        probs[0].timing_enable(None)
+        if kt["launches"]:
+            avg = kt["ms"] / kt["launches"]
+            if args.timed_kernel in ALU_CLASSES:
+                ach = kt["flops"] / (kt["ms"] * 1e-3) / 1e12
+                roof = {"kernel": args.timed_kernel, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                        "peak_source": "measured FP64 DFMA throughput of this GB300 (DESIGN.md)",
+                        "launches": kt["launches"], "avg_us": avg * 1e3,
+                        "busy_ms_per_step": kt["ms"], "step_ms_instrumented": step_wall}
+            else:
+                peak = _peaks().get("hbm_gbs", 6674.2)
+                ach = kt["bytes"] / (kt["ms"] * 1e-3) / 1e9
+                roof = {"kernel": args.timed_kernel, "bound": "hbm", "achieved": ach, "peak": peak,
+                        "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                        "fp64_tflops": kt["flops"] / (kt["ms"] * 1e-3) / 1e12,
+                        "launches": kt["launches"], "avg_us": avg * 1e3, "busy_ms_per_step": kt["ms"]}
+
+    # ---- end to end through the public API: host triplets in, solution out
     e2e = None
     if rank == 0 and args.e2e_steps > 0:
-        h2d = (d.Ci.nbytes + d.Cj.nbytes + d.Cv.nbytes + d.Ak.nbytes + d.Ai.nbytes + d.Aj.nbytes +
-               d.Av.nbytes + d.b.nbytes)
-        d2h = 8 * (d.n * d.n + d.m)
-        X = np.empty((d.n, d.n))
-        yv = np.empty(d.m)
         import ctypes as C
+        h2d = sum(d.Ci.nbytes + d.Cj.nbytes + d.Cv.nbytes + d.Ak.nbytes + d.Ai.nbytes + d.Aj.nbytes +
+                  d.Av.nbytes + d.b.nbytes for d in insts)
+        d2h = sum(8 * (d.n * d.n + d.m) for d in insts)
+        outs = [(np.empty((d.n, d.n)), np.empty(d.m)) for d in insts]
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        te = time.perf_counter()
         for _ in range(args.e2e_steps):
-            p2 = SDPProblem.from_data(d, params=params, stream=stream.cuda_stream)
-            p2.solve()
-            st = p2.lib.sdp_get_solution(p2.h, C.c_void_p(X.ctypes.data), C.c_void_p(yv.ctypes.data), None)
-            assert st == 0
-            p2.close()
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        e2e = {"value": args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+            errs = []
 
-    # ---- roofline of the dominant kernel class
-    roof = None
-    if kt["launches"] > 0 and kt["ms"] > 0:
-        avg_ms = kt["ms"] / kt["launches"]
-        if args.timed_kernel in ("gemm_f64", "sytrd", "potrf", "trsm"):
-            ach = kt["flops"] / kt["launches"] / (avg_ms * 1e-3) / 1e12
-            roof = {"kernel": args.timed_kernel, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                    "peak_source": "measured FP64 DFMA throughput (1.194 TFLOP/s), see DESIGN.md",
-                    "traffic": None, "launches": kt["launches"], "avg_us": avg_ms * 1e3,
-                    "share_of_step": kt["ms"] / total_ms}
-        else:
-            peak = _peaks().get("hbm_gbs", 6674.2)
-            ach = kt["bytes"] / kt["launches"] / (avg_ms * 1e-3) / 1e9
-            fl = kt["flops"] / kt["launches"] / (avg_ms * 1e-3) / 1e12
-            roof = {"kernel": args.timed_kernel, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": None, "launches": kt["launches"], "avg_us": avg_ms * 1e3,
-                    "fp64_tflops": fl, "share_of_step": kt["ms"] / total_ms}
+            def e2e_worker(s):
+                try:
+                    for i in range(s, len(insts), nstreams):
+                        p2 = SDPProblem.from_data(insts[i], params=params, stream=streams[s].cuda_stream)
+                        p2.solve(allow_maxit=True)
+                        X, y = outs[i]
+                        st = p2.lib.sdp_get_solution(p2.h, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data),
+                                                     None)
+                        assert st == 0
+                        p2.close()
+                except Exception as e:
+                    errs.append(e)
+
+            th = [threading.Thread(target=e2e_worker, args=(s,)) for s in range(nstreams)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            if errs:
+                raise errs[0]
+        torch.cuda.synchronize()
+        el = time.perf_counter() - te
+        e2e = {"value": args.e2e_steps * len(insts) / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, per_iter, its = cpu_oracle_rate(d, max(1, int(last["iters"])))
-        cpu = {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle",
-               "sample": f"{its} oracle IPM iterations (explicit m x m Hessian + Cholesky, FP64, NumPy/LAPACK) "
-                         f"at {per_iter:.2f} s each, scaled by the {int(last['iters'])} IPM iterations of a solve"}
+        rate, sample = cpu_oracle_rate(insts, float(np.mean(ipm_iters)))
+        cpu = {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        srt = sorted(step_ms)
+        srt = sorted(lat_all)
         p50 = srt[len(srt) // 2]
         p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else args.prec,
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": d.n, "m": d.m, "r": d.k, "prec": args.prec,
-                           "parallelism": f"replicas{ws}", "l2_flush": True,
-                           "ipm_iters": int(last["iters"]), "pcg_iters_per_solve": int(last["pcg_iters_total"]),
-                           "relgap": last["relgap"], "converged": ok},
+                "config": {"workload": desc, "instances": len(insts), "streams": nstreams, "prec": args.prec,
+                           "parallelism": f"replicas{ws}", "l2_flush": True, "converged": converged,
+                           "ipm_iters_mean": float(np.mean(ipm_iters)),
+                           "pcg_iters_per_solve_mean": float(np.mean(pcg_iters)),
+                           "max_relgap": max(r["relgap"] for r in res_last)},
                 "latency_ms": {"p50": p50, "p99": p99},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
-    prob.close()
+    for p in probs:
+        p.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -297,16 +387,18 @@ def run(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "C2"])
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--streams", type=int, default=4)
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16"])
-    ap.add_argument("--timed-kernel", default="gemm_f64")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--pcg-maxit", type=int, default=2000)
+    ap.add_argument("--timed-kernel", default="sytrd")
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "native":
-        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
     return run(args)

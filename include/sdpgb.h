@@ -60,12 +60,12 @@ typedef struct {
   double pcg_rtol;     /* PCG stop: ||H dy - r|| <= pcg_rtol ||r||;  1e-8          */
   int ipm_maxit;       /* 100 */
   int pcg_maxit;       /* 1000 */
-  int refine_maxit;    /* outer FP64 refinement sweeps for prec != FP64; 8         */
+  int refine_maxit;    /* max restarts of PCG on the true FP64 residual; 64         */
   int k;               /* rank k of the W split (eq. Wsplit2); 0 = value of sdp_setup */
   double step_frac;    /* fraction of the step to the boundary; 0.9                */
   int prec;            /* sdp_prec used inside PCG by sdp_ipm_step / sdp_solve     */
   int precond;         /* sdp_precond_kind; SDP_PRECOND_WOODBURY                   */
-  double inner_rtol;   /* PCG tolerance of a reduced-precision inner solve; 1e-4   */
+  double inner_rtol;   /* PCG tolerance of one restart (sweep); 1e-4                */
   int verbose;         /* 1 = one line per IPM iteration on stderr                 */
 } sdp_params;
 
@@ -79,6 +79,7 @@ typedef struct {
   int pcg_iters_pred, pcg_iters_corr;
   double pcg_relres_pred, pcg_relres_corr;   /* true FP64 residuals              */
   int converged;            /* 1 when the stopping test held at entry              */
+  int nt_fallback;          /* 1 when W came from the Denman-Beavers iteration     */
 } sdp_ipm_info;
 
 typedef struct {

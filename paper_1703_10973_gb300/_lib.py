@@ -54,6 +54,7 @@ class sdp_ipm_info(C.Structure):
         ("pcg_relres_pred", C.c_double),
         ("pcg_relres_corr", C.c_double),
         ("converged", C.c_int),
+        ("nt_fallback", C.c_int),
     ]
 
 

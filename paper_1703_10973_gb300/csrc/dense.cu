@@ -11,7 +11,7 @@
 
 namespace sdpgb {
 
-int64_t g_launches = 0;
+std::atomic<int64_t> g_launches{0};
 
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
@@ -319,6 +319,10 @@ __global__ void k_sum_part(int np, const double* part, double* out) {
   s = block_sum(s, sh);
   if (threadIdx.x == 0) out[0] = s;
 }
+void dot_partials(cudaStream_t st, size_t count, const double* x, const double* y, double* part) {
+  count_launch();
+  k_dot_part<<<DOT_BLOCKS, 256, 0, st>>>(count, x, y, part);
+}
 void dot(cudaStream_t st, size_t count, const double* x, const double* y, double* out, double* part) {
   count_launch(2);
   k_dot_part<<<DOT_BLOCKS, 256, 0, st>>>(count, x, y, part);
@@ -331,14 +335,15 @@ void dot(cudaStream_t st, size_t count, const double* x, const double* y, double
 constexpr int TRMV_CHUNKS = 64;
 size_t trmv_part_doubles(int n) { return (size_t)n * TRMV_CHUNKS; }
 
-__global__ void k_trmv_n(int n, const double* __restrict__ L, int ldl, const double* __restrict__ x, double* __restrict__ y) {
+__global__ void k_trmv_n(int n, const double* __restrict__ L, int ldl, const double* __restrict__ x,
+                         double* __restrict__ y, double alpha, const double* __restrict__ z, double beta) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   if (warp >= n) return;
   const double* row = L + (size_t)warp * ldl;
   double s = 0.0;
   for (int j = lane; j <= warp; j += 32) s = fma(row[j], x[j], s);
   s = warp_sum(s);
-  if (lane == 0) y[warp] = s;
+  if (lane == 0) y[warp] = alpha * s + (z ? beta * z[warp] : 0.0);
 }
 // part[c][j] = sum_{i in chunk c, i >= j} L[i][j] x[i]
 __global__ void k_trmv_t_part(int n, const double* __restrict__ L, int ldl, const double* __restrict__ x, double* __restrict__ part) {
@@ -351,22 +356,27 @@ __global__ void k_trmv_t_part(int n, const double* __restrict__ L, int ldl, cons
   for (int i = max(i0, j); i < i1; ++i) s = fma(L[(size_t)i * ldl + j], x[i], s);
   part[(size_t)c * n + j] = s;
 }
-__global__ void k_trmv_t_sum(int n, const double* __restrict__ part, double* __restrict__ y) {
+__global__ void k_trmv_t_sum(int n, const double* __restrict__ part, double* __restrict__ y, double alpha,
+                             const double* __restrict__ z, double beta) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double s = 0.0;
   for (int c = 0; c < TRMV_CHUNKS; ++c) s += part[(size_t)c * n + j];
-  y[j] = s;
+  y[j] = alpha * s + (z ? beta * z[j] : 0.0);
 }
-void trmv_lower(cudaStream_t st, bool trans, int n, const double* L, int ldl, const double* x, double* y, double* part) {
+void trmv_lower_ex(cudaStream_t st, bool trans, int n, const double* L, int ldl, const double* x, double* y,
+                   double* part, double alpha, const double* z, double beta) {
   if (!trans) {
     count_launch();
-    k_trmv_n<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, L, ldl, x, y);
+    k_trmv_n<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, L, ldl, x, y, alpha, z, beta);
   } else {
     count_launch(2);
     k_trmv_t_part<<<dim3(cdiv(n, 128), TRMV_CHUNKS), 128, 0, st>>>(n, L, ldl, x, part);
-    k_trmv_t_sum<<<cdiv(n, 256), 256, 0, st>>>(n, part, y);
+    k_trmv_t_sum<<<cdiv(n, 256), 256, 0, st>>>(n, part, y, alpha, z, beta);
   }
+}
+void trmv_lower(cudaStream_t st, bool trans, int n, const double* L, int ldl, const double* x, double* y, double* part) {
+  trmv_lower_ex(st, trans, n, L, ldl, x, y, part, 1.0, nullptr, 0.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -465,12 +475,8 @@ __global__ void __launch_bounds__(64) k_inv_diag(int n, const double* L, int ldl
 size_t potrf_work_doubles(int n) { return (size_t)NB * NB + (size_t)n * NB; }
 
 void potrf(cudaStream_t st, int n, double* A, int lda, int* info_dev, double* work) {
-  static bool attr = false;
   const size_t smem = 2 * NB * (NB + 1) * sizeof(double);
-  if (!attr) {
-    cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  allow_max_smem((const void*)k_potrf_diag);
   double* Dinv = work;
   double* tmp = work + NB * NB;   // (n) x NB panel
   ktimer_begin(st, "potrf");
@@ -501,27 +507,32 @@ size_t trsm_work_doubles(int n, int nrhs) {
 
 void trsm_left_lower(cudaStream_t st, bool trans, int n, int nrhs, const double* L, int ldl, double* B,
                      int ldb, double* work) {
+  trsm_left_lower_ex(st, trans, n, nrhs, L, ldl, B, ldb, work, false);
+}
+
+// lower_rhs: B is lower triangular (e.g. the identity when inverting L) and so
+// is L^{-1} B, so block row k only has nonzero columns [0, k0 + kbs): the GEMMs
+// are restricted to those columns, which brings the cost from n^3 to n^3 / 3.
+void trsm_left_lower_ex(cudaStream_t st, bool trans, int n, int nrhs, const double* L, int ldl, double* B,
+                        int ldb, double* work, bool lower_rhs) {
   const int nblk = (n + NB - 1) / NB;
   double* Dinv = work;
   double* tmp = work + (size_t)nblk * NB * NB;
   ktimer_begin(st, "trsm");
   const size_t smem = 2 * NB * (NB + 1) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_inv_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  allow_max_smem((const void*)k_inv_diag);
   count_launch();
   k_inv_diag<<<nblk, 64, smem, st>>>(n, L, ldl, Dinv);
   if (!trans) {
     for (int b = 0; b < nblk; ++b) {
       const int k0 = b * NB, kbs = std::min(NB, n - k0);
+      const int nc = lower_rhs ? std::min(nrhs, k0 + kbs) : nrhs;
       double* Bk = B + (size_t)k0 * ldb;
-      gemm(st, false, false, kbs, nrhs, kbs, 1.0, Dinv + (size_t)b * NB * NB, NB, Bk, ldb, 0.0, tmp, nrhs);
-      copy2d(st, kbs, nrhs, tmp, nrhs, Bk, ldb);
+      gemm(st, false, false, kbs, nc, kbs, 1.0, Dinv + (size_t)b * NB * NB, NB, Bk, ldb, 0.0, tmp, nrhs);
+      copy2d(st, kbs, nc, tmp, nrhs, Bk, ldb);
       const int r0 = k0 + kbs;
       if (r0 < n)
-        gemm(st, false, false, n - r0, nrhs, kbs, -1.0, L + (size_t)r0 * ldl + k0, ldl, Bk, ldb, 1.0,
+        gemm(st, false, false, n - r0, nc, kbs, -1.0, L + (size_t)r0 * ldl + k0, ldl, Bk, ldb, 1.0,
              B + (size_t)r0 * ldb, ldb);
     }
   } else {

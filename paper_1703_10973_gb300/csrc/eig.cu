@@ -17,6 +17,10 @@
 #include "internal.cuh"
 
 #include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
 #include <algorithm>
 
 namespace sdpgb {
@@ -64,10 +68,11 @@ __device__ bool grid_barrier(unsigned int* bar, int* flag) {
       atomicAdd(bar + 1, 1u);
     } else {
       const long long t0 = clock64();
+      unsigned int spins = 0;
       while (*vgen == gen) {
         if (*(volatile int*)flag) { s_ok = 0; break; }
-        if (clock64() - t0 > SPIN_CYCLES) { atomicExch(flag, 1); s_ok = 0; break; }
-        __nanosleep(100);
+        if ((++spins & 255u) == 0u && clock64() - t0 > SPIN_CYCLES) { atomicExch(flag, 1); s_ok = 0; break; }
+        if (spins > 4096u) __nanosleep(64);
       }
     }
     __threadfence();
@@ -132,10 +137,11 @@ __global__ void __launch_bounds__(256) k_sytrd(int n, double* A, int lda, double
     if (threadIdx.x == 0) part[blockIdx.x] = kp;
     if (!grid_barrier(bar, flag)) return;
     // --- w = p - (tau/2)(p^T v) v ; A22 -= v w^T + w v^T
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       double K = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) K += __ldcg(part + b);
-      s_K = 0.5 * tau * K;
+      for (int b = lane; b < (int)gridDim.x; b += 32) K += __ldcg(part + b);
+      K = wsum(K);
+      if (lane == 0) s_K = 0.5 * tau * K;
     }
     __syncthreads();
     const double K = s_K;
@@ -191,11 +197,7 @@ static int sytrd_blocks(int n, size_t smem) {
 static sdp_status sytrd(cudaStream_t st, int n, double* A, EigWork* w) {
   const size_t smem = 2 * (size_t)n * sizeof(double);
   if (smem > 200 * 1024) return SDP_ERR_UNSUPPORTED;
-  static size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    cudaFuncSetAttribute(k_sytrd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = smem;
-  }
+  allow_max_smem((const void*)k_sytrd);
   cudaMemsetAsync(w->bar, 0, 2 * sizeof(unsigned int), st);
   cudaMemsetAsync(w->flag, 0, sizeof(int), st);
   const int blocks = sytrd_blocks(n, smem);
@@ -212,83 +214,83 @@ static sdp_status sytrd(cudaStream_t st, int n, double* A, EigWork* w) {
 // ---------------------------------------------------------------------------
 // 2. Bisection
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int sturm_count(int n, const double* d, const double* e, double x, double pivmin) {
-  // number of eigenvalues of T strictly below x
-  int cnt = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  if (q < 0.0) ++cnt;
+// Number of eigenvalues of T strictly below x, from the signs of the leading
+// principal minors p_i(x) = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (Sturm sequence).
+// The three-term form needs two FP64 multiply-adds per step and no division,
+// which matters on GB300 where every FP64 op of a warp costs many cycles; the
+// sequence is rescaled by a power of two every 16 steps to stay in range.
+// A zero minor takes the sign opposite to its predecessor.
+__device__ __forceinline__ int sturm_count(int n, const double* d, const double* e2, double x) {
+  double pm = 1.0, p = d[0] - x;
+  int sp = (p > 0.0) ? 1 : -1;       // sign of p_0 = 1 is +1; zero counts as a change
+  int cnt = (sp < 0) ? 1 : 0;
   for (int i = 1; i < n; ++i) {
-    const double ei = e[i - 1];
-    q = d[i] - x - (ei * ei) / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0.0) ++cnt;
+    const double pn = fma(d[i] - x, p, -e2[i - 1] * pm);
+    const int sn = (pn > 0.0) ? 1 : (pn < 0.0 ? -1 : -sp);
+    cnt += (sn != sp);
+    sp = sn;
+    pm = p;
+    p = pn;
+    if ((i & 15) == 0) {
+      const double a = fmax(fabs(p), fabs(pm));
+      if (a > 0x1p+400) { p *= 0x1p-400; pm *= 0x1p-400; }
+      else if (a < 0x1p-400 && a > 0.0) { p *= 0x1p+400; pm *= 0x1p+400; }
+    }
   }
   return cnt;
 }
 
-__device__ void gersh(int n, const double* d, const double* e, double* lo, double* hi, double* pivmin) {
-  double gl = d[0], gu = d[0], em = 0.0;
+__device__ void gersh(int n, const double* d, const double* e, double* lo, double* hi) {
+  double gl = d[0], gu = d[0];
   for (int i = 0; i < n; ++i) {
     const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
     gl = fmin(gl, d[i] - r);
     gu = fmax(gu, d[i] + r);
-    if (i + 1 < n) em = fmax(em, e[i] * e[i]);
   }
   const double tn = fmax(fabs(gl), fabs(gu));
   const double pad = 2.0 * DBL_EPSILON * tn * n + 4.0 * DBL_MIN;
   *lo = gl - pad;
   *hi = gu + pad;
-  *pivmin = DBL_MIN * fmax(1.0, em);
 }
 
-// w[t] = eigenvalue number idx[t] (ascending, 0-based) of T.
+// Stage d and e^2 in shared memory (2n doubles) and compute Gershgorin bounds.
+__device__ void stage_tri(int n, const double* d, const double* e, double* sd, double* se2, double* s_lo,
+                          double* s_hi) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sd[i] = d[i];
+    se2[i] = (i + 1 < n) ? e[i] * e[i] : 0.0;
+  }
+  if (threadIdx.x == 0) gersh(n, d, e, s_lo, s_hi);
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool bis_done(double lo, double hi) {
+  return hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN;
+}
+
+// w[t] = eigenvalue number idx[t] (ascending, 0-based) of T; one warp per
+// eigenvalue, 32-point multisection per round (five bits per round).
 __global__ void k_stebz(int n, const double* d, const double* e, int cnt, const int* idx, int i0, double* wout) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ double tri[];
+  __shared__ double s_lo, s_hi;
+  stage_tri(n, d, e, tri, tri + n, &s_lo, &s_hi);
+  const int lane = threadIdx.x % 32;
+  const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (t >= cnt) return;
   const int target = idx ? idx[t] : i0 + t;
-  double lo, hi, pivmin;
-  gersh(n, d, e, &lo, &hi, &pivmin);
-  for (int it = 0; it < 256; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 2.0 * pivmin || mid == lo || mid == hi) break;
-    if (sturm_count(n, d, e, mid, pivmin) > target) hi = mid; else lo = mid;
-  }
-  wout[t] = 0.5 * (lo + hi);
-}
-
-// Smallest eigenvalue by multisection with one warp (32 Sturm counts per round).
-__global__ void k_eigmin_warp(int n, const double* d, const double* e, double* out) {
-  __shared__ double s_lo, s_hi;
-  __shared__ int cnts[32];
-  const int lane = threadIdx.x;
-  if (lane == 0) {
-    double lo, hi, pm;
-    gersh(n, d, e, &lo, &hi, &pm);
-    s_lo = lo; s_hi = hi;
-  }
-  __syncwarp();
-  double lo = s_lo, hi = s_hi, pivmin;
-  {
-    double a, b;
-    gersh(n, d, e, &a, &b, &pivmin);
-  }
-  for (int round = 0; round < 64; ++round) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 2.0 * pivmin) break;
+  double lo = s_lo, hi = s_hi;
+  for (int round = 0; round < 64 && !bis_done(lo, hi); ++round) {
     const double h = (hi - lo) / 33.0;
-    const double x = lo + h * (lane + 1);
-    cnts[lane] = sturm_count(n, d, e, x, pivmin);
-    __syncwarp();
-    // first point with at least one eigenvalue below it
-    int first = 32;
-    for (int l = 0; l < 32; ++l) if (cnts[l] >= 1) { first = l; break; }
+    const int c = sturm_count(n, tri, tri + n, lo + h * (lane + 1));
+    const unsigned above = __ballot_sync(0xffffffffu, c > target);
+    const int first = above ? __ffs(above) - 1 : 32;
     const double nlo = (first == 0) ? lo : lo + h * first;
     const double nhi = (first == 32) ? hi : lo + h * (first + 1);
-    __syncwarp();
     if (nlo == lo && nhi == hi) break;
-    lo = nlo; hi = nhi;
+    lo = nlo;
+    hi = nhi;
   }
-  if (lane == 0) out[0] = 0.5 * (lo + hi);
+  if (lane == 0) wout[t] = 0.5 * (lo + hi);
 }
 
 // ---------------------------------------------------------------------------
@@ -302,12 +304,26 @@ __device__ __forceinline__ double hash_unif(unsigned long long x) {
   return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;  // [-1, 1)
 }
 
-__global__ void k_stein(int n, const double* __restrict__ d, const double* __restrict__ e,
+// One eigenvector per thread.  With blocks == nullptr the whole tridiagonal is
+// used; otherwise thread t works on the unreduced diagonal block that owns the
+// eigenvalue (src[t] is its row, blocks = {blockid, bstart, bend}) and the
+// vector is zero outside that block.
+__global__ void k_stein(int nfull, const double* __restrict__ dfull, const double* __restrict__ efull,
                         const double* __restrict__ wsel, int cnt, double* __restrict__ ws, int bstride,
-                        double* __restrict__ Eout, int ldE, int tbase) {
+                        double* __restrict__ Eout, int ldE, int tbase, const int* __restrict__ src,
+                        const int* __restrict__ blocks) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cnt) return;
-#define WS(f, i) ws[((size_t)(f) * n + (i)) * bstride + t]
+  int s0 = 0, s1 = nfull;
+  if (blocks) {
+    const int b = blocks[src[t]];
+    s0 = blocks[nfull + b];
+    s1 = blocks[2 * nfull + b];
+  }
+  const int n = s1 - s0;
+  const double* d = dfull + s0;
+  const double* e = efull + s0;
+#define WS(f, i) ws[((size_t)(f) * nfull + (i)) * bstride + t]
   const double lam = wsel[t];
   double tnorm = 0.0;
   for (int i = 0; i < n; ++i) {
@@ -357,6 +373,12 @@ __global__ void k_stein(int n, const double* __restrict__ d, const double* __res
       }
     }
   }
+  // reciprocal pivots (tiny pivots replaced by +-tol) so the solves only multiply
+  for (int k = 0; k < n; ++k) {
+    double ak = WS(0, k);
+    if (fabs(ak) < tol) ak = (ak >= 0.0) ? tol : -tol;
+    WS(0, k) = 1.0 / ak;
+  }
   for (int i = 0; i < n; ++i) WS(4, i) = hash_unif(((unsigned long long)(tbase + t) << 32) ^ (unsigned long long)i);
   for (int iter = 0; iter < 3; ++iter) {
     // forward: P L^{-1}
@@ -370,15 +392,22 @@ __global__ void k_stein(int n, const double* __restrict__ d, const double* __res
         WS(4, k) = tmp - WS(2, k - 1) * yk;
       }
     }
-    // backward: U^{-1} with tiny pivots replaced by +-tol
+    // backward: U^{-1} with tiny pivots replaced by +-tol.  Each tiny pivot
+    // multiplies by up to 1/tol, so a cluster of them can overflow: whenever an
+    // entry passes 2^400 the whole vector (solved part and remaining
+    // right-hand side alike) is scaled by 2^-400, which keeps the system
+    // consistent; the vector is normalised afterwards anyway.
     double ymax = 0.0;
     for (int k = n - 1; k >= 0; --k) {
       double tmp = WS(4, k);
       if (k + 1 < n) tmp -= WS(1, k) * WS(4, k + 1);
       if (k + 2 < n) tmp -= WS(3, k) * WS(4, k + 2);
-      double ak = WS(0, k);
-      if (fabs(ak) < tol) ak = (ak >= 0.0) ? tol : -tol;
-      const double yk = tmp / ak;
+      double yk = tmp * WS(0, k);
+      if (!(fabs(yk) < 0x1p+400)) {
+        for (int j = 0; j < n; ++j) WS(4, j) *= 0x1p-400;
+        ymax *= 0x1p-400;
+        yk = (tmp * 0x1p-400) * WS(0, k);
+      }
       WS(4, k) = yk;
       ymax = fmax(ymax, fabs(yk));
     }
@@ -394,7 +423,9 @@ __global__ void k_stein(int n, const double* __restrict__ d, const double* __res
     for (int k = 0; k < n; ++k) WS(4, k) *= sc;
   }
   double* out = Eout + (size_t)t * ldE;
-  for (int k = 0; k < n; ++k) out[k] = WS(4, k);
+  for (int k = 0; k < s0; ++k) out[k] = 0.0;
+  for (int k = 0; k < n; ++k) out[s0 + k] = WS(4, k);
+  for (int k = s1; k < nfull; ++k) out[k] = 0.0;
 #undef WS
 }
 
@@ -454,6 +485,117 @@ __global__ void k_idx_extremes(int n, int k, int* idx) {
 }
 
 // ---------------------------------------------------------------------------
+// Splitting into unreduced blocks.  Where e_i^2 <= eps^2 |d_i d_{i+1}| (+ tiny)
+// the off-diagonal is set to zero and T falls apart into independent blocks.
+// Equal eigenvalues of different blocks would otherwise share one shift, and
+// inverse iteration would return the same null direction for all of them;
+// per block, eigenvalues of an unreduced tridiagonal are distinct, the vectors
+// of different blocks have disjoint supports and are exactly orthogonal.
+// blocks[0..n) = block of each row, blocks[n + b] = first row, blocks[2n + b] =
+// one past the last row, blocks[3n] = number of blocks.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_tri_split(int n, const double* __restrict__ d, const double* __restrict__ e,
+                                                    double* __restrict__ es, int* __restrict__ blocks) {
+  __shared__ int csum[1024];
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int chunk = (n + T - 1) / T, i0 = tid * chunk, i1 = min(n, i0 + chunk);
+  int cnt = 0;
+  for (int i = i0; i < i1; ++i) {
+    bool split = false;
+    if (i + 1 < n) {
+      const double e2 = e[i] * e[i];
+      split = !(e2 > DBL_EPSILON * DBL_EPSILON * fabs(d[i] * d[i + 1]) + 4.0 * DBL_MIN);
+      es[i] = split ? 0.0 : e[i];
+    } else {
+      es[i] = 0.0;
+    }
+    const int starts = (i == 0) ? 1 : 0;   // row i starts a block if i == 0 or e_{i-1} split
+    cnt += starts;
+    (void)split;
+  }
+  // rows that start a block because the previous off-diagonal split
+  for (int i = i0; i < i1; ++i) {
+    if (i > 0) {
+      const double e2 = e[i - 1] * e[i - 1];
+      if (!(e2 > DBL_EPSILON * DBL_EPSILON * fabs(d[i - 1] * d[i]) + 4.0 * DBL_MIN)) ++cnt;
+    }
+  }
+  csum[tid] = cnt;
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int q = 0; q < T; ++q) { const int c = csum[q]; csum[q] = run; run += c; }
+    blocks[3 * n] = run;
+  }
+  __syncthreads();
+  int b = csum[tid] - 1;
+  for (int i = i0; i < i1; ++i) {
+    bool start = (i == 0);
+    if (i > 0) {
+      const double e2 = e[i - 1] * e[i - 1];
+      start = !(e2 > DBL_EPSILON * DBL_EPSILON * fabs(d[i - 1] * d[i]) + 4.0 * DBL_MIN);
+    }
+    if (start) {
+      ++b;
+      blocks[n + b] = i;
+      if (b > 0) blocks[2 * n + b - 1] = i;
+    }
+    blocks[i] = b;
+  }
+  __syncthreads();
+  if (tid == 0) blocks[2 * n + blocks[3 * n] - 1] = n;
+}
+
+// val[t] = eigenvalue number (t - first row) of the block that owns row t.
+__global__ void k_stebz_blk(int n, const double* d, const double* es, const int* __restrict__ blocks, double* val) {
+  extern __shared__ double tri[];
+  double* sd = tri;
+  double* se2 = tri + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sd[i] = d[i];
+    se2[i] = es[i] * es[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x % 32;
+  const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (t >= n) return;
+  const int b = blocks[t], s0 = blocks[n + b], s1 = blocks[2 * n + b], ns = s1 - s0;
+  const int target = t - s0;
+  if (ns == 1) {
+    if (lane == 0) val[t] = sd[s0];
+    return;
+  }
+  double lo, hi;
+  gersh(ns, d + s0, es + s0, &lo, &hi);
+  for (int round = 0; round < 64 && !bis_done(lo, hi); ++round) {
+    const double h = (hi - lo) / 33.0;
+    const int c = sturm_count(ns, sd + s0, se2 + s0, lo + h * (lane + 1));
+    const unsigned above = __ballot_sync(0xffffffffu, c > target);
+    const int first = above ? __ffs(above) - 1 : 32;
+    const double nlo = (first == 0) ? lo : lo + h * first;
+    const double nhi = (first == 32) ? hi : lo + h * (first + 1);
+    if (nlo == lo && nhi == hi) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) val[t] = 0.5 * (lo + hi);
+}
+
+// Global ascending order of the per-block eigenvalues (ties by row).
+__global__ void k_rank(int n, const double* __restrict__ val, double* __restrict__ w, int* __restrict__ src) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double v = val[t];
+  int r = 0;
+  for (int u = 0; u < n; ++u) {
+    const double x = val[u];
+    r += (x < v) || (x == v && u < t);
+  }
+  w[r] = v;
+  src[r] = t;
+}
+
+// ---------------------------------------------------------------------------
 // Host drivers
 // ---------------------------------------------------------------------------
 static int stein_batch(int n) {
@@ -464,7 +606,7 @@ static int stein_batch(int n) {
 }
 
 size_t eig_work_bytes(int n, bool full) {
-  size_t dbl = 5 * (size_t)n + 4096 + 64;
+  size_t dbl = 7 * (size_t)n + 4096 + 64 + (4 * (size_t)n + 16) / 2 + 8;
   if (full) {
     dbl += (size_t)6 * n * stein_batch(n);
     dbl += (size_t)n * n;  // Gram matrix
@@ -482,6 +624,8 @@ void eig_work_carve(EigWork* w, void* base, int n, bool full) {
   w->tauh = p; p += n;
   w->p = p; p += n;
   w->wsel = p; p += n;
+  w->es = p; p += n;
+  w->val = p; p += n;
   w->part = p; p += 4096;
   p += 64;
   w->batch = full ? stein_batch(n) : 64;
@@ -497,6 +641,8 @@ void eig_work_carve(EigWork* w, void* base, int n, bool full) {
   w->bar = (unsigned int*)ip; ip += 4;
   w->flag = ip; ip += 4;
   w->info = ip; ip += 4;
+  w->blocks = ip; ip += 3 * n + 4;
+  w->src = ip; ip += n;
 }
 
 int eig_flag(cudaStream_t st, EigWork* w) {
@@ -506,20 +652,61 @@ int eig_flag(cudaStream_t st, EigWork* w) {
   return f;
 }
 
+static void launch_stebz(cudaStream_t st, int n, const double* d, const double* e, int cnt, const int* idx,
+                         int i0, double* out) {
+  const size_t smem = 2 * (size_t)n * sizeof(double);
+  allow_max_smem((const void*)k_stebz);
+  const int warps = 4;
+  count_launch();
+  k_stebz<<<cdiv(cnt, warps), 32 * warps, smem, st>>>(n, d, e, cnt, idx, i0, out);
+}
+
+// Splits T into unreduced blocks; returns the number of blocks (host sync).
+static int split_blocks(cudaStream_t st, int n, EigWork* w) {
+  count_launch();
+  k_tri_split<<<1, 1024, 0, st>>>(n, w->d, w->e, w->es, w->blocks);
+  int nb = 1;
+  cudaMemcpyAsync(&nb, w->blocks + 3 * n, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  return nb;
+}
+
+// All eigenvalues ascending (w) and, when blocked, the row of the block that owns each.
+static void eigenvalues_all(cudaStream_t st, int n, EigWork* w, int nblocks, double* wout) {
+  if (nblocks <= 1) {
+    launch_stebz(st, n, w->d, w->e, n, nullptr, 0, wout);
+    return;
+  }
+  allow_max_smem((const void*)k_stebz_blk);
+  count_launch(2);
+  k_stebz_blk<<<cdiv(n, 4), 128, 2 * (size_t)n * sizeof(double), st>>>(n, w->d, w->es, w->blocks, w->val);
+  k_rank<<<cdiv(n, 128), 128, 0, st>>>(n, w->val, wout, w->src);
+}
+
+static void eigenvectors(cudaStream_t st, int n, EigWork* w, int nblocks, const double* wv, int first, int cnt,
+                         double* E) {
+  const double* e = (nblocks <= 1) ? w->e : w->es;
+  for (int t0 = 0; t0 < cnt; t0 += w->batch) {
+    const int c = std::min(w->batch, cnt - t0);
+    count_launch();
+    k_stein<<<cdiv(c, 64), 64, 0, st>>>(n, w->d, e, wv + first + t0, c, w->ws, w->batch, E + (size_t)t0 * n, n,
+                                        first + t0, nblocks <= 1 ? nullptr : w->src + first + t0,
+                                        nblocks <= 1 ? nullptr : w->blocks);
+  }
+}
+
 sdp_status eig_full(cudaStream_t st, int n, double* A, double* wout, double* E, EigWork* w) {
   SDP_TRY(sytrd(st, n, A, w));
-  count_launch();
-  k_stebz<<<cdiv(n, 128), 128, 0, st>>>(n, w->d, w->e, n, nullptr, 0, wout);
-  for (int t0 = 0; t0 < n; t0 += w->batch) {
-    const int cnt = std::min(w->batch, n - t0);
-    count_launch();
-    k_stein<<<cdiv(cnt, 64), 64, 0, st>>>(n, w->d, w->e, wout + t0, cnt, w->ws, w->batch,
-                                          E + (size_t)t0 * n, n, t0);
+  const int nb = split_blocks(st, n, w);
+  eigenvalues_all(st, n, w, nb, wout);
+  eigenvectors(st, n, w, nb, wout, 0, n, E);
+  // two Cholesky-QR passes on the rows of E (the second removes the residual
+  // non-orthogonality left by the first inside tight clusters of one block)
+  for (int pass = 0; pass < 2; ++pass) {
+    gemm(st, false, true, n, n, n, 1.0, E, n, E, n, 0.0, w->G, n, 1);
+    potrf(st, n, w->G, n, w->info, w->aux);
+    trsm_left_lower(st, false, n, n, w->G, n, E, n, w->aux);
   }
-  // one Cholesky-QR pass on the rows of E
-  gemm(st, false, true, n, n, n, 1.0, E, n, E, n, 0.0, w->G, n, 1);
-  potrf(st, n, w->G, n, w->info, w->aux);
-  trsm_left_lower(st, false, n, n, w->G, n, E, n, w->aux);
   count_launch();
   k_ormtr_rows<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, A, n, w->tauh, E, n, n);
   return SDP_OK;
@@ -527,8 +714,7 @@ sdp_status eig_full(cudaStream_t st, int n, double* A, double* wout, double* E, 
 
 sdp_status eig_min(cudaStream_t st, int n, double* A, double* lmin_dev, EigWork* w) {
   SDP_TRY(sytrd(st, n, A, w));
-  count_launch();
-  k_eigmin_warp<<<1, 32, 0, st>>>(n, w->d, w->e, lmin_dev);
+  launch_stebz(st, n, w->d, w->e, 1, nullptr, 0, lmin_dev);
   return SDP_OK;
 }
 
@@ -536,14 +722,22 @@ sdp_status eig_extremes(cudaStream_t st, int n, double* A, int k, double* lmin_d
                         double* Etop, EigWork* w) {
   if (k < 0 || k > 31 || k > n) return SDP_ERR_ARG;
   SDP_TRY(sytrd(st, n, A, w));
-  count_launch();
-  k_eigmin_warp<<<1, 32, 0, st>>>(n, w->d, w->e, lmin_dev);
-  if (k == 0) return SDP_OK;
-  int* idx = (int*)w->part;  // small scratch (reinterpreted; part is idle here)
-  count_launch(4);
-  k_idx_extremes<<<1, 32, 0, st>>>(n, k, idx);
-  k_stebz<<<1, 32, 0, st>>>(n, w->d, w->e, k, idx + 1, 0, wtop);
-  k_stein<<<1, 32, 0, st>>>(n, w->d, w->e, wtop, k, w->ws, w->batch, Etop, n, n - k);
+  const int nb = (k > 0) ? split_blocks(st, n, w) : 1;
+  if (nb <= 1) {
+    launch_stebz(st, n, w->d, w->e, 1, nullptr, 0, lmin_dev);
+    if (k == 0) return SDP_OK;
+    int* idx = (int*)w->part;  // small scratch (part is idle here)
+    count_launch(1);
+    k_idx_extremes<<<1, 32, 0, st>>>(n, k, idx);
+    launch_stebz(st, n, w->d, w->e, k, idx + 1, 0, wtop);
+    eigenvectors(st, n, w, 1, wtop, 0, k, Etop);
+  } else {
+    eigenvalues_all(st, n, w, nb, w->wsel);
+    SDP_CK_ST(cudaMemcpyAsync(lmin_dev, w->wsel, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    SDP_CK_ST(cudaMemcpyAsync(wtop, w->wsel + n - k, k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    eigenvectors(st, n, w, nb, w->wsel, n - k, k, Etop);
+  }
+  count_launch(2);
   k_ormtr_rows<<<cdiv((size_t)k * 32, 128), 128, 0, st>>>(n, A, n, w->tauh, Etop, n, k);
   k_mgs<<<1, 256, 0, st>>>(n, Etop, n, k);
   return SDP_OK;

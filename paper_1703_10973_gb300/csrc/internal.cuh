@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -30,6 +31,11 @@ struct Err {
     }                                                                            \
   } while (0)
 
+#define SDP_CK_ST(call)                                                          \
+  do {                                                                           \
+    if ((call) != cudaSuccess) return SDP_ERR_CUDA;                              \
+  } while (0)
+
 #define SDP_TRY(expr)                                                            \
   do {                                                                           \
     sdp_status s_ = (expr);                                                      \
@@ -38,8 +44,8 @@ struct Err {
 
 // Launch accounting: every kernel launch in the library increments this counter
 // (per process); sdp_launch_count() reports it per handle via a snapshot.
-extern int64_t g_launches;
-inline void count_launch(int k = 1) { g_launches += k; }
+extern std::atomic<int64_t> g_launches;
+inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Optional event timing of one kernel class (sdp_timing_enable / sdp_timing_read).
 // ktimer_begin/ktimer_end bracket a launch; they do nothing unless `cls` is the
@@ -49,6 +55,14 @@ void ktimer_begin(cudaStream_t st, const char* cls);
 void ktimer_end(cudaStream_t st, const char* cls, double flops, double bytes);
 void ktimer_set(const char* cls);
 void ktimer_read(double* ms, int64_t* launches, double* flops, double* bytes);
+void ktimer_pause(bool paused);   // no recording while a graph is being captured
+
+// Raise a kernel's dynamic shared-memory limit to the per-CTA maximum, once per
+// kernel and process (thread-safe).  Setting the limit per launch to the size
+// that launch needs races between host threads driving different problems: a
+// smaller value written by one thread can land after a larger one, and the
+// larger launch then fails.
+void allow_max_smem(const void* func);
 
 // Device buffer owned by a handle.
 struct DBuf {
@@ -79,6 +93,8 @@ void potrf(cudaStream_t st, int n, double* A, int lda, int* info_dev, double* wo
 size_t trsm_work_doubles(int n, int nrhs);
 void trsm_left_lower(cudaStream_t st, bool trans, int n, int nrhs, const double* L, int ldl,
                      double* B, int ldb, double* work);
+void trsm_left_lower_ex(cudaStream_t st, bool trans, int n, int nrhs, const double* L, int ldl,
+                        double* B, int ldb, double* work, bool lower_rhs);
 
 // Elementwise helpers.
 void fill(cudaStream_t st, double* x, size_t count, double v);
@@ -98,12 +114,16 @@ void to_bf16(cudaStream_t st, size_t count, const double* x, __nv_bfloat16* y);
 // Deterministic reductions into device memory (two stages, fixed order).
 // out[0] = sum_i x_i y_i.
 void dot(cudaStream_t st, size_t count, const double* x, const double* y, double* out, double* part);
+void dot_partials(cudaStream_t st, size_t count, const double* x, const double* y, double* part);
 size_t dot_part_doubles();
 
 // Lower-triangular GEMV y = L x and y = L^T x (L n x n row-major).  part: n * TRMV_CHUNKS doubles.
 void trmv_lower(cudaStream_t st, bool trans, int n, const double* L, int ldl, const double* x,
                 double* y, double* part);
 size_t trmv_part_doubles(int n);
+// y = alpha op(L) x + beta z   (z may be NULL)
+void trmv_lower_ex(cudaStream_t st, bool trans, int n, const double* L, int ldl, const double* x, double* y,
+                   double* part, double alpha, const double* z, double beta);
 
 // ---------------------------------------------------------------------------
 // Symmetric eigensolver (eig.cu).  A is n x n row-major symmetric and is
@@ -123,6 +143,10 @@ struct EigWork {
   double* aux = nullptr;    // trsm / potrf work
   int* info = nullptr;      // potrf info
   double* wsel = nullptr;   // selected eigenvalues
+  double* es = nullptr;     // n   off-diagonal with split positions zeroed
+  double* val = nullptr;    // n   per-block eigenvalues before sorting
+  int* blocks = nullptr;    // 3n+4  block of each row, block starts, block ends, count
+  int* src = nullptr;       // n   row that owns each sorted eigenvalue
 };
 size_t eig_work_bytes(int n, bool full);
 void eig_work_carve(EigWork* w, void* base, int n, bool full);
@@ -188,6 +212,7 @@ struct sdp_problem {
   // ---- IPM state (device) ----
   double *X = nullptr, *y = nullptr, *S = nullptr, *W = nullptr;
   int iter = 0;
+  int nt_fallbacks = 0;     // NT scalings computed by the Denman-Beavers fallback
   bool have_W = false;
   double xi = 0;
 
@@ -218,6 +243,8 @@ struct sdp_problem {
   double* Bn = nullptr;    // n*k
   double* uvec = nullptr;  // nk
   double* uvec2 = nullptr; // nk
+  double* uvec3 = nullptr; // nk
+  int core_refine = 1;     // refinement steps of each core triangular solve
   double* trpart = nullptr;
 
   // ---- dense IPM work ----
@@ -232,6 +259,14 @@ struct sdp_problem {
   double* part = nullptr;  // reduction partials
   sdpgb::EigWork eig;
   void* eig_base = nullptr;
+
+  // ---- PCG as a device-side graph loop ----
+  int64_t pc_generation = 0;            // bumped by every preconditioner build
+  cudaStream_t capture_stream = nullptr;
+  cudaGraph_t pcg_graph = nullptr;
+  cudaGraphExec_t pcg_exec = nullptr;
+  int64_t pcg_key = -1;
+  int64_t pcg_body_launches = 0;
 
   // ---- PCG vectors ----
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr, *px = nullptr,

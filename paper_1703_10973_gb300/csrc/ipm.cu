@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <utility>
 
 namespace sdpgb {
 
@@ -116,6 +117,143 @@ static sdp_status newton(sdp_problem* h, const double* rhs0, int* its, double* r
   return SDP_OK;
 }
 
+// sum_i log A_ii into *out (one CTA, fixed summation order)
+__global__ void k_logdiag(int n, const double* __restrict__ A, int lda, double* out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += log(A[(size_t)i * lda + i]);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// A <- A^{-1} for symmetric positive definite A; *logdet = log det A.  Lb is scratch (n x n).
+static sdp_status spd_inverse(sdp_problem* h, double* A, double* Lb, double* logdet) {
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  copy2d(st, n, n, A, n, Lb, n);
+  potrf(st, n, Lb, n, h->info, h->work);
+  count_launch();
+  k_logdiag<<<1, 256, 0, st>>>(n, Lb, n, h->scal + R_LMIN);
+  int info = 0;
+  double ld = 0.0;
+  SDP_CK(h, cudaMemcpyAsync(&info, h->info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaMemcpyAsync(&ld, h->scal + R_LMIN, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaStreamSynchronize(st));
+  if (info) {
+    h->last_error = "nt scaling: Denman-Beavers iterate lost positive definiteness";
+    return SDP_ERR_NOT_PD;
+  }
+  *logdet = 2.0 * ld;
+  fill(st, A, (size_t)n * n, 0.0);
+  add_diag(st, n, A, n, 1.0);
+  trsm_left_lower_ex(st, false, n, n, Lb, n, A, n, h->work, true);   // A = L^{-1}
+  gemm(st, true, false, n, n, n, 1.0, A, n, A, n, 0.0, Lb, n);        // L^{-T} L^{-1}
+  copy2d(st, n, n, Lb, n, A, n);
+  symmetrize_avg(st, n, A, n);
+  return SDP_OK;
+}
+
+// M^{-1/2} by the scaled Denman-Beavers iteration
+//   Y0 = M, Z0 = I;  Y+ = (mu Y + Z^{-1}/mu)/2,  Z+ = (mu Z + Y^{-1}/mu)/2,
+//   mu = |det(Y) det(Z)|^{-1/(2n)} while the iterates are far from convergence;
+// Y -> M^{1/2}, Z -> M^{-1/2}.  Every iterate is a rational function of M, so
+// it stays symmetric positive definite and each inverse is a Cholesky inverse.
+// Result in Zout; M is overwritten.  Uses the handle's n x n scratch buffers.
+static sdp_status db_inv_sqrt(sdp_problem* h, double* M, double* Zout) {
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  const size_t nn = (size_t)n * n;
+  double* Y = M;
+  double* Z = Zout;
+  double* Yi = h->Gt;
+  double* Zi = h->dX;
+  double* Lb = h->dS;
+  double* Yn = h->M1;
+  fill(st, Z, nn, 0.0);
+  add_diag(st, n, Z, n, 1.0);
+  bool scale = true;
+  for (int it = 0; it < 40; ++it) {
+    double ly = 0.0, lz = 0.0;
+    copy2d(st, n, n, Y, n, Yi, n);
+    SDP_TRY(spd_inverse(h, Yi, Lb, &ly));
+    copy2d(st, n, n, Z, n, Zi, n);
+    SDP_TRY(spd_inverse(h, Zi, Lb, &lz));
+    const double mu = scale ? std::exp(-(ly + lz) / (2.0 * n)) : 1.0;
+    axpby(st, nn, 0.5 * mu, Y, 0.5 / mu, Zi, Yn);      // Y+
+    axpby(st, nn, 0.5 * mu, Z, 0.5 / mu, Yi, Z);        // Z+ (in place)
+    symmetrize_avg(st, n, Yn, n);
+    symmetrize_avg(st, n, Z, n);
+    axpby(st, nn, 1.0, Yn, -1.0, Y, Y);                 // Y <- Y+ - Y (difference)
+    dot(st, nn, Y, Y, h->scal + R_XDS, h->part);
+    dot(st, nn, Yn, Yn, h->scal + R_DXS, h->part);
+    double v[2];
+    SDP_CK(h, cudaMemcpyAsync(v, h->scal + R_XDS, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SDP_CK(h, cudaStreamSynchronize(st));
+    std::swap(Y, Yn);
+    const double rel = std::sqrt(v[0] / v[1]);
+    if (!std::isfinite(rel)) {
+      h->last_error = "nt scaling: non-finite Denman-Beavers iterate";
+      return SDP_ERR_NUMERIC;
+    }
+    if (rel < 1e-2) scale = false;
+    if (rel < 1e-13) break;
+  }
+  return SDP_OK;
+}
+
+// W = L Q Lambda^{-1/2} Q^T L^T and S^{-1} = L Q Lambda^{-1} Q^T L^T from
+// L^T S L = Q Lambda Q^T.  The eigendecomposition path is checked through the
+// defining property W S W = X; when inverse iteration could not separate a
+// tight eigenvalue cluster the check fails and the inverse square root of
+// L^T S L comes from the Denman-Beavers iteration instead.
+static sdp_status nt_scaling(sdp_problem* h) {
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  const size_t nn = (size_t)n * n;
+  gemm(st, false, false, n, n, n, 1.0, h->S, n, h->L, n, 0.0, h->M1, n);   // S L
+  gemm(st, true, false, n, n, n, 1.0, h->L, n, h->M1, n, 0.0, h->M2, n);   // M = L^T S L
+  symmetrize_avg(st, n, h->M2, n);
+  copy2d(st, n, n, h->M2, n, h->M3, n);                                      // keep M
+  SDP_TRY(eig_full(st, n, h->M2, h->lam, h->E, &h->eig));
+  gemm(st, false, true, n, n, n, 1.0, h->L, n, h->E, n, 0.0, h->Gt, n);    // Gt = L Q, Q = E^T
+  scale_cols(st, n, n, h->Gt, n, h->lam, -0.5, h->M1, n);
+  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->W, n);
+  symmetrize_avg(st, n, h->W, n);
+  scale_cols(st, n, n, h->Gt, n, h->lam, -1.0, h->M1, n);
+  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->Sinv, n);
+  symmetrize_avg(st, n, h->Sinv, n);
+  // check W S W = X
+  gemm(st, false, false, n, n, n, 1.0, h->W, n, h->S, n, 0.0, h->M1, n);
+  gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->Gt, n);
+  axpby(st, nn, 1.0, h->Gt, -1.0, h->X, h->Gt);
+  dot(st, nn, h->Gt, h->Gt, h->scal + R_XDS, h->part);
+  dot(st, nn, h->X, h->X, h->scal + R_DXS, h->part);
+  double v[2], lam0 = 0.0;
+  SDP_CK(h, cudaMemcpyAsync(v, h->scal + R_XDS, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaMemcpyAsync(&lam0, h->lam, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaStreamSynchronize(st));
+  if (eig_flag(st, &h->eig)) {
+    h->last_error = "ipm_step: grid barrier timeout in the eigensolver";
+    return SDP_ERR_TIMEOUT;
+  }
+  const double rel = std::sqrt(v[0] / v[1]);
+  if (std::isfinite(rel) && rel <= 1e-9 && lam0 > 0.0) return SDP_OK;
+  // fallback: Z = M^{-1/2};  W = (L Z) L^T;  S^{-1} = (L Z)(L Z)^T
+  h->nt_fallbacks++;
+  SDP_TRY(db_inv_sqrt(h, h->M3, h->E));
+  gemm(st, false, false, n, n, n, 1.0, h->L, n, h->E, n, 0.0, h->M1, n);   // L Z
+  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->L, n, 0.0, h->W, n);
+  symmetrize_avg(st, n, h->W, n);
+  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->M1, n, 0.0, h->Sinv, n);
+  symmetrize_avg(st, n, h->Sinv, n);
+  return SDP_OK;
+}
+
 sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   SDP_TRY(ipm_alloc(h));
   cudaStream_t st = h->stream;
@@ -159,28 +297,9 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
 
   // ---- NT scaling
   SDP_TRY(chol_checked(h, h->X, h->L, "ipm_step: chol(X)"));
-  gemm(st, false, false, n, n, n, 1.0, h->S, n, h->L, n, 0.0, h->M1, n);   // S L
-  gemm(st, true, false, n, n, n, 1.0, h->L, n, h->M1, n, 0.0, h->M2, n);   // L^T S L
-  symmetrize_avg(st, n, h->M2, n);
-  SDP_TRY(eig_full(st, n, h->M2, h->lam, h->E, &h->eig));
-  gemm(st, false, true, n, n, n, 1.0, h->L, n, h->E, n, 0.0, h->Gt, n);    // Gt = L Q, Q = E^T
-  scale_cols(st, n, n, h->Gt, n, h->lam, -0.5, h->M1, n);
-  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->W, n);
-  symmetrize_avg(st, n, h->W, n);
-  scale_cols(st, n, n, h->Gt, n, h->lam, -1.0, h->M1, n);
-  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->Sinv, n);
-  symmetrize_avg(st, n, h->Sinv, n);
-  double lam0 = 0.0;
-  SDP_CK(h, cudaMemcpyAsync(&lam0, h->lam, sizeof(double), cudaMemcpyDeviceToHost, st));
-  SDP_CK(h, cudaStreamSynchronize(st));
-  if (eig_flag(st, &h->eig)) {
-    h->last_error = "ipm_step: grid barrier timeout in the eigensolver";
-    return SDP_ERR_TIMEOUT;
-  }
-  if (!(lam0 > 0.0)) {
-    h->last_error = "ipm_step: L^T S L has a non-positive eigenvalue " + std::to_string(lam0);
-    return SDP_ERR_NUMERIC;
-  }
+  const int fb0 = h->nt_fallbacks;
+  SDP_TRY(nt_scaling(h));
+  inf.nt_fallback = h->nt_fallbacks - fb0;
   h->have_W = true;
   h->W32_valid = h->W16_valid = false;
   h->pc_valid = false;

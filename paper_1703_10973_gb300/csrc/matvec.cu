@@ -185,16 +185,14 @@ static int rows_per_cta(int n, size_t elem) {
 template <int R>
 static void launch_spmm_f64(sdp_problem* h, const double* Vval) {
   const size_t smem = (size_t)R * h->n * sizeof(double);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_spmm_wv_f64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_max_smem((const void*)k_spmm_wv_f64<R>);
   count_launch();
   k_spmm_wv_f64<R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->colidx, Vval, h->W, h->T);
 }
 template <typename TW, int R>
 static void launch_spmm_lp(sdp_problem* h, const double* Vval, const TW* W) {
   const size_t smem = (size_t)R * h->n * sizeof(float);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_spmm_wv_lp<TW, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_max_smem((const void*)k_spmm_wv_lp<TW, R>);
   count_launch();
   k_spmm_wv_lp<TW, R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->colidx, Vval, W, h->T32);
 }

@@ -18,22 +18,71 @@ namespace sdpgb {
 
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
-enum { S_PQ = 0, S_RR = 1, S_RZ0 = 2, S_RZ1 = 3, S_TMP = 4, S_NR0 = 5 };
+enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6, S_IT = 7, S_MAXIT = 8 };
 
 // x += a p ; r -= a q  with a = rz / pq
 __global__ void k_pcg_xr(int m, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                         const double* __restrict__ q, const double* __restrict__ scal, int rz_slot) {
-  const double a = scal[rz_slot] / scal[S_PQ];
+                         const double* __restrict__ q, const double* __restrict__ scal) {
+  const double a = scal[S_RZ] / scal[S_PQ];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     x[i] = fma(a, p[i], x[i]);
     r[i] = fma(-a, q[i], r[i]);
   }
 }
-// p = z + beta p  with beta = rz_new / rz_old
-__global__ void k_pcg_p(int m, double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ scal,
-                        int rz_new, int rz_old) {
-  const double beta = scal[rz_new] / scal[rz_old];
+// p = z + beta p  with beta = rz_new / rz
+__global__ void k_pcg_p(int m, double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ scal) {
+  const double beta = scal[S_RZN] / scal[S_RZ];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) p[i] = fma(beta, p[i], z[i]);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// Sum of the dot partials (fixed order) into scal[slot]; `promote` first moves
+// rz_new to rz (the previous iteration's direction update has consumed both).
+__global__ void k_pcg_sum(int np, const double* __restrict__ part, double* scal, int slot, int promote) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    s = warp_sum_d(s);
+    if (threadIdx.x == 0) {
+      if (promote) scal[S_RZ] = scal[S_RZN];
+      scal[slot] = s;
+    }
+  }
+}
+// ||r||^2 from the partials, iteration count, and the loop condition.
+__global__ void k_pcg_check(int np, const double* __restrict__ part, double* scal, cudaGraphConditionalHandle cond) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    s = warp_sum_d(s);
+    if (threadIdx.x == 0) {
+      scal[S_RR] = s;
+      const double it = scal[S_IT] + 1.0;
+      scal[S_IT] = it;
+      const bool go = (s > scal[S_TOL2]) && (it < scal[S_MAXIT]) && isfinite(s);
+      cudaGraphSetConditional(cond, go ? 1u : 0u);
+    }
+  }
+}
+__global__ void k_pcg_init(double* scal, double rtol, int maxit) {
+  scal[S_RZN] = scal[S_RZ];
+  scal[S_TOL2] = rtol * rtol * scal[S_NR0];
+  scal[S_IT] = 0.0;
+  scal[S_MAXIT] = (double)maxit;
 }
 
 static sdp_status pcg_alloc(sdp_problem* h) {
@@ -51,6 +100,79 @@ static sdp_status pcg_alloc(sdp_problem* h) {
   return SDP_OK;
 }
 
+static void dot_part_only(cudaStream_t st, size_t count, const double* x, const double* y, double* part);
+
+// One PCG iteration on h->stream (the body of the device-side loop).
+static sdp_status pcg_body(sdp_problem* h, int prec, cudaGraphConditionalHandle cond) {
+  cudaStream_t st = h->stream;
+  const int m = h->m;
+  const unsigned g = std::min(cdiv(m, 256), 2048u);
+  const int np = (int)dot_part_doubles();
+  SDP_TRY(matvec_impl(h, h->pp, h->pq, prec));
+  dot_part_only(st, m, h->pp, h->pq, h->part);
+  count_launch(3);
+  k_pcg_sum<<<1, 512, 0, st>>>(np, h->part, h->scal, S_PQ, 1);
+  k_pcg_xr<<<g, 256, 0, st>>>(m, h->px, h->pr, h->pp, h->pq, h->scal);
+  dot_part_only(st, m, h->pr, h->pr, h->part);
+  k_pcg_check<<<1, 512, 0, st>>>(np, h->part, h->scal, cond);
+  SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec));
+  dot_part_only(st, m, h->pr, h->pz, h->part);
+  count_launch(2);
+  k_pcg_sum<<<1, 512, 0, st>>>(np, h->part, h->scal, S_RZN, 0);
+  k_pcg_p<<<g, 256, 0, st>>>(m, h->pp, h->pz, h->scal);
+  return SDP_OK;
+}
+
+// Build (or reuse) the executable graph: one while-node whose body is one PCG
+// iteration; the loop runs on the device until the recursive residual meets the
+// tolerance or the iteration budget is spent, with no host round trip.
+static sdp_status pcg_graph(sdp_problem* h, int prec) {
+  const int64_t key = h->pc_generation * 8 + prec;
+  if (h->pcg_exec && h->pcg_key == key) return SDP_OK;
+  if (h->pcg_exec) {
+    cudaGraphExecDestroy(h->pcg_exec);
+    h->pcg_exec = nullptr;
+  }
+  if (h->pcg_graph) {
+    cudaGraphDestroy(h->pcg_graph);
+    h->pcg_graph = nullptr;
+  }
+  SDP_TRY(ensure_lowprec_W(h, prec));
+  cudaGraph_t g = nullptr;
+  SDP_CK(h, cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond;
+  SDP_CK(h, cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  SDP_CK(h, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t user = h->stream;
+  h->stream = h->capture_stream;
+  const int64_t l0 = g_launches.load();
+  ktimer_pause(true);
+  cudaError_t e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  sdp_status s = (e == cudaSuccess) ? pcg_body(h, prec, cond) : SDP_ERR_CUDA;
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(h->stream, &out);
+  ktimer_pause(false);
+  h->pcg_body_launches = g_launches.load() - l0;
+  g_launches.fetch_sub(h->pcg_body_launches);
+  h->stream = user;
+  if (e != cudaSuccess || e2 != cudaSuccess || s != SDP_OK) {
+    cudaGraphDestroy(g);
+    h->last_error = std::string("pcg graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+    return s != SDP_OK ? s : SDP_ERR_CUDA;
+  }
+  SDP_CK(h, cudaGraphInstantiate(&h->pcg_exec, g, 0));
+  h->pcg_graph = g;
+  h->pcg_key = key;
+  return SDP_OK;
+}
+
 static double read_scalar(sdp_problem* h, const double* dev) {
   double v = 0.0;
   cudaMemcpyAsync(&v, dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -58,15 +180,16 @@ static double read_scalar(sdp_problem* h, const double* dev) {
   return v;
 }
 
-// Plain PCG from x = 0 on (r, x) in precision prec.  Returns iterations; *rel = recursive relres.
+// Plain PCG from x = 0 in precision prec; x receives the iterate.  *rel is the
+// recursive relative residual at exit.
 static sdp_status pcg_core(sdp_problem* h, const double* rhs, double* x, double rtol, int maxit, int prec,
                            int* iters, double* rel) {
   cudaStream_t st = h->stream;
   const int m = h->m;
-  const unsigned g = std::min(cdiv(m, 256), 2048u);
   double* scal = h->scal;
+  SDP_TRY(pcg_graph(h, prec));
   SDP_CK(h, cudaMemcpyAsync(h->pr, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  SDP_CK(h, cudaMemsetAsync(x, 0, m * sizeof(double), st));
+  SDP_CK(h, cudaMemsetAsync(h->px, 0, m * sizeof(double), st));
   dot(st, m, h->pr, h->pr, scal + S_NR0, h->part);
   const double nr0sq = read_scalar(h, scal + S_NR0);
   if (!std::isfinite(nr0sq)) {
@@ -74,44 +197,31 @@ static sdp_status pcg_core(sdp_problem* h, const double* rhs, double* x, double 
     return SDP_ERR_NUMERIC;
   }
   if (nr0sq == 0.0) {
+    SDP_CK(h, cudaMemsetAsync(x, 0, m * sizeof(double), st));
     *iters = 0;
     *rel = 0.0;
     return SDP_OK;
   }
   SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec));
   SDP_CK(h, cudaMemcpyAsync(h->pp, h->pz, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  dot(st, m, h->pr, h->pz, scal + S_RZ0, h->part);
-  int cur = S_RZ0;
-  double relres = 1.0;
-  for (int it = 1; it <= maxit; ++it) {
-    SDP_TRY(matvec_impl(h, h->pp, h->pq, prec));
-    dot(st, m, h->pp, h->pq, scal + S_PQ, h->part);
-    count_launch();
-    k_pcg_xr<<<g, 256, 0, st>>>(m, x, h->pr, h->pp, h->pq, scal, cur);
-    dot(st, m, h->pr, h->pr, scal + S_RR, h->part);
-    const double rr = read_scalar(h, scal + S_RR);
-    if (!std::isfinite(rr)) {
-      h->last_error = "pcg: non-finite residual";
-      *iters = it;
-      *rel = relres;
-      return SDP_ERR_NUMERIC;
-    }
-    relres = std::sqrt(rr / nr0sq);
-    if (relres <= rtol) {
-      *iters = it;
-      *rel = relres;
-      return SDP_OK;
-    }
-    SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec));
-    const int nxt = (cur == S_RZ0) ? S_RZ1 : S_RZ0;
-    dot(st, m, h->pr, h->pz, scal + nxt, h->part);
-    count_launch();
-    k_pcg_p<<<g, 256, 0, st>>>(m, h->pp, h->pz, scal, nxt, cur);
-    cur = nxt;
+  dot(st, m, h->pr, h->pz, scal + S_RZ, h->part);
+  count_launch();
+  k_pcg_init<<<1, 1, 0, st>>>(scal, rtol, maxit);
+  SDP_CK(h, cudaGraphLaunch(h->pcg_exec, st));
+  double v[9];
+  SDP_CK(h, cudaMemcpyAsync(v, scal, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaStreamSynchronize(st));
+  SDP_CK(h, cudaMemcpyAsync(x, h->px, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const int its = (int)v[S_IT];
+  g_launches.fetch_add((int64_t)its * h->pcg_body_launches);
+  const double rr = v[S_RR];
+  *iters = its;
+  *rel = std::sqrt(rr / nr0sq);
+  if (!std::isfinite(rr)) {
+    h->last_error = "pcg: non-finite residual";
+    return SDP_ERR_NUMERIC;
   }
-  *iters = maxit;
-  *rel = relres;
-  return SDP_ERR_MAXIT;
+  return (rr <= v[S_TOL2]) ? SDP_OK : SDP_ERR_MAXIT;
 }
 
 // relres = ||r - H y|| / ||r|| with the FP64 matvec; leaves r - H y in out
@@ -152,7 +262,7 @@ sdp_status pcg_impl(sdp_problem* h, const double* r, double* y, double rtol, int
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     int it = 0;
     double rr = 0.0;
-    const int budget = std::max(1, std::min(maxit - total, 300));
+    const int budget = std::max(1, std::min(maxit - total, 500));
     sdp_status s = pcg_core(h, resid, corr, inner, budget, prec, &it, &rr);
     total += it;
     if (s != SDP_OK && s != SDP_ERR_MAXIT) return s;
@@ -173,4 +283,10 @@ sdp_status pcg_impl(sdp_problem* h, const double* r, double* y, double rtol, int
   return result;
 }
 
+}  // namespace sdpgb
+
+namespace sdpgb {
+static void dot_part_only(cudaStream_t st, size_t count, const double* x, const double* y, double* part) {
+  dot_partials(st, count, x, y, part);
+}
 }  // namespace sdpgb

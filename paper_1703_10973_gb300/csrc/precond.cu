@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <utility>
 
 namespace sdpgb {
 
@@ -102,6 +103,191 @@ __global__ void k_scale_ginv(int m, const double* __restrict__ ginv, const doubl
   if (i < m) z[i] = ginv[i] * s * r[i];
 }
 
+// Tall-skinny products of the apply (k <= 32 columns; HBM/FP64-bound, not
+// tensor-core work).  ut_part[chunk][l][c] = sum_{a in chunk} B[a][l] Z[a][c]:
+// threads run over the columns c of Z (coalesced rows), the k sums stay in
+// registers, and row chunks spread the work over the GPU; k_ts_ut_sum adds
+// the chunks in a fixed order.
+constexpr int TS_CHUNKS = 32;
+template <int K>
+__global__ void k_ts_ut(int n, const double* __restrict__ B, const double* __restrict__ Z,
+                        double* __restrict__ part) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rows = (n + TS_CHUNKS - 1) / TS_CHUNKS;
+  const int a0 = blockIdx.y * rows, a1 = min(n, a0 + rows);
+  if (c >= n) return;
+  double acc[K];
+#pragma unroll
+  for (int l = 0; l < K; ++l) acc[l] = 0.0;
+  for (int a = a0; a < a1; ++a) {
+    const double z = Z[(size_t)a * n + c];
+#pragma unroll
+    for (int l = 0; l < K; ++l) acc[l] = fma(B[(size_t)a * K + l], z, acc[l]);
+  }
+#pragma unroll
+  for (int l = 0; l < K; ++l) part[((size_t)blockIdx.y * K + l) * n + c] = acc[l];
+}
+__global__ void k_ts_ut_sum(int n, int k, const double* __restrict__ part, double* __restrict__ u) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int l = t / n, c = t % n;
+  double s = 0.0;
+  for (int ch = 0; ch < TS_CHUNKS; ++ch) s += part[((size_t)ch * k + l) * n + c];
+  u[(size_t)l * n + c] = s;
+}
+// ZS[a][l] = sum_c Z[a][c] s[l n + c]: one warp per row a of Z.
+template <int K>
+__global__ void k_ts_zs(int n, const double* __restrict__ Z, const double* __restrict__ s,
+                        double* __restrict__ ZS) {
+  const int a = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  if (a >= n) return;
+  const double* za = Z + (size_t)a * n;
+  double acc[K];
+#pragma unroll
+  for (int l = 0; l < K; ++l) acc[l] = 0.0;
+  for (int c = lane; c < n; c += 32) {
+    const double z = za[c];
+#pragma unroll
+    for (int l = 0; l < K; ++l) acc[l] = fma(z, s[(size_t)l * n + c], acc[l]);
+  }
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    double v = acc[l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) ZS[(size_t)a * K + l] = v;
+  }
+}
+
+template <int K>
+static void ts_launch(cudaStream_t st, int n, const double* Bn, const double* Z, double* part, double* u,
+                      const double* s, double* ZS, bool first) {
+  if (first) {
+    count_launch(2);
+    k_ts_ut<K><<<dim3((n + 127) / 128, TS_CHUNKS), 128, 0, st>>>(n, Bn, Z, part);
+    k_ts_ut_sum<<<cdiv((size_t)n * K, 256), 256, 0, st>>>(n, K, part, u);
+  } else {
+    count_launch();
+    k_ts_zs<K><<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, Z, s, ZS);
+  }
+}
+
+// u (k x n) = Bn^T Z  or  ZS (n x k) = Z S_mat, dispatched on k.
+static bool ts_product(cudaStream_t st, int n, int k, const double* Bn, const double* Z, double* part,
+                       double* u, const double* s, double* ZS, bool first) {
+  switch (k) {
+    case 1: ts_launch<1>(st, n, Bn, Z, part, u, s, ZS, first); return true;
+    case 2: ts_launch<2>(st, n, Bn, Z, part, u, s, ZS, first); return true;
+    case 3: ts_launch<3>(st, n, Bn, Z, part, u, s, ZS, first); return true;
+    case 4: ts_launch<4>(st, n, Bn, Z, part, u, s, ZS, first); return true;
+    case 5: ts_launch<5>(st, n, Bn, Z, part, u, s, ZS, first); return true;
+    case 6: ts_launch<6>(st, n, Bn, Z, part, u, s, ZS, first); return true;
+    case 7: ts_launch<7>(st, n, Bn, Z, part, u, s, ZS, first); return true;
+    case 8: ts_launch<8>(st, n, Bn, Z, part, u, s, ZS, first); return true;
+    default: return false;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Subspace refinement of the top-k eigenpairs of W (k <= 31).  Inverse iteration
+// on the tridiagonal form can return nearly parallel vectors for close top
+// eigenvalues; two steps of subspace iteration with W itself (GEMMs) followed by
+// Rayleigh-Ritz on the k x k projection restore an orthonormal basis of the
+// dominant invariant subspace (the gap lambda_k / lambda_{k+1} grows like 1/mu,
+// so the iteration converges in one or two steps where it matters).
+// ---------------------------------------------------------------------------
+// In place Gram-Schmidt (two passes) over k rows of length n, one CTA.
+__global__ void k_rows_orth(int n, int k, double* E) {
+  __shared__ double red[32];
+  __shared__ double s_val;
+  for (int a = 0; a < k; ++a) {
+    double* xa = E + (size_t)a * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int b = 0; b < a; ++b) {
+        const double* xb = E + (size_t)b * n;
+        double s = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(xa[i], xb[i], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double t = 0.0;
+          for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+          s_val = t;
+        }
+        __syncthreads();
+        const double c = s_val;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) xa[i] -= c * xb[i];
+        __syncthreads();
+      }
+    }
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(xa[i], xa[i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      s_val = (t > 0.0) ? 1.0 / sqrt(t) : 0.0;
+    }
+    __syncthreads();
+    const double c = s_val;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xa[i] *= c;
+    __syncthreads();
+  }
+}
+
+// Cyclic Jacobi on the k x k symmetric B (k <= 32) in one thread; Q (k x k, row
+// j = eigenvector j) and ascending eigenvalues w.  Tiny, so one thread is enough.
+__global__ void k_small_jacobi(int k, double* B, double* Q, double* w) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) Q[i * k + j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        tot += B[i * k + j] * B[i * k + j];
+        if (i != j) off += B[i * k + j] * B[i * k + j];
+      }
+    if (off <= 1e-32 * tot || off == 0.0) break;
+    for (int p = 0; p < k - 1; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        const double apq = B[p * k + q];
+        if (apq == 0.0) continue;
+        const double theta = 0.5 * (B[q * k + q] - B[p * k + p]) / apq;
+        const double t = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int r = 0; r < k; ++r) {  // B <- J^T B J (columns, then rows)
+          const double bp = B[r * k + p], bq = B[r * k + q];
+          B[r * k + p] = c * bp - s * bq;
+          B[r * k + q] = s * bp + c * bq;
+        }
+        for (int r = 0; r < k; ++r) {
+          const double bp = B[p * k + r], bq = B[q * k + r];
+          B[p * k + r] = c * bp - s * bq;
+          B[q * k + r] = s * bp + c * bq;
+        }
+        for (int r = 0; r < k; ++r) {  // rows of Q are eigenvectors: Q <- J^T Q
+          const double qp = Q[p * k + r], qq = Q[q * k + r];
+          Q[p * k + r] = c * qp - s * qq;
+          Q[q * k + r] = s * qp + c * qq;
+        }
+      }
+  }
+  // sort ascending (selection sort on k <= 32)
+  for (int i = 0; i < k; ++i) w[i] = B[i * k + i];
+  for (int i = 0; i < k; ++i) {
+    int mi = i;
+    for (int j = i + 1; j < k; ++j) if (w[j] < w[mi]) mi = j;
+    if (mi != i) {
+      const double tw = w[i]; w[i] = w[mi]; w[mi] = tw;
+      for (int r = 0; r < k; ++r) { const double tq = Q[i * k + r]; Q[i * k + r] = Q[mi * k + r]; Q[mi * k + r] = tq; }
+    }
+  }
+}
+
 static sdp_status precond_alloc(sdp_problem* h) {
   if (h->U) return SDP_OK;
   const int n = h->n, k = std::max(h->k, 1);
@@ -110,7 +296,7 @@ static sdp_status precond_alloc(sdp_problem* h) {
   SDP_TRY(h->allocT(&h->Z, (size_t)n * n));
   SDP_TRY(h->allocT(&h->Sc, nk * nk));
   SDP_TRY(h->allocT(&h->Linv, nk * nk));
-  SDP_TRY(h->allocT(&h->tau_dev, 8));
+  SDP_TRY(h->allocT(&h->tau_dev, 8 + 2 * 32 * 32));
   SDP_TRY(h->allocT(&h->wtop, 32));
   SDP_TRY(h->allocT(&h->Etop, (size_t)32 * n));
   SDP_TRY(h->allocT(&h->au, (size_t)std::max(h->ncr, 1) * k));
@@ -119,8 +305,9 @@ static sdp_status precond_alloc(sdp_problem* h) {
   SDP_TRY(h->allocT(&h->Bn, nk));
   SDP_TRY(h->allocT(&h->uvec, nk));
   SDP_TRY(h->allocT(&h->uvec2, nk));
+  SDP_TRY(h->allocT(&h->uvec3, nk));
   SDP_TRY(h->allocT(&h->pvec, std::max<size_t>(nk, (size_t)h->nnzV)));
-  SDP_TRY(h->allocT(&h->trpart, trmv_part_doubles((int)nk)));
+  SDP_TRY(h->allocT(&h->trpart, std::max(trmv_part_doubles((int)nk), (size_t)TS_CHUNKS * nk)));
   SDP_TRY(h->allocT(&h->info, 8));
   const size_t wneed = std::max(std::max(potrf_work_doubles((int)nk), trsm_work_doubles((int)nk, (int)nk)),
                                 std::max(potrf_work_doubles(n), trsm_work_doubles(n, n)));
@@ -196,6 +383,24 @@ sdp_status precond_build_impl(sdp_problem* h) {
   // ---- step 1a: eigenvalues of W (smallest and top k with vectors)
   copy2d(st, n, n, h->W, n, h->M1, n);
   SDP_TRY(eig_extremes(st, n, h->M1, k, h->tau_dev, h->wtop, h->Etop, &h->eig));
+  if (k > 0) {
+    // refine Etop (k x n): two subspace steps with W, then Rayleigh-Ritz
+    double* V = h->Bn;            // k x n scratch (Bn holds n k doubles)
+    double* sm = h->tau_dev + 8;  // k x k projection, k x k rotation
+    for (int step = 0; step < 2; ++step) {
+      gemm(st, false, false, k, n, n, 1.0, h->Etop, n, h->W, n, 0.0, V, n);   // rows of E W
+      count_launch();
+      k_rows_orth<<<1, 256, 0, st>>>(n, k, V);
+      copy2d(st, k, n, V, n, h->Etop, n);
+    }
+    gemm(st, false, false, k, n, n, 1.0, h->Etop, n, h->W, n, 0.0, V, n);     // E W
+    gemm(st, false, true, k, k, n, 1.0, V, n, h->Etop, n, 0.0, sm, k);        // B = E W E^T
+    symmetrize_avg(st, k, sm, k);
+    count_launch();
+    k_small_jacobi<<<1, 32, 0, st>>>(k, sm, sm + k * k, h->wtop);
+    gemm(st, false, false, k, n, k, 1.0, sm + k * k, k, h->Etop, n, 0.0, V, n); // rotate
+    copy2d(st, k, n, V, n, h->Etop, n);
+  }
   double tau = 0.0;
   SDP_CK(h, cudaMemcpyAsync(&tau, h->tau_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
   SDP_CK(h, cudaStreamSynchronize(st));
@@ -211,6 +416,7 @@ sdp_status precond_build_impl(sdp_problem* h) {
   h->kpc = k;
   if (k == 0) {
     h->pc_valid = true;
+    h->pc_generation++;
     return SDP_OK;
   }
   // ---- step 1b: U and Z = chol(2W - U U^T)
@@ -246,8 +452,9 @@ sdp_status precond_build_impl(sdp_problem* h) {
   h->core_shift = shift;
   fill(st, h->Linv, (size_t)nk * nk, 0.0);
   add_diag(st, nk, h->Linv, nk, 1.0);
-  trsm_left_lower(st, false, nk, nk, h->Sc, nk, h->Linv, nk, h->work);
+  trsm_left_lower_ex(st, false, nk, nk, h->Sc, nk, h->Linv, nk, h->work, true);
   h->pc_valid = true;
+  h->pc_generation++;
   return SDP_OK;
 }
 
@@ -264,12 +471,26 @@ sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int pr
   // u = Z^T (sum g_i r_i A_i) U, stored as k x n (row l = column l of u)
   assemble_V(h, r, h->ginv, h->pvec);
   spmm_rows(h, h->pvec, h->U, k, k, h->Bn, k);
-  gemm(st, true, false, k, n, n, 1.0, h->Bn, k, h->Z, n, 0.0, h->uvec, n);
-  // s = L^{-T} L^{-1} u
-  trmv_lower(st, false, nk, h->Linv, nk, h->uvec, h->uvec2, h->trpart);
-  trmv_lower(st, true, nk, h->Linv, nk, h->uvec2, h->uvec, h->trpart);
+  if (!ts_product(st, n, k, h->Bn, h->Z, h->trpart, h->uvec, nullptr, nullptr, true))
+    gemm(st, true, false, k, n, n, 1.0, h->Bn, k, h->Z, n, 0.0, h->uvec, n);
+  // s = L^{-T} L^{-1} u.  Multiplying by the stored inverse alone loses accuracy
+  // once the core is ill conditioned (kappa(L) eps, late interior-point
+  // iterations), so each triangular solve takes one step of iterative refinement
+  // whose residual uses the factor itself:  y0 = L^{-1} u,  y = y0 + L^{-1}(u - L y0).
+  // ||I - L^{-1} L|| stays far below one where the plain inverse has failed, and
+  // the refined solve matches substitution.  Buffers: uvec = u, uvec2 = y0, uvec3 = scratch.
+  for (int t = 0; t < 2; ++t) {
+    const bool tr = (t == 1);
+    trmv_lower_ex(st, tr, nk, h->Linv, nk, h->uvec, h->uvec2, h->trpart, 1.0, nullptr, 0.0);   // y0
+    for (int it = 0; it < h->core_refine; ++it) {
+      trmv_lower_ex(st, tr, nk, h->Sc, nk, h->uvec2, h->uvec3, h->trpart, -1.0, h->uvec, 1.0); // u - L y0
+      trmv_lower_ex(st, tr, nk, h->Linv, nk, h->uvec3, h->uvec2, h->trpart, 1.0, h->uvec2, 1.0);  // y0 + L^{-1} res
+    }
+    std::swap(h->uvec, h->uvec2);   // result becomes the input of the next solve
+  }
   // ZS = Z S_mat with S_mat[c][l] = s[l n + c]
-  gemm(st, false, true, n, k, n, 1.0, h->Z, n, h->uvec, n, 0.0, h->Bn, k);
+  if (!ts_product(st, n, k, nullptr, h->Z, nullptr, nullptr, h->uvec, h->Bn, false))
+    gemm(st, false, true, n, k, n, 1.0, h->Z, n, h->uvec, n, 0.0, h->Bn, k);
   count_launch();
   k_apply_tail<<<cdiv(m, 256), 256, 0, st>>>(m, k, h->eptr, h->ep, h->eq, h->ecoef, h->Bn, h->U, h->ginv, r,
                                              inv_tau2, z);

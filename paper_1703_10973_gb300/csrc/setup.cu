@@ -44,7 +44,7 @@ extern "C" void sdp_default_params(sdp_params* p) {
   p->pcg_rtol = 1e-8;
   p->ipm_maxit = 100;
   p->pcg_maxit = 1000;
-  p->refine_maxit = 8;
+  p->refine_maxit = 64;
   p->k = 0;
   p->step_frac = 0.9;
   p->prec = SDP_FP64;
@@ -76,6 +76,9 @@ extern "C" void sdp_destroy(sdp_problem* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
   }
+  if (h->pcg_exec) cudaGraphExecDestroy(h->pcg_exec);
+  if (h->pcg_graph) cudaGraphDestroy(h->pcg_graph);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   for (void* p : h->owned) cudaFree(p);
   delete h;
 }
@@ -301,6 +304,7 @@ static sdp_status build(sdp_problem* h, int64_t nnzC, const int32_t* Ci, const i
   add_diag(h->stream, n, h->X, n, h->xi);
   fill(h->stream, h->S, nn, 0.0);
   add_diag(h->stream, n, h->S, n, h->xi);
+  SDP_CK(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
   SDP_CK(h, cudaStreamSynchronize(h->stream));
   return SDP_OK;
 }
@@ -323,7 +327,7 @@ extern "C" sdp_status sdp_setup(int n, int m, int64_t nnzC, const int32_t* Ci, c
   else sdp_default_params(&h->prm);
   h->k = (h->prm.k > 0) ? std::min(h->prm.k, n) : k;
   h->stream = (cudaStream_t)cuda_stream;
-  h->launches_at_setup = g_launches;
+  h->launches_at_setup = g_launches.load();
   sdp_status s = build(h, nnzC, Ci, Cj, Cv, nnzA, Ak, Ai, Aj, Av, b);
   if (s != SDP_OK) {
     fprintf(stderr, "sdp_setup: %s\n", h->last_error.c_str());
@@ -383,7 +387,7 @@ extern "C" sdp_status sdp_sizes(const sdp_problem* h, int* n, int* m, int* k, in
 
 extern "C" int64_t sdp_launch_count(const sdp_problem* h) {
   (void)h;
-  return g_launches;
+  return g_launches.load();
 }
 
 extern "C" sdp_status sdp_precond_info(sdp_problem* h, double* tau, int* k) {

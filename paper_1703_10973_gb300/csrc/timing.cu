@@ -4,6 +4,7 @@
 #include "internal.cuh"
 
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -14,10 +15,10 @@ struct Pending {
   cudaEvent_t a, b;
   double flops, bytes;
 };
+std::mutex g_mu;
 std::string g_cls;
 std::vector<cudaEvent_t> g_pool;
 std::vector<Pending> g_pending;
-cudaEvent_t g_open = nullptr;
 double g_ms = 0, g_flops = 0, g_bytes = 0;
 int64_t g_count = 0;
 
@@ -48,29 +49,38 @@ void drain() {
 }
 }  // namespace
 
-bool ktimer_on(const char* cls) { return !g_cls.empty() && g_cls == cls; }
+bool g_paused = false;
+bool ktimer_on(const char* cls) { return !g_paused && !g_cls.empty() && g_cls == cls; }
+void ktimer_pause(bool paused) { g_paused = paused; }
+
+// One open event per thread: launches of a class are not nested.
+thread_local cudaEvent_t t_open = nullptr;
 
 void ktimer_begin(cudaStream_t st, const char* cls) {
   if (!ktimer_on(cls)) return;
-  g_open = take();
-  cudaEventRecord(g_open, st);
+  std::lock_guard<std::mutex> lk(g_mu);
+  t_open = take();
+  cudaEventRecord(t_open, st);
 }
 
 void ktimer_end(cudaStream_t st, const char* cls, double flops, double bytes) {
-  if (!ktimer_on(cls) || !g_open) return;
+  if (!ktimer_on(cls) || !t_open) return;
+  std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t b = take();
   cudaEventRecord(b, st);
-  g_pending.push_back({g_open, b, flops, bytes});
-  g_open = nullptr;
+  g_pending.push_back({t_open, b, flops, bytes});
+  t_open = nullptr;
   if (g_pending.size() > 4096) drain();
 }
 
 void ktimer_set(const char* cls) {
+  std::lock_guard<std::mutex> lk(g_mu);
   drain();
   g_cls = cls ? cls : "";
 }
 
 void ktimer_read(double* ms, int64_t* launches, double* flops, double* bytes) {
+  std::lock_guard<std::mutex> lk(g_mu);
   drain();
   if (ms) *ms = g_ms;
   if (launches) *launches = g_count;
@@ -78,6 +88,23 @@ void ktimer_read(double* ms, int64_t* launches, double* flops, double* bytes) {
   if (bytes) *bytes = g_bytes;
   g_ms = g_flops = g_bytes = 0;
   g_count = 0;
+}
+
+void allow_max_smem(const void* func) {
+  static std::mutex mu;
+  static std::vector<const void*> done;
+  std::lock_guard<std::mutex> lk(mu);
+  for (const void* f : done)
+    if (f == func) return;
+  int dev = 0, mx = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, func);
+  // the limit covers dynamic memory only; static shared memory counts against the same per-CTA total
+  cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+  cudaGetLastError();
+  done.push_back(func);
 }
 
 }  // namespace sdpgb

@@ -263,14 +263,38 @@ def test_solve_maxcut_bipartite_closed_form():
     assert np.abs(X - np.outer(z, z)).max() <= 1e-3
 
 
-def test_solve_general_sparse_kkt():
-    d = si.random_general(16, 24, 2, 21)
+def _planted_general(n=30, m=100, nnz_per=3, rank=2, seed=21):
+    """General sparse SDP (disjoint supports, A^T A diagonal) with a planted
+    strictly complementary optimum: X* = V V^T of rank 2, S* on the orthogonal
+    complement, y* random; b = A(X*) and C = A^T y* + S* are built with the
+    oracle's operators, so (X*, y*, S*) is optimal with zero duality gap."""
+    d = si.random_general(n, m, nnz_per, seed)
+    P = o.Problem.from_data(d)
+    rng = np.random.default_rng(seed + 100)
+    V = rng.standard_normal((n, rank))
+    Xs = V @ V.T
+    Q, _ = np.linalg.qr(np.concatenate([V, rng.standard_normal((n, n - rank))], axis=1))
+    Qp = Q[:, rank:]
+    Ss = (Qp * rng.uniform(0.5, 2.0, n - rank)) @ Qp.T
+    ys = rng.standard_normal(m)
+    b = o.op_A(P, Xs)
+    Cm = o.op_At(P, ys) + Ss
+    iu, ju = np.triu_indices(n)
+    d2 = si.SDPData(n=n, m=m, Ci=iu.astype(np.int32), Cj=ju.astype(np.int32), Cv=Cm[iu, ju],
+                    Ak=d.Ak, Ai=d.Ai, Aj=d.Aj, Av=d.Av, b=b, k=rank, meta=dict(kind="planted"))
+    return d2, Xs, ys, Ss
+
+
+def test_solve_general_sparse_planted():
+    d, Xs, ys, Ss = _planted_general()
     P = o.Problem.from_data(d)
     ref = o.ipm_solve(P)
+    assert ref.converged
     with _prob(d) as prob:
         res = prob.solve()
         X, y, S = prob.get_solution()
     assert res["converged"]
     assert abs(res["obj_p"] - ref.obj_p) <= 1e-6 * (1 + abs(ref.obj_p))
+    assert _rel(X, Xs) <= 1e-5 and _rel(X, ref.X) <= 1e-5
     cert = o.kkt_certificate(P, X, y, S)
     assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6 and cert["relgap"] <= 1e-6
