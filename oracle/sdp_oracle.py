@@ -316,6 +316,35 @@ def precond_build(P: Problem, W, k, z_kind="chol"):
     return Precond(tau=sp.tau, U=sp.U, Z=sp.Z, ginv=ginv, Sc=Sc, Lc=Lc)
 
 
+def precond_hat_build(P: Problem, W, k):
+    """Section V, eq. (sparse_prec): Hhat = A^T (tau^2 I + 2 tau (U U^T kron I)) A.
+
+    Hhat replaces Z Z^T = 2 W0 + U U^T of eq. (hessExp2) by 2 tau I, so it is the
+    Algorithm 1 matrix tau^2 A^T A + UU UU^T with Z = sqrt(2 tau) I.  Its core
+    tau^2 I + UU^T G^{-1} UU then has condition number of order lambda_max(W) / tau
+    instead of (lambda_max(W) / tau)^2, which is what the section is after.  The
+    same eq. (SMW2) apply (precond_apply) serves both; tau and U come from
+    eq. (Wsplit2) as in Algorithm 1 step 1.
+    """
+    sp = split_W(W, k, "eig")
+    n = W.shape[0]
+    Z = math.sqrt(2.0 * sp.tau) * np.eye(n)
+    ginv = 1.0 / gram_AtA_diag(P)
+    UU = UU_explicit(P, sp.U, Z)
+    Sc = sp.tau ** 2 * np.eye(n * k) + UU.T @ (ginv[:, None] * UU)
+    Lc = np.linalg.cholesky(Sc)
+    return Precond(tau=sp.tau, U=sp.U, Z=Z, ginv=ginv, Sc=Sc, Lc=Lc)
+
+
+def precond_hat_dense(P: Problem, W, k):
+    """eq. (sparse_prec) written out with an explicit n^2 x n^2 Kronecker product (tiny n)."""
+    sp = split_W(W, k, "eig")
+    n = W.shape[0]
+    A = P.A_matrix()
+    mid = sp.tau ** 2 * np.eye(n * n) + 2.0 * sp.tau * np.kron(sp.U @ sp.U.T, np.eye(n))
+    return A.T @ mid @ A
+
+
 def precond_apply(P: Problem, pc: Precond, r):
     """eq. (SMW2): Ht^{-1} r = (tau^2 G)^{-1} (r - UU S^{-1} UU^T G^{-1} r).
 

@@ -218,6 +218,67 @@ def test_lemma_bounds(mu):
     assert np.linalg.cond(o.hessian_entries(P, W)) > 10 * k0 ** 2
 
 
+def test_hat_smw_apply_equals_definition():
+    """eq. (sparse_prec): the eq. (SMW2) apply with Z = sqrt(2 tau) I inverts
+    A^T (tau^2 I + 2 tau U U^T kron I) A built with an explicit Kronecker product."""
+    P = _mc(5, 5, 2, 15, 7)
+    W = _ipm_like_W(P.n, 2, 1e-4, 3)
+    pc = o.precond_hat_build(P, W, 2)
+    Hh = o.precond_hat_dense(P, W, 2)
+    assert _rel(o.precond_dense(P, pc), Hh) < 1e-12
+    r = si.random_vec(P.m, 1)
+    assert _rel(o.precond_apply(P, pc, r), np.linalg.solve(Hh, r)) < 1e-9
+
+
+def test_hat_general_constraints():
+    """Same identity for constraints with several entries each, and for diagonal ones."""
+    for d in (si.random_general(10, 12, 3, 31), si.unit_diag_instance(8)):
+        P = o.Problem.from_data(d)
+        W = si.random_spd(P.n, 5, cond=1e3)
+        pc = o.precond_hat_build(P, W, 2)
+        Hh = o.precond_hat_dense(P, W, 2)
+        r = si.random_vec(P.m, 2)
+        assert _rel(o.precond_apply(P, pc, r), np.linalg.solve(Hh, r)) < 1e-9
+
+
+def test_hat_exact_up_to_rank_k2_when_W0_is_tau_I():
+    """W = tau I + U U^T: H - Hhat = A^T (U U^T kron U U^T) A (sym kron lemma), of rank
+    <= k(k+1)/2 for symmetric A_i, so PCG with Hhat stops within k(k+1)/2 + 1 steps.
+    With tau instead of 2 tau in eq. (sparse_prec) the difference has full rank."""
+    P = _mc(6, 6, 2, 24, 9)
+    rng = np.random.default_rng(5)
+    U0 = rng.standard_normal((P.n, 2)) * 3.0
+    W = 0.8 * np.eye(P.n) + U0 @ U0.T
+    H = o.hessian_entries(P, W)
+    Hh = o.precond_hat_dense(P, W, 2)
+    s = np.linalg.svd(H - Hh, compute_uv=False)
+    assert s[3] <= 1e-10 * s[0]
+    r = si.random_vec(P.m, 3)
+    pc = o.precond_hat_build(P, W, 2)
+    res = o.pcg(lambda v: H @ v, lambda v: o.precond_apply(P, pc, v), r, rtol=1e-10)
+    assert res.converged and res.iters <= 4
+    A = P.A_matrix()
+    bad = A.T @ (0.64 * np.eye(P.n ** 2) + 0.8 * np.kron(U0 @ U0.T, np.eye(P.n))) @ A
+    sb = np.linalg.svd(H - bad, compute_uv=False)
+    assert sb[3] > 1e-3 * sb[0]
+
+
+@pytest.mark.parametrize("mu", [1e-2, 1e-5])
+def test_lemma_aug_prec(mu):
+    """Lemma aug_prec: apart from the k^2 largest, the eigenvalues of Hhat^{-1} H lie
+    within a factor kappa(W0)^2 of the smallest."""
+    P = _mc(5, 5, 2, 16, 10)
+    W = _ipm_like_W(P.n, 2, mu, 6)
+    sp = o.split_W(W, 2)
+    k0 = np.linalg.cond(sp.W0)
+    ev = sla.eigh(o.hessian_entries(P, W), o.precond_hat_dense(P, W, 2), eigvals_only=True)
+    assert ev[:-4].max() / ev[0] <= k0 ** 2 * (1 + 1e-8)
+    # while the Alg. 1 core is far worse conditioned than the Hhat core
+    c1 = np.linalg.cond(o.precond_build(P, W, 2).Sc)
+    c2 = np.linalg.cond(o.precond_hat_build(P, W, 2).Sc)
+    assert c2 < c1
+
+
 # --------------------------------------------------------------------------
 # PCG
 # --------------------------------------------------------------------------
