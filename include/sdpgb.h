@@ -51,7 +51,13 @@ typedef enum { SDP_FP64 = 0, SDP_FP32 = 1, SDP_BF16 = 2 } sdp_prec;
 
 typedef enum {
   SDP_PRECOND_DIAG = 0,     /* tau^2 A^T A only (U = 0)                            */
-  SDP_PRECOND_WOODBURY = 1  /* Ht = tau^2 A^T A + UU UU^T, eq. (AtIUUtAt)/(SMW2)   */
+  SDP_PRECOND_WOODBURY = 1, /* Ht = tau^2 A^T A + UU UU^T, eq. (AtIUUtAt)/(SMW2),    */
+                            /* Algorithm 1 (Section III)                           */
+  SDP_PRECOND_HAT = 2       /* Hhat = A^T (tau^2 I + 2 tau U U^T kron I) A,        */
+                            /* eq. (sparse_prec) of Section V: the Algorithm 1     */
+                            /* construction with Z = sqrt(2 tau) I, whose core is  */
+                            /* conditioned like 1/mu instead of 1/mu^2; this is    */
+                            /* the preconditioner of the paper's experiments       */
 } sdp_precond_kind;
 
 typedef struct {
@@ -64,7 +70,7 @@ typedef struct {
   int k;               /* rank k of the W split (eq. Wsplit2); 0 = value of sdp_setup */
   double step_frac;    /* fraction of the step to the boundary; 0.9                */
   int prec;            /* sdp_prec used inside PCG by sdp_ipm_step / sdp_solve     */
-  int precond;         /* sdp_precond_kind; SDP_PRECOND_WOODBURY                   */
+  int precond;         /* sdp_precond_kind; SDP_PRECOND_HAT                        */
   double inner_rtol;   /* PCG tolerance of one restart (sweep); 1e-4                */
   int verbose;         /* 1 = one line per IPM iteration on stderr                 */
 } sdp_params;
@@ -127,14 +133,18 @@ sdp_status sdp_hessian_matvec(sdp_problem* h, const double* v_dev, double* Hv_de
  * tau = lambda_min(W), U = V_l (Lambda_l - tau I)^{1/2} from the k largest
  * eigenpairs (eq. Wsplit2), Z = chol(2 W0 + U U^T) (eq. hessExp2), the core
  * S = tau^2 I + UU^T (A^T A)^{-1} UU with UU = A^T (U kron Z) (eq. SMW2, using
- * tau^2), its Cholesky factor L and L^{-1}.  SDP_ERR_NOT_PD if a factor fails.
+ * tau^2), its Cholesky factor L and L^{-1}.  With params.precond =
+ * SDP_PRECOND_HAT, Z = sqrt(2 tau) I (eq. sparse_prec, Section V): the core is
+ * then tau^2 I + 2 tau K with K_(l,l') = sum_i (A_i u_l)(A_i u_l')^T / ||A_i||^2,
+ * a sparse matrix scattered into the dense core.  SDP_ERR_NOT_PD if a factor fails.
  */
 sdp_status sdp_precond_build(sdp_problem* h);
 
 /*
  * sdp_precond_apply -- eq. (SMW2): z = (tau^2 G)^{-1} (r - UU S^{-1} UU^T G^{-1} r)
  * with G = A^T A, UU^T y = Z^T (sum y_i A_i) U and (UU X)_i = A_i . (Z X U^T)
- * (eq. Umv).  r_dev, z_dev: device double[m].  Needs sdp_precond_build first.
+ * (eq. Umv); Z = sqrt(2 tau) I for SDP_PRECOND_HAT, so neither product needs Z.
+ * r_dev, z_dev: device double[m].  Needs sdp_precond_build first.
  */
 sdp_status sdp_precond_apply(sdp_problem* h, const double* r_dev, double* z_dev, int prec);
 

@@ -14,7 +14,7 @@ from ._build import LIB
 SDP_OK, SDP_ERR_ARG, SDP_ERR_OOM, SDP_ERR_NOT_PD, SDP_ERR_MAXIT = 0, 1, 2, 3, 4
 SDP_ERR_UNSUPPORTED, SDP_ERR_NUMERIC, SDP_ERR_TIMEOUT, SDP_ERR_CUDA = 5, 6, 7, 8
 SDP_FP64, SDP_FP32, SDP_BF16 = 0, 1, 2
-SDP_PRECOND_DIAG, SDP_PRECOND_WOODBURY = 0, 1
+SDP_PRECOND_DIAG, SDP_PRECOND_WOODBURY, SDP_PRECOND_HAT = 0, 1, 2
 
 PREC = {"fp64": SDP_FP64, "fp32": SDP_FP32, "bf16": SDP_BF16}
 

@@ -384,11 +384,11 @@ void trmv_lower(cudaStream_t st, bool trans, int n, const double* L, int ldl, co
 // ---------------------------------------------------------------------------
 constexpr int NB = 64;
 
-// Factor the nbs x nbs diagonal block in place (lower) and write its inverse to Dinv (ld NB).
-__global__ void __launch_bounds__(256) k_potrf_diag(int nbs, double* A, int lda, double* Dinv, int* info, int base) {
+// Factor the nbs x nbs diagonal block in place (lower).
+__global__ void __launch_bounds__(256) k_potrf_diag(int nbs, double* A, int lda, int* info, int base,
+                                                    double floor_) {
   extern __shared__ double sm[];
   double* a = sm;                  // NB x (NB+1)
-  double* x = sm + NB * (NB + 1);  // NB x (NB+1)
   constexpr int LD = NB + 1;
   for (int t = threadIdx.x; t < nbs * nbs; t += blockDim.x) {
     const int i = t / nbs, j = t % nbs;
@@ -398,7 +398,14 @@ __global__ void __launch_bounds__(256) k_potrf_diag(int nbs, double* A, int lda,
   for (int j = 0; j < nbs; ++j) {
     if (threadIdx.x == 0) {
       double p = a[j * LD + j];
-      if (!(p > 0.0)) {
+      if (floor_ > 0.0) {
+        // the matrix is known to satisfy A >= floor I, so every Cholesky pivot
+        // (a Schur-complement diagonal) is >= floor; smaller ones are rounding
+        if (!(p >= floor_)) {
+          if (info) atomicAdd(info + 1, 1);
+          p = floor_;
+        }
+      } else if (!(p > 0.0)) {
         if (info && *info == 0) *info = base + j + 1;
         p = 1.0;
       }
@@ -419,80 +426,89 @@ __global__ void __launch_bounds__(256) k_potrf_diag(int nbs, double* A, int lda,
     const int i = t / nbs, j = t % nbs;
     A[(size_t)i * lda + j] = (j <= i) ? a[i * LD + j] : 0.0;
   }
-  if (Dinv) {
-    if (threadIdx.x < nbs) {
-      const int c = threadIdx.x;
-      for (int i = 0; i < nbs; ++i) {
-        double v = 0.0;
-        if (i >= c) {
-          double s = (i == c) ? 1.0 : 0.0;
-          for (int l = c; l < i; ++l) s -= a[i * LD + l] * x[l * LD + c];
-          v = s / a[i * LD + i];
-        }
-        x[i * LD + c] = v;
-      }
+}
+
+// Substitution solves with one NB x NB diagonal block (L in shared memory, the
+// reciprocal of its diagonal precomputed).  Solving by substitution instead of
+// multiplying with an explicitly inverted block keeps the componentwise
+// accuracy of triangular solves, which the core of the Woodbury preconditioner
+// needs late in the interior-point method.
+//   left:  op(Lbb) X = B  for a kbs x nrhs block B, one thread per column
+//   right: X Lbb^T = P    for a rows x kbs panel P, one thread per row
+__global__ void __launch_bounds__(128) k_trsm_sub_left(int kbs, bool trans, const double* __restrict__ L, int ldl,
+                                                       double* __restrict__ B, int ldb, int nrhs) {
+  __shared__ double sl[NB][NB + 1];
+  __shared__ double rd[NB];
+  for (int t = threadIdx.x; t < kbs * kbs; t += blockDim.x) {
+    const int i = t / kbs, j = t % kbs;
+    sl[i][j] = (j <= i) ? L[(size_t)i * ldl + j] : 0.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kbs; i += blockDim.x) rd[i] = 1.0 / sl[i][i];
+  __syncthreads();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nrhs) return;
+  if (!trans) {
+    for (int i = 0; i < kbs; ++i) {
+      double s = B[(size_t)i * ldb + c];
+      for (int l = 0; l < i; ++l) s = fma(-sl[i][l], B[(size_t)l * ldb + c], s);
+      B[(size_t)i * ldb + c] = s * rd[i];
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
-      const int i = t / NB, j = t % NB;
-      Dinv[(size_t)i * NB + j] = (i < nbs && j < nbs) ? x[i * LD + j] : 0.0;
+  } else {
+    for (int i = kbs - 1; i >= 0; --i) {
+      double s = B[(size_t)i * ldb + c];
+      for (int l = i + 1; l < kbs; ++l) s = fma(-sl[l][i], B[(size_t)l * ldb + c], s);
+      B[(size_t)i * ldb + c] = s * rd[i];
     }
   }
 }
-
-// Inverse of each lower-triangular diagonal block of L (one CTA per block).
-__global__ void __launch_bounds__(64) k_inv_diag(int n, const double* L, int ldl, double* Dinv) {
-  extern __shared__ double sm[];
-  constexpr int LD = NB + 1;
-  double* a = sm;             // NB x LD
-  double* x = sm + NB * LD;   // NB x LD
-  const int b = blockIdx.x, k0 = b * NB, nbs = min(NB, n - k0);
-  for (int t = threadIdx.x; t < nbs * nbs; t += blockDim.x) {
-    const int i = t / nbs, j = t % nbs;
-    a[i * LD + j] = (j <= i) ? L[(size_t)(k0 + i) * ldl + k0 + j] : 0.0;
+__global__ void __launch_bounds__(128) k_trsm_sub_right_lt(int kbs, const double* __restrict__ L, int ldl,
+                                                           double* __restrict__ P, int ldp, int rows) {
+  __shared__ double sl[NB][NB + 1];
+  __shared__ double rd[NB];
+  for (int t = threadIdx.x; t < kbs * kbs; t += blockDim.x) {
+    const int i = t / kbs, j = t % kbs;
+    sl[i][j] = (j <= i) ? L[(size_t)i * ldl + j] : 0.0;
   }
   __syncthreads();
-  if (threadIdx.x < nbs) {
-    const int c = threadIdx.x;
-    for (int i = 0; i < nbs; ++i) {
-      double v = 0.0;
-      if (i >= c) {
-        double s = (i == c) ? 1.0 : 0.0;
-        for (int l = c; l < i; ++l) s -= a[i * LD + l] * x[l * LD + c];
-        v = s / a[i * LD + i];
-      }
-      x[i * LD + c] = v;
-    }
-  }
+  for (int i = threadIdx.x; i < kbs; i += blockDim.x) rd[i] = 1.0 / sl[i][i];
   __syncthreads();
-  double* D = Dinv + (size_t)b * NB * NB;
-  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
-    const int i = t / NB, j = t % NB;
-    D[t] = (i < nbs && j < nbs) ? x[i * LD + j] : 0.0;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  double* pr = P + (size_t)r * ldp;
+  for (int j = 0; j < kbs; ++j) {
+    double s = pr[j];
+    for (int l = 0; l < j; ++l) s = fma(-pr[l], sl[j][l], s);
+    pr[j] = s * rd[j];
   }
 }
 
 size_t potrf_work_doubles(int n) { return (size_t)NB * NB + (size_t)n * NB; }
 
 void potrf(cudaStream_t st, int n, double* A, int lda, int* info_dev, double* work) {
-  const size_t smem = 2 * NB * (NB + 1) * sizeof(double);
+  potrf_floor(st, n, A, lda, info_dev, work, 0.0);
+}
+
+// Cholesky of a matrix known to satisfy A >= floor I (floor > 0): pivots below
+// floor are raised to floor and counted in info_dev[1] instead of failing.
+void potrf_floor(cudaStream_t st, int n, double* A, int lda, int* info_dev, double* work, double floor_) {
+  const size_t smem = NB * (NB + 1) * sizeof(double);
   allow_max_smem((const void*)k_potrf_diag);
-  double* Dinv = work;
-  double* tmp = work + NB * NB;   // (n) x NB panel
+  (void)work;
   ktimer_begin(st, "potrf");
-  cudaMemsetAsync(info_dev, 0, sizeof(int), st);
+  cudaMemsetAsync(info_dev, 0, 2 * sizeof(int), st);
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kbs = std::min(NB, n - k0);
     double* Akk = A + (size_t)k0 * lda + k0;
     count_launch();
-    k_potrf_diag<<<1, 256, smem, st>>>(kbs, Akk, lda, Dinv, info_dev, k0);
+    k_potrf_diag<<<1, 256, smem, st>>>(kbs, Akk, lda, info_dev, k0, floor_);
     const int r0 = k0 + kbs;
     const int rows = n - r0;
     if (rows <= 0) break;
     double* P = A + (size_t)r0 * lda + k0;
-    // panel: P <- P L_kk^{-T}
-    gemm(st, false, true, rows, kbs, kbs, 1.0, P, lda, Dinv, NB, 0.0, tmp, NB);
-    copy2d(st, rows, kbs, tmp, NB, P, lda);
+    // panel: P <- P L_kk^{-T} by substitution (row per thread)
+    count_launch();
+    k_trsm_sub_right_lt<<<cdiv(rows, 128), 128, 0, st>>>(kbs, Akk, lda, P, lda, rows);
     // trailing: A22 -= P P^T (lower tiles only)
     gemm(st, false, true, rows, rows, kbs, -1.0, P, lda, P, lda, 1.0, A + (size_t)r0 * lda + r0, lda, 1);
   }
@@ -515,21 +531,16 @@ void trsm_left_lower(cudaStream_t st, bool trans, int n, int nrhs, const double*
 // are restricted to those columns, which brings the cost from n^3 to n^3 / 3.
 void trsm_left_lower_ex(cudaStream_t st, bool trans, int n, int nrhs, const double* L, int ldl, double* B,
                         int ldb, double* work, bool lower_rhs) {
+  (void)work;
   const int nblk = (n + NB - 1) / NB;
-  double* Dinv = work;
-  double* tmp = work + (size_t)nblk * NB * NB;
   ktimer_begin(st, "trsm");
-  const size_t smem = 2 * NB * (NB + 1) * sizeof(double);
-  allow_max_smem((const void*)k_inv_diag);
-  count_launch();
-  k_inv_diag<<<nblk, 64, smem, st>>>(n, L, ldl, Dinv);
   if (!trans) {
     for (int b = 0; b < nblk; ++b) {
       const int k0 = b * NB, kbs = std::min(NB, n - k0);
       const int nc = lower_rhs ? std::min(nrhs, k0 + kbs) : nrhs;
       double* Bk = B + (size_t)k0 * ldb;
-      gemm(st, false, false, kbs, nc, kbs, 1.0, Dinv + (size_t)b * NB * NB, NB, Bk, ldb, 0.0, tmp, nrhs);
-      copy2d(st, kbs, nc, tmp, nrhs, Bk, ldb);
+      count_launch();
+      k_trsm_sub_left<<<cdiv(nc, 128), 128, 0, st>>>(kbs, false, L + (size_t)k0 * ldl + k0, ldl, Bk, ldb, nc);
       const int r0 = k0 + kbs;
       if (r0 < n)
         gemm(st, false, false, n - r0, nc, kbs, -1.0, L + (size_t)r0 * ldl + k0, ldl, Bk, ldb, 1.0,
@@ -539,8 +550,8 @@ void trsm_left_lower_ex(cudaStream_t st, bool trans, int n, int nrhs, const doub
     for (int b = nblk - 1; b >= 0; --b) {
       const int k0 = b * NB, kbs = std::min(NB, n - k0);
       double* Bk = B + (size_t)k0 * ldb;
-      gemm(st, true, false, kbs, nrhs, kbs, 1.0, Dinv + (size_t)b * NB * NB, NB, Bk, ldb, 0.0, tmp, nrhs);
-      copy2d(st, kbs, nrhs, tmp, nrhs, Bk, ldb);
+      count_launch();
+      k_trsm_sub_left<<<cdiv(nrhs, 128), 128, 0, st>>>(kbs, true, L + (size_t)k0 * ldl + k0, ldl, Bk, ldb, nrhs);
       if (k0 > 0)
         gemm(st, true, false, k0, nrhs, kbs, -1.0, L + (size_t)k0 * ldl, ldl, Bk, ldb, 1.0, B, ldb);
     }

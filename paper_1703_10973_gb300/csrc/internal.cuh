@@ -87,6 +87,8 @@ void gemm_f32(cudaStream_t st, bool tA, bool tB, int M, int N, int K, float alph
 // work: at least potrf_work_doubles(n) doubles.
 size_t potrf_work_doubles(int n);
 void potrf(cudaStream_t st, int n, double* A, int lda, int* info_dev, double* work);
+// info_dev needs 2 ints; info_dev[1] counts pivots raised to floor.
+void potrf_floor(cudaStream_t st, int n, double* A, int lda, int* info_dev, double* work, double floor_);
 
 // Triangular solves with a lower-triangular L (n x n), in place on B (n x nrhs):
 // trans == false: B <- L^{-1} B;  trans == true: B <- L^{-T} B.
@@ -227,8 +229,11 @@ struct sdp_problem {
   // ---- preconditioner ----
   bool pc_valid = false;
   double tau = 0;
-  double core_shift = 0;   // diagonal of the factored core (tau^2, or more after a retry)
+  double core_shift = 0;   // diagonal added to the core (tau^2)
+  int core_floor_pivots = 0;  // pivots raised to tau^2 in the last core Cholesky
   int kpc = 0;             // split rank used
+  bool pc_hat = false;     // built as Hhat (Z = sqrt(2 tau) I, eq. sparse_prec)
+  double zscale = 0;       // sqrt(2 tau)
   double* U = nullptr;     // n*k
   double* Z = nullptr;     // n*n
   double* Sc = nullptr;    // nk*nk core, then its Cholesky factor

@@ -18,20 +18,35 @@ namespace sdpgb {
 
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
-enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6, S_IT = 7, S_MAXIT = 8 };
+enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6, S_IT = 7, S_MAXIT = 8, S_BRK = 9 };
+
+// A breakdown (p.q or r.z not positive and finite: rounding has made the
+// preconditioned operator indefinite in some direction) leaves x and r at the
+// last good iterate, sets scal[S_BRK] and ends the loop; the restarted outer
+// solve then continues from the true residual.
 
 // x += a p ; r -= a q  with a = rz / pq
 __global__ void k_pcg_xr(int m, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                         const double* __restrict__ q, const double* __restrict__ scal) {
-  const double a = scal[S_RZ] / scal[S_PQ];
+                         const double* __restrict__ q, double* scal) {
+  const double pq = scal[S_PQ], rz = scal[S_RZ];
+  if (!(pq > 0.0 && rz > 0.0 && isfinite(pq) && isfinite(rz))) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_BRK] = 1.0;
+    return;
+  }
+  const double a = rz / pq;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     x[i] = fma(a, p[i], x[i]);
     r[i] = fma(-a, q[i], r[i]);
   }
 }
 // p = z + beta p  with beta = rz_new / rz
-__global__ void k_pcg_p(int m, double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ scal) {
-  const double beta = scal[S_RZN] / scal[S_RZ];
+__global__ void k_pcg_p(int m, double* __restrict__ p, const double* __restrict__ z, double* scal) {
+  const double rzn = scal[S_RZN], rz = scal[S_RZ];
+  if (!(rzn > 0.0 && isfinite(rzn) && rz > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_BRK] = 1.0;
+    return;
+  }
+  const double beta = rzn / rz;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) p[i] = fma(beta, p[i], z[i]);
 }
 
@@ -73,7 +88,7 @@ __global__ void k_pcg_check(int np, const double* __restrict__ part, double* sca
       scal[S_RR] = s;
       const double it = scal[S_IT] + 1.0;
       scal[S_IT] = it;
-      const bool go = (s > scal[S_TOL2]) && (it < scal[S_MAXIT]) && isfinite(s);
+      const bool go = (s > scal[S_TOL2]) && (it < scal[S_MAXIT]) && isfinite(s) && scal[S_BRK] == 0.0;
       cudaGraphSetConditional(cond, go ? 1u : 0u);
     }
   }
@@ -83,6 +98,7 @@ __global__ void k_pcg_init(double* scal, double rtol, int maxit) {
   scal[S_TOL2] = rtol * rtol * scal[S_NR0];
   scal[S_IT] = 0.0;
   scal[S_MAXIT] = (double)maxit;
+  scal[S_BRK] = 0.0;
 }
 
 static sdp_status pcg_alloc(sdp_problem* h) {
@@ -183,7 +199,7 @@ static double read_scalar(sdp_problem* h, const double* dev) {
 // Plain PCG from x = 0 in precision prec; x receives the iterate.  *rel is the
 // recursive relative residual at exit.
 static sdp_status pcg_core(sdp_problem* h, const double* rhs, double* x, double rtol, int maxit, int prec,
-                           int* iters, double* rel) {
+                           int* iters, double* rel, bool* brk) {
   cudaStream_t st = h->stream;
   const int m = h->m;
   double* scal = h->scal;
@@ -200,6 +216,7 @@ static sdp_status pcg_core(sdp_problem* h, const double* rhs, double* x, double 
     SDP_CK(h, cudaMemsetAsync(x, 0, m * sizeof(double), st));
     *iters = 0;
     *rel = 0.0;
+    if (brk) *brk = false;
     return SDP_OK;
   }
   SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec));
@@ -208,8 +225,8 @@ static sdp_status pcg_core(sdp_problem* h, const double* rhs, double* x, double 
   count_launch();
   k_pcg_init<<<1, 1, 0, st>>>(scal, rtol, maxit);
   SDP_CK(h, cudaGraphLaunch(h->pcg_exec, st));
-  double v[9];
-  SDP_CK(h, cudaMemcpyAsync(v, scal, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double v[10];
+  SDP_CK(h, cudaMemcpyAsync(v, scal, 10 * sizeof(double), cudaMemcpyDeviceToHost, st));
   SDP_CK(h, cudaStreamSynchronize(st));
   SDP_CK(h, cudaMemcpyAsync(x, h->px, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const int its = (int)v[S_IT];
@@ -217,6 +234,7 @@ static sdp_status pcg_core(sdp_problem* h, const double* rhs, double* x, double 
   const double rr = v[S_RR];
   *iters = its;
   *rel = std::sqrt(rr / nr0sq);
+  if (brk) *brk = (v[S_BRK] != 0.0);
   if (!std::isfinite(rr)) {
     h->last_error = "pcg: non-finite residual";
     return SDP_ERR_NUMERIC;
@@ -263,9 +281,11 @@ sdp_status pcg_impl(sdp_problem* h, const double* r, double* y, double rtol, int
     int it = 0;
     double rr = 0.0;
     const int budget = std::max(1, std::min(maxit - total, 500));
-    sdp_status s = pcg_core(h, resid, corr, inner, budget, prec, &it, &rr);
+    bool brk = false;
+    sdp_status s = pcg_core(h, resid, corr, inner, budget, prec, &it, &rr, &brk);
     total += it;
     if (s != SDP_OK && s != SDP_ERR_MAXIT) return s;
+    if (brk && it <= 1) break;   // breakdown before any progress: keep the best iterate
     if (it > 0) axpby(st, m, 1.0, y, 1.0, corr, y);
     SDP_TRY(true_residual(h, r, y, resid, &tr));
     if (!std::isfinite(tr)) {

@@ -14,6 +14,13 @@
 //
 // Apply (eq. SMW2):  t = G^{-1} r;  u = UU^T t = Z^T (sum t_i A_i) U;
 //   s = L^{-T} L^{-1} u;  z = tau^{-2} G^{-1} (r - UU s),  (UU s)_i = A_i . (Z S U^T).
+//
+// Section V's Hhat = A^T (tau^2 I + 2 tau U U^T kron I) A (eq. sparse_prec) is
+// the same construction with Z = sqrt(2 tau) I: the core blocks become
+// tau^2 delta_ll' I + 2 tau K_ll' (K scattered, no dense GEMM), and both Z
+// products of the apply become scalings.  Near the optimum the Algorithm 1
+// core has condition number ~ (lambda_max(W) / tau)^2, beyond FP64 once
+// mu ~ 1e-5, while the Hhat core stays near lambda_max(W) / tau.
 #include "internal.cuh"
 
 #include <algorithm>
@@ -95,6 +102,35 @@ __global__ void k_apply_tail(int m, int k, const int* __restrict__ eptr, const i
     }
   }
   z[i] = ginv[i] * inv_tau2 * (r[i] - us);
+}
+
+// Sc[l n + a][l2 n + b] = alpha K_ll2[a][b] for every stored slot (a, b) of K;
+// for l != l2 the mirror entry of block (l2, l) as well.  One CTA per row a.
+__global__ void k_scatter_K(int n, int nk, const int* __restrict__ krowptr, const int* __restrict__ kcol,
+                            const double* __restrict__ Kval, int l, int l2, double alpha, double* __restrict__ Sc) {
+  const int a = blockIdx.x;
+  if (a >= n) return;
+  for (int s = krowptr[a] + threadIdx.x; s < krowptr[a + 1]; s += blockDim.x) {
+    const int b = kcol[s];
+    const double v = alpha * Kval[s];
+    Sc[(size_t)(l * n + a) * nk + (size_t)l2 * n + b] = v;
+    if (l != l2) Sc[(size_t)(l2 * n + b) * nk + (size_t)l * n + a] = v;
+  }
+}
+
+// out[l n + c] = alpha in[c k + l]   (n x k  ->  k x n)
+__global__ void k_nk_to_kn(int n, int k, double alpha, const double* __restrict__ in, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int l = t / n, c = t % n;
+  out[t] = alpha * in[(size_t)c * k + l];
+}
+// out[c k + l] = alpha in[l n + c]   (k x n  ->  n x k)
+__global__ void k_kn_to_nk(int n, int k, double alpha, const double* __restrict__ in, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int c = t / k, l = t % k;
+  out[t] = alpha * in[(size_t)l * n + c];
 }
 
 __global__ void k_scale_ginv(int m, const double* __restrict__ ginv, const double* __restrict__ r, double s,
@@ -353,25 +389,20 @@ static void form_core(sdp_problem* h, int k, double shift) {
   if (shift != 0.0) add_diag(st, nk, h->Sc, nk, shift);
 }
 
-__global__ void k_max_diag(int n, const double* A, int lda, double* out) {
-  __shared__ double sh[256];
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v = fmax(v, fabs(A[(size_t)i * lda + i]));
-  sh[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
-    __syncthreads();
+// Hhat core: Sc = tau^2 I + 2 tau K (blocks l, l'), K on its sparse pattern.
+static void form_core_hat(sdp_problem* h, int k, double tau) {
+  cudaStream_t st = h->stream;
+  const int n = h->n, nk = n * k;
+  fill(st, h->Sc, (size_t)nk * nk, 0.0);
+  for (int l = 0; l < k; ++l) {
+    for (int l2 = l; l2 < k; ++l2) {
+      count_launch(2);
+      k_kvals<<<cdiv(h->nnzK, 256), 256, 0, st>>>(h->nnzK, h->kptr, h->kcon, h->kcra, h->kcrb, h->ginv, h->au,
+                                                 k, l, l2, h->Kval);
+      k_scatter_K<<<n, 128, 0, st>>>(n, nk, h->krowptr, h->kcol, h->Kval, l, l2, 2.0 * tau, h->Sc);
+    }
   }
-  if (threadIdx.x == 0) out[0] = sh[0];
-}
-
-static sdp_status max_diag(sdp_problem* h, const double* A, int n, double* out) {
-  count_launch();
-  k_max_diag<<<1, 256, 0, h->stream>>>(n, A, n, h->tau_dev + 4);
-  SDP_CK(h, cudaMemcpyAsync(out, h->tau_dev + 4, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  SDP_CK(h, cudaStreamSynchronize(h->stream));
-  return SDP_OK;
+  add_diag(st, nk, h->Sc, nk, tau * tau);
 }
 
 sdp_status precond_build_impl(sdp_problem* h) {
@@ -419,37 +450,39 @@ sdp_status precond_build_impl(sdp_problem* h) {
     h->pc_generation++;
     return SDP_OK;
   }
-  // ---- step 1b: U and Z = chol(2W - U U^T)
+  const bool hat = (h->prm.precond == SDP_PRECOND_HAT);
+  h->pc_hat = hat;
+  h->zscale = std::sqrt(2.0 * tau);
+  // ---- step 1b: U, and Z = chol(2W - U U^T) (Algorithm 1) or sqrt(2 tau) I (Hhat)
   count_launch();
   k_make_U<<<cdiv((size_t)n * k, 256), 256, 0, st>>>(n, k, h->Etop, h->wtop, h->tau_dev, h->U);
-  axpby(st, (size_t)n * n, 2.0, h->W, 0.0, nullptr, h->Z);
-  gemm(st, false, true, n, n, k, -1.0, h->U, k, h->U, k, 1.0, h->Z, n);
-  potrf(st, n, h->Z, n, h->info, h->work);
-  SDP_TRY(read_info(h, "precond_build: chol(2 W0 + U U^T)"));
+  if (!hat) {
+    axpby(st, (size_t)n * n, 2.0, h->W, 0.0, nullptr, h->Z);
+    gemm(st, false, true, n, n, k, -1.0, h->U, k, h->U, k, 1.0, h->Z, n);
+    potrf(st, n, h->Z, n, h->info, h->work);
+    SDP_TRY(read_info(h, "precond_build: chol(2 W0 + U U^T)"));
+  }
   // ---- step 2: core S = tau^2 I + Z^T K Z (block l, l'), Cholesky, inverse
   count_launch();
   k_au<<<cdiv(h->ncr, 256), 256, 0, st>>>(h->ncr, k, h->crlist_ptr, h->crlist_col, h->crlist_coef, h->U, h->au);
-  // When nk > m (or near the optimum) UU^T G^{-1} UU is singular or nearly so and
-  // the core's smallest eigenvalue is tau^2 itself; if the FP64 Cholesky then
-  // meets a non-positive pivot, the core is rebuilt with tau^2 + delta on the
-  // diagonal.  S + delta I is the Woodbury core of tau^2 G + c UU UU^T with
-  // c = tau^2 / (tau^2 + delta) < 1, still a symmetric positive definite
-  // preconditioner, so PCG still converges to the exact Newton direction.
-  double shift = tau * tau;
-  sdp_status fs = SDP_OK;
-  for (int attempt = 0; attempt < 8; ++attempt) {
-    form_core(h, k, shift);
-    potrf(st, nk, h->Sc, nk, h->info, h->work);
-    fs = read_info(h, "precond_build: chol(core)");
-    if (fs == SDP_OK) break;
-    if (fs != SDP_ERR_NOT_PD) return fs;
-    form_core(h, k, 0.0);
-    double dmax = 0.0;
-    SDP_TRY(max_diag(h, h->Sc, nk, &dmax));
-    shift = std::max(shift * 100.0, tau * tau + 1e-14 * dmax * std::pow(100.0, attempt));
+  // S = tau^2 I + UU^T G^{-1} UU >= tau^2 I exactly, so every Cholesky pivot of
+  // S is at least tau^2.  Near the optimum S is ill conditioned (kappa ~
+  // (lambda_max(W) / tau)^2) and FP64 rounding in its formation can push a pivot
+  // below that bound or below zero; such pivots are raised to tau^2 (a
+  // modified Cholesky with the bound the mathematics gives), which keeps the
+  // factor of an SPD matrix close to S in every direction.
+  if (hat)
+    form_core_hat(h, k, tau);
+  else
+    form_core(h, k, tau * tau);
+  potrf_floor(st, nk, h->Sc, nk, h->info, h->work, tau * tau);
+  {
+    int inf2[2] = {0, 0};
+    SDP_CK(h, cudaMemcpyAsync(inf2, h->info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SDP_CK(h, cudaStreamSynchronize(st));
+    h->core_floor_pivots = inf2[1];
   }
-  SDP_TRY(fs);
-  h->core_shift = shift;
+  h->core_shift = tau * tau;
   fill(st, h->Linv, (size_t)nk * nk, 0.0);
   add_diag(st, nk, h->Linv, nk, 1.0);
   trsm_left_lower_ex(st, false, nk, nk, h->Sc, nk, h->Linv, nk, h->work, true);
@@ -471,8 +504,12 @@ sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int pr
   // u = Z^T (sum g_i r_i A_i) U, stored as k x n (row l = column l of u)
   assemble_V(h, r, h->ginv, h->pvec);
   spmm_rows(h, h->pvec, h->U, k, k, h->Bn, k);
-  if (!ts_product(st, n, k, h->Bn, h->Z, h->trpart, h->uvec, nullptr, nullptr, true))
+  if (h->pc_hat) {
+    count_launch();
+    k_nk_to_kn<<<cdiv((size_t)nk, 256), 256, 0, st>>>(n, k, h->zscale, h->Bn, h->uvec);
+  } else if (!ts_product(st, n, k, h->Bn, h->Z, h->trpart, h->uvec, nullptr, nullptr, true)) {
     gemm(st, true, false, k, n, n, 1.0, h->Bn, k, h->Z, n, 0.0, h->uvec, n);
+  }
   // s = L^{-T} L^{-1} u.  Multiplying by the stored inverse alone loses accuracy
   // once the core is ill conditioned (kappa(L) eps, late interior-point
   // iterations), so each triangular solve takes one step of iterative refinement
@@ -489,8 +526,12 @@ sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int pr
     std::swap(h->uvec, h->uvec2);   // result becomes the input of the next solve
   }
   // ZS = Z S_mat with S_mat[c][l] = s[l n + c]
-  if (!ts_product(st, n, k, nullptr, h->Z, nullptr, nullptr, h->uvec, h->Bn, false))
+  if (h->pc_hat) {
+    count_launch();
+    k_kn_to_nk<<<cdiv((size_t)nk, 256), 256, 0, st>>>(n, k, h->zscale, h->uvec, h->Bn);
+  } else if (!ts_product(st, n, k, nullptr, h->Z, nullptr, nullptr, h->uvec, h->Bn, false)) {
     gemm(st, false, true, n, k, n, 1.0, h->Z, n, h->uvec, n, 0.0, h->Bn, k);
+  }
   count_launch();
   k_apply_tail<<<cdiv(m, 256), 256, 0, st>>>(m, k, h->eptr, h->ep, h->eq, h->ecoef, h->Bn, h->U, h->ginv, r,
                                              inv_tau2, z);

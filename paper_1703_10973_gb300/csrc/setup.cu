@@ -48,7 +48,7 @@ extern "C" void sdp_default_params(sdp_params* p) {
   p->k = 0;
   p->step_frac = 0.9;
   p->prec = SDP_FP64;
-  p->precond = SDP_PRECOND_WOODBURY;
+  p->precond = SDP_PRECOND_HAT;
   p->inner_rtol = 1e-4;
   p->verbose = 0;
 }

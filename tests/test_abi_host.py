@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol():
 def test_default_params():
     from paper_1703_10973_gb300 import default_params
     p = default_params()
-    assert p.gap_tol == 1e-6 and p.pcg_rtol == 1e-8 and p.step_frac == 0.9 and p.precond == 1
+    assert p.gap_tol == 1e-6 and p.pcg_rtol == 1e-8 and p.step_frac == 0.9 and p.precond == 2   # Hhat of Section V
 
 
 def _setup(n, m, C_trip, A_trip, b, k=1):
