@@ -215,7 +215,7 @@ def run(args):
     load()
     insts, desc = workload(args.workload, args.batch)
     kk = 8 if args.workload == "C2" else 0
-    params = default_params(prec=args.prec, k=kk, pcg_maxit=args.pcg_maxit)
+    params = default_params(prec=args.prec, k=kk, pcg_maxit=args.pcg_maxit, pcg_graph=args.pcg_graph)
     nstreams = min(args.streams, len(insts))
     streams = [torch.cuda.Stream() for _ in range(nstreams)]
     probs = [SDPProblem.from_data(d, params=params, stream=streams[i % nstreams].cuda_stream)
@@ -368,7 +368,7 @@ def run(args):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else args.prec,
                 "data": "synthetic",
-                "config": {"workload": desc, "instances": len(insts), "streams": nstreams, "prec": args.prec,
+                "config": {"workload": desc, "instances": len(insts), "streams": nstreams, "prec": args.prec, "pcg_loop": "graph" if args.pcg_graph else "host",
                            "parallelism": f"replicas{ws}", "l2_flush": True, "converged": converged,
                            "ipm_iters_mean": float(np.mean(ipm_iters)),
                            "pcg_iters_per_solve_mean": float(np.mean(pcg_iters)),
@@ -398,6 +398,8 @@ def main():
     ap.add_argument("--timed-kernel", default="sytrd")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pcg-graph", type=int, default=1, choices=[0, 1],
+                    help="0: host-driven PCG loop (same kernels; for profilers without conditional-graph support)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

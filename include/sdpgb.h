@@ -73,6 +73,10 @@ typedef struct {
   int precond;         /* sdp_precond_kind; SDP_PRECOND_HAT                        */
   double inner_rtol;   /* PCG tolerance of one restart (sweep); 1e-4                */
   int verbose;         /* 1 = one line per IPM iteration on stderr                 */
+  int pcg_graph;       /* 1 = the PCG loop runs on the device as a CUDA graph with */
+                       /* a conditional while node (default); 0 = host-driven     */
+                       /* loop launching the same kernels (for profilers that do  */
+                       /* not support conditional graph nodes)                    */
 } sdp_params;
 
 typedef struct {

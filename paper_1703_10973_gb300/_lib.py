@@ -33,6 +33,7 @@ class sdp_params(C.Structure):
         ("precond", C.c_int),
         ("inner_rtol", C.c_double),
         ("verbose", C.c_int),
+        ("pcg_graph", C.c_int),
     ]
 
 

@@ -12,6 +12,7 @@
 namespace sdpgb {
 
 std::atomic<int64_t> g_launches{0};
+thread_local int64_t t_launches = 0;
 
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 

@@ -45,7 +45,11 @@ struct Err {
 // Launch accounting: every kernel launch in the library increments this counter
 // (per process); sdp_launch_count() reports it per handle via a snapshot.
 extern std::atomic<int64_t> g_launches;
-inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+extern thread_local int64_t t_launches;   // this host thread's launches (graph capture accounting)
+inline void count_launch(int k = 1) {
+  g_launches.fetch_add(k, std::memory_order_relaxed);
+  t_launches += k;
+}
 
 // Optional event timing of one kernel class (sdp_timing_enable / sdp_timing_read).
 // ktimer_begin/ktimer_end bracket a launch; they do nothing unless `cls` is the

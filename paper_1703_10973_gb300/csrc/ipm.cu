@@ -75,12 +75,14 @@ static sdp_status chol_checked(sdp_problem* h, const double* src, double* L, con
 static sdp_status max_step(sdp_problem* h, const double* Lf, const double* D, double* alpha) {
   cudaStream_t st = h->stream;
   const int n = h->n;
+  ktimer_begin(st, "max_step");
   copy2d(st, n, n, D, n, h->M1, n);
   trsm_left_lower(st, false, n, n, Lf, n, h->M1, n, h->work);   // Lf^{-1} D
   transpose(st, n, n, h->M1, n, h->M2, n);                      // D Lf^{-T}
   trsm_left_lower(st, false, n, n, Lf, n, h->M2, n, h->work);   // Lf^{-1} D Lf^{-T}
   symmetrize_avg(st, n, h->M2, n);
   SDP_TRY(eig_min(st, n, h->M2, h->scal + R_LMIN, &h->eig));
+  ktimer_end(st, "max_step", 0.0, 0.0);
   double lmin = 0.0;
   SDP_CK(h, cudaMemcpyAsync(&lmin, h->scal + R_LMIN, sizeof(double), cudaMemcpyDeviceToHost, st));
   SDP_CK(h, cudaStreamSynchronize(st));
@@ -298,14 +300,18 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   // ---- NT scaling
   SDP_TRY(chol_checked(h, h->X, h->L, "ipm_step: chol(X)"));
   const int fb0 = h->nt_fallbacks;
+  ktimer_begin(st, "nt_scaling");
   SDP_TRY(nt_scaling(h));
+  ktimer_end(st, "nt_scaling", 0.0, 0.0);
   inf.nt_fallback = h->nt_fallbacks - fb0;
   h->have_W = true;
   h->W32_valid = h->W16_valid = false;
   h->pc_valid = false;
 
   // ---- preconditioner (Algorithm 1 steps 1-2)
+  ktimer_begin(st, "precond_build");
   SDP_TRY(precond_build_impl(h));
+  ktimer_end(st, "precond_build", 0.0, 0.0);
   inf.tau = h->tau;
   SDP_TRY(chol_checked(h, h->S, h->Rs, "ipm_step: chol(S)"));
 

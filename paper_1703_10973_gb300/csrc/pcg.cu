@@ -18,7 +18,7 @@ namespace sdpgb {
 
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
-enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6, S_IT = 7, S_MAXIT = 8, S_BRK = 9 };
+enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6, S_IT = 7, S_MAXIT = 8, S_BRK = 9, S_GO = 10 };
 
 // A breakdown (p.q or r.z not positive and finite: rounding has made the
 // preconditioned operator indefinite in some direction) leaves x and r at the
@@ -74,7 +74,9 @@ __global__ void k_pcg_sum(int np, const double* __restrict__ part, double* scal,
   }
 }
 // ||r||^2 from the partials, iteration count, and the loop condition.
-__global__ void k_pcg_check(int np, const double* __restrict__ part, double* scal, cudaGraphConditionalHandle cond) {
+// With use_cond = 0 (host-driven loop) the decision is only stored in scal[S_GO].
+__global__ void k_pcg_check(int np, const double* __restrict__ part, double* scal, cudaGraphConditionalHandle cond,
+                            int use_cond) {
   __shared__ double sh[32];
   double s = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
@@ -89,7 +91,8 @@ __global__ void k_pcg_check(int np, const double* __restrict__ part, double* sca
       const double it = scal[S_IT] + 1.0;
       scal[S_IT] = it;
       const bool go = (s > scal[S_TOL2]) && (it < scal[S_MAXIT]) && isfinite(s) && scal[S_BRK] == 0.0;
-      cudaGraphSetConditional(cond, go ? 1u : 0u);
+      scal[S_GO] = go ? 1.0 : 0.0;
+      if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
     }
   }
 }
@@ -119,7 +122,7 @@ static sdp_status pcg_alloc(sdp_problem* h) {
 static void dot_part_only(cudaStream_t st, size_t count, const double* x, const double* y, double* part);
 
 // One PCG iteration on h->stream (the body of the device-side loop).
-static sdp_status pcg_body(sdp_problem* h, int prec, cudaGraphConditionalHandle cond) {
+static sdp_status pcg_body(sdp_problem* h, int prec, cudaGraphConditionalHandle cond, bool use_cond) {
   cudaStream_t st = h->stream;
   const int m = h->m;
   const unsigned g = std::min(cdiv(m, 256), 2048u);
@@ -130,7 +133,7 @@ static sdp_status pcg_body(sdp_problem* h, int prec, cudaGraphConditionalHandle 
   k_pcg_sum<<<1, 512, 0, st>>>(np, h->part, h->scal, S_PQ, 1);
   k_pcg_xr<<<g, 256, 0, st>>>(m, h->px, h->pr, h->pp, h->pq, h->scal);
   dot_part_only(st, m, h->pr, h->pr, h->part);
-  k_pcg_check<<<1, 512, 0, st>>>(np, h->part, h->scal, cond);
+  k_pcg_check<<<1, 512, 0, st>>>(np, h->part, h->scal, cond, use_cond ? 1 : 0);
   SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec));
   dot_part_only(st, m, h->pr, h->pz, h->part);
   count_launch(2);
@@ -168,15 +171,16 @@ static sdp_status pcg_graph(sdp_problem* h, int prec) {
   cudaGraph_t body = np.conditional.phGraph_out[0];
   cudaStream_t user = h->stream;
   h->stream = h->capture_stream;
-  const int64_t l0 = g_launches.load();
+  const int64_t l0 = t_launches;
   ktimer_pause(true);
   cudaError_t e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  sdp_status s = (e == cudaSuccess) ? pcg_body(h, prec, cond) : SDP_ERR_CUDA;
+  sdp_status s = (e == cudaSuccess) ? pcg_body(h, prec, cond, true) : SDP_ERR_CUDA;
   cudaGraph_t out = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(h->stream, &out);
   ktimer_pause(false);
-  h->pcg_body_launches = g_launches.load() - l0;
+  h->pcg_body_launches = t_launches - l0;   // captured, not launched: counted per iteration instead
   g_launches.fetch_sub(h->pcg_body_launches);
+  t_launches = l0;
   h->stream = user;
   if (e != cudaSuccess || e2 != cudaSuccess || s != SDP_OK) {
     cudaGraphDestroy(g);
@@ -203,7 +207,9 @@ static sdp_status pcg_core(sdp_problem* h, const double* rhs, double* x, double 
   cudaStream_t st = h->stream;
   const int m = h->m;
   double* scal = h->scal;
-  SDP_TRY(pcg_graph(h, prec));
+  const bool use_graph = h->prm.pcg_graph != 0;
+  if (use_graph) SDP_TRY(pcg_graph(h, prec));
+  else SDP_TRY(ensure_lowprec_W(h, prec));
   SDP_CK(h, cudaMemcpyAsync(h->pr, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   SDP_CK(h, cudaMemsetAsync(h->px, 0, m * sizeof(double), st));
   dot(st, m, h->pr, h->pr, scal + S_NR0, h->part);
@@ -224,13 +230,22 @@ static sdp_status pcg_core(sdp_problem* h, const double* rhs, double* x, double 
   dot(st, m, h->pr, h->pz, scal + S_RZ, h->part);
   count_launch();
   k_pcg_init<<<1, 1, 0, st>>>(scal, rtol, maxit);
-  SDP_CK(h, cudaGraphLaunch(h->pcg_exec, st));
-  double v[10];
-  SDP_CK(h, cudaMemcpyAsync(v, scal, 10 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  SDP_CK(h, cudaStreamSynchronize(st));
+  double v[11];
+  if (use_graph) {
+    SDP_CK(h, cudaGraphLaunch(h->pcg_exec, st));
+    SDP_CK(h, cudaMemcpyAsync(v, scal, 11 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SDP_CK(h, cudaStreamSynchronize(st));
+  } else {
+    // the same body, launched from the host one iteration at a time
+    do {
+      SDP_TRY(pcg_body(h, prec, cudaGraphConditionalHandle{}, false));
+      SDP_CK(h, cudaMemcpyAsync(v, scal, 11 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SDP_CK(h, cudaStreamSynchronize(st));
+    } while (v[S_GO] != 0.0);
+  }
   SDP_CK(h, cudaMemcpyAsync(x, h->px, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const int its = (int)v[S_IT];
-  g_launches.fetch_add((int64_t)its * h->pcg_body_launches);
+  if (use_graph) g_launches.fetch_add((int64_t)its * h->pcg_body_launches);
   const double rr = v[S_RR];
   *iters = its;
   *rel = std::sqrt(rr / nr0sq);
@@ -257,8 +272,17 @@ static sdp_status true_residual(sdp_problem* h, const double* r, const double* y
   return SDP_OK;
 }
 
+static sdp_status pcg_impl_(sdp_problem* h, const double* r, double* y, double rtol, int maxit, int prec,
+                            int* iters, double* relres);
 sdp_status pcg_impl(sdp_problem* h, const double* r, double* y, double rtol, int maxit, int prec, int* iters,
                     double* relres) {
+  ktimer_begin(h->stream, "pcg");
+  sdp_status s = pcg_impl_(h, r, y, rtol, maxit, prec, iters, relres);
+  ktimer_end(h->stream, "pcg", 0.0, 0.0);
+  return s;
+}
+static sdp_status pcg_impl_(sdp_problem* h, const double* r, double* y, double rtol, int maxit, int prec,
+                            int* iters, double* relres) {
   SDP_TRY(pcg_alloc(h));
   if (!h->pc_valid) SDP_TRY(precond_build_impl(h));
   cudaStream_t st = h->stream;

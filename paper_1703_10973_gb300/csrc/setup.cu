@@ -51,6 +51,7 @@ extern "C" void sdp_default_params(sdp_params* p) {
   p->precond = SDP_PRECOND_HAT;
   p->inner_rtol = 1e-4;
   p->verbose = 0;
+  p->pcg_graph = 1;
 }
 
 extern "C" const char* sdp_status_str(sdp_status s) {

@@ -49,7 +49,7 @@ void drain() {
 }
 }  // namespace
 
-bool g_paused = false;
+thread_local bool g_paused = false;   // per host thread: set while this thread captures a graph
 bool ktimer_on(const char* cls) { return !g_paused && !g_cls.empty() && g_cls == cls; }
 void ktimer_pause(bool paused) { g_paused = paused; }
 

@@ -209,6 +209,22 @@ def test_pcg_matches_direct_solve(mu, kind):
     assert its <= 60
 
 
+def test_pcg_host_loop_matches_graph_loop():
+    """The host-driven PCG loop launches the same kernels as the graph's while node."""
+    d = si.mc_instance(12, 14, 2, 100, 10)
+    W = _ipm_like_W(d.n, 2, 1e-4, 4)
+    r = si.random_vec(d.m, 5)
+    out = []
+    for g in (1, 0):
+        with _prob(d, pcg_graph=g) as prob:
+            prob.set_W(_dev(W))
+            prob.precond_build()
+            y, its, rel, st = prob.pcg_solve(_dev(r), rtol=1e-10, maxit=500)
+            out.append((y.cpu().numpy(), its, rel))
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
+
+
 @pytest.mark.parametrize("prec,mu", [("fp32", 1e-3), ("bf16", 1e-1)])
 def test_pcg_reduced_precision_refined_to_fp64(prec, mu):
     d = si.mc_instance(12, 14, 2, 100, 10)
