@@ -216,9 +216,36 @@ sdp_status sdp_timing_read(sdp_problem* h, double* ms, int64_t* launches, double
 /* Number of kernel launches issued by this handle since setup (for accounting). */
 int64_t sdp_launch_count(const sdp_problem* h);
 
+/*
+ * sdp_hessian_matvec_static -- handle-free, allocation-free variant of
+ * sdp_hessian_matvec.  This call is an addition of this library for callers
+ * that cannot allocate device memory; the paper has no counterpart.
+ *
+ * Computes Hv_dev[k] = A_k . (W V W), V = sum_j v_dev[j] A_j (eq. hesseqn2) in
+ * FP64 from the constraint triplets (same convention as sdp_setup: (k, i, j, v)
+ * sets (A_k)_ij = (A_k)_ji = v, duplicates add), all in device memory:
+ *   Ak_dev, Ai_dev, Aj_dev: int32[nnzA];  Av_dev: double[nnzA];
+ *   W_dev: double[n*n], symmetric, row-major;  v_dev: double[m];
+ *   Hv_dev: double[m], overwritten (cleared first).
+ * Scratch: two n x n FP64 matrices in a static __device__ array of this
+ * library (SDP_STATIC_MAX_N^2 * 16 bytes = 4 MiB); nothing is allocated.
+ * n > SDP_STATIC_MAX_N returns SDP_ERR_ARG before any launch.  Triplets with
+ * an index out of range are skipped by the kernels, counted, and make the call
+ * return SDP_ERR_ARG.  The call synchronises cuda_stream once, to read that
+ * count.  The first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress), which can load the module: make that first call
+ * before capturing any stream.  Calls whose executions overlap (several
+ * streams or host threads) share the scratch and race: serialise them.
+ * Error text for this call: sdp_last_error(NULL), per host thread.
+ */
+#define SDP_STATIC_MAX_N 512
+sdp_status sdp_hessian_matvec_static(int n, int m, int64_t nnzA, const int32_t* Ak_dev, const int32_t* Ai_dev,
+                                     const int32_t* Aj_dev, const double* Av_dev, const double* W_dev,
+                                     const double* v_dev, double* Hv_dev, void* cuda_stream);
+
 void sdp_destroy(sdp_problem* h);
 const char* sdp_status_str(sdp_status s);
-const char* sdp_last_error(const sdp_problem* h);
+const char* sdp_last_error(const sdp_problem* h);   /* NULL: the last handle-free call */
 
 #ifdef __cplusplus
 }

@@ -14,6 +14,7 @@ from ._build import LIB
 SDP_OK, SDP_ERR_ARG, SDP_ERR_OOM, SDP_ERR_NOT_PD, SDP_ERR_MAXIT = 0, 1, 2, 3, 4
 SDP_ERR_UNSUPPORTED, SDP_ERR_NUMERIC, SDP_ERR_TIMEOUT, SDP_ERR_CUDA = 5, 6, 7, 8
 SDP_FP64, SDP_FP32, SDP_BF16 = 0, 1, 2
+SDP_STATIC_MAX_N = 512
 SDP_PRECOND_DIAG, SDP_PRECOND_WOODBURY, SDP_PRECOND_HAT = 0, 1, 2
 
 PREC = {"fp64": SDP_FP64, "fp32": SDP_FP32, "bf16": SDP_BF16}
@@ -98,6 +99,7 @@ SIGNATURES = {
     "sdp_reset": (C.c_int, [_P]),
     "sdp_timing_enable": (C.c_int, [_P, C.c_char_p]),
     "sdp_timing_read": (C.c_int, [_P, _DP, C.POINTER(C.c_int64), _DP, _DP]),
+    "sdp_hessian_matvec_static": (C.c_int, [C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "sdp_destroy": (None, [_P]),
     "sdp_status_str": (C.c_char_p, [C.c_int]),
     "sdp_last_error": (C.c_char_p, [_P]),

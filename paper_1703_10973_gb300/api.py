@@ -203,3 +203,32 @@ class SDPProblem:
         self._raise(self.lib.sdp_timing_read(self.h, C.byref(ms), C.byref(n), C.byref(f), C.byref(b)),
                     "sdp_timing_read")
         return dict(ms=ms.value, launches=n.value, flops=f.value, bytes=b.value)
+
+
+def hessian_matvec_static(n, m, Ak, Ai, Aj, Av, W, v, out=None, stream=None):
+    """sdp_hessian_matvec_static: handle-free FP64 Hessian matvec with static scratch.
+
+    Ak, Ai, Aj: int32 CUDA tensors (triplets), Av: float64 CUDA tensor, W: (n, n)
+    float64 CUDA tensor, v: float64 CUDA tensor of length m.  n <= SDP_STATIC_MAX_N.
+    """
+    lib = L.load()
+    nnz = int(Ak.numel())
+    for t, name in ((Ak, "Ak"), (Ai, "Ai"), (Aj, "Aj")):
+        if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous() or t.numel() != nnz:
+            raise ValueError(f"{name} must be a contiguous int32 CUDA tensor with {nnz} entries")
+    _check_dev(Av, nnz, "Av")
+    _check_dev(W, n * n, "W")
+    _check_dev(v, m, "v")
+    if out is None:
+        out = torch.empty_like(v)
+    _check_dev(out, m, "out")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.sdp_hessian_matvec_static(int(n), int(m), nnz, C.c_void_p(Ak.data_ptr()), C.c_void_p(Ai.data_ptr()),
+                                       C.c_void_p(Aj.data_ptr()), C.c_void_p(Av.data_ptr()),
+                                       C.c_void_p(W.data_ptr()), C.c_void_p(v.data_ptr()),
+                                       C.c_void_p(out.data_ptr()), C.c_void_p(stream) if stream else None)
+    if st != L.SDP_OK:
+        raise L.SDPError(st, f"sdp_hessian_matvec_static: {lib.sdp_status_str(st).decode()}: "
+                             f"{lib.sdp_last_error(None).decode()}")
+    return out

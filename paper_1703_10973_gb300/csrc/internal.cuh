@@ -12,6 +12,7 @@
 #include "../../include/sdpgb.h"
 
 namespace sdpgb {
+const char* free_call_error();   // error text of the last handle-free call on this thread
 
 // ---------------------------------------------------------------------------
 // Error plumbing: every CUDA call inside the library goes through CK(), which

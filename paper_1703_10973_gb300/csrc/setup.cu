@@ -69,7 +69,9 @@ extern "C" const char* sdp_status_str(sdp_status s) {
   return "unknown status";
 }
 
-extern "C" const char* sdp_last_error(const sdp_problem* h) { return h ? h->last_error.c_str() : ""; }
+extern "C" const char* sdp_last_error(const sdp_problem* h) {
+  return h ? h->last_error.c_str() : sdpgb::free_call_error();
+}
 
 extern "C" void sdp_destroy(sdp_problem* h) {
   if (!h) return;
