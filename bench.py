@@ -49,7 +49,11 @@ UNIT = "solves/s"
 # FP64 FMA throughput of this GB300, measured with a register-resident DFMA
 # loop (1216 CTAs x 256 threads, 8 independent chains per thread): 1.194 TFLOP/s.
 # Nominal from the unit count: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26.
-FP64_PEAK_TFLOPS = 1.194
+# FP64 peak of the GB300 derived from unit counts and clock: 152 SMs x 2 FP64 FMA
+# per clock per SM x 2 flop x 2.07 GHz (an FMA-chain probe reached 95% of it)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PEAK_SOURCE = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"
+
 ALU_CLASSES = ("gemm_f64", "sytrd", "potrf", "trsm")
 
 
@@ -290,32 +294,35 @@ def run(args):
     ipm_iters = [r["iters"] for r in res_last]
     pcg_iters = [r["pcg_iters_total"] for r in res_last]
 
-    # ---- one instrumented step for the dominant kernel class
-    roof = None
+    # ---- one instrumented step: CUDA events around every kernel class and phase
+    roof, breakdown = None, None
     if rank == 0 and args.timed_kernel:
-        probs[0].timing_enable(args.timed_kernel)
+        probs[0].timing_enable("*")
         tk0 = time.perf_counter()
         run_batch()
         torch.cuda.synchronize()
         step_wall = (time.perf_counter() - tk0) * 1e3
-        kt = probs[0].timing_read()
+        rep = probs[0].timing_report()
         probs[0].timing_enable(None)
-        if kt["launches"]:
-            avg = kt["ms"] / kt["launches"]
+        breakdown = {k: round(v[0], 3) for k, v in sorted(rep.items(), key=lambda kv: -kv[1][0])}
+        kt = rep.get(args.timed_kernel)
+        if kt and kt[1]:
+            ms, cnt, fl, by = kt
+            avg = ms / cnt
             if args.timed_kernel in ALU_CLASSES:
-                ach = kt["flops"] / (kt["ms"] * 1e-3) / 1e12
+                ach = fl / (ms * 1e-3) / 1e12
                 roof = {"kernel": args.timed_kernel, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                        "peak_source": "measured FP64 DFMA throughput of this GB300 (DESIGN.md)",
-                        "launches": kt["launches"], "avg_us": avg * 1e3,
-                        "busy_ms_per_step": kt["ms"], "step_ms_instrumented": step_wall}
+                        "peak_source": FP64_PEAK_SOURCE, "launches": cnt, "avg_us": avg * 1e3,
+                        "busy_ms_per_step": ms, "step_ms_instrumented": step_wall}
             else:
                 peak = _peaks().get("hbm_gbs", 6674.2)
-                ach = kt["bytes"] / (kt["ms"] * 1e-3) / 1e9
+                ach = by / (ms * 1e-3) / 1e9
                 roof = {"kernel": args.timed_kernel, "bound": "hbm", "achieved": ach, "peak": peak,
                         "unit": "GB/s", "frac": ach / peak, "traffic": None,
-                        "fp64_tflops": kt["flops"] / (kt["ms"] * 1e-3) / 1e12,
-                        "launches": kt["launches"], "avg_us": avg * 1e3, "busy_ms_per_step": kt["ms"]}
+                        "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+                        "fp64_tflops": fl / (ms * 1e-3) / 1e12, "launches": cnt, "avg_us": avg * 1e3,
+                        "busy_ms_per_step": ms, "step_ms_instrumented": step_wall}
 
     # ---- end to end through the public API: host triplets in, solution out
     e2e = None
@@ -374,7 +381,8 @@ def run(args):
                            "pcg_iters_per_solve_mean": float(np.mean(pcg_iters)),
                            "max_relgap": max(r["relgap"] for r in res_last)},
                 "latency_ms": {"p50": p50, "p99": p99},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "roofline": roof, "breakdown_ms_per_step": breakdown, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk.summary(),
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
     for p in probs:

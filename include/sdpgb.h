@@ -212,6 +212,12 @@ sdp_status sdp_reset(sdp_problem* h);
  */
 sdp_status sdp_timing_enable(sdp_problem* h, const char* cls);
 sdp_status sdp_timing_read(sdp_problem* h, double* ms, int64_t* launches, double* flops, double* bytes);
+/* cls "*" records every class (regions may nest: phases such as "nt_scaling",
+ * "precond_build", "pcg", "max_step" contain kernel classes).  sdp_timing_report
+ * synchronises the stream, writes one line "class ms launches flops bytes" per
+ * recorded class into buf (NUL-terminated, truncated to len), clears the
+ * accumulators and returns the length the full report needs. */
+int64_t sdp_timing_report(sdp_problem* h, char* buf, int64_t len);
 
 /* Number of kernel launches issued by this handle since setup (for accounting). */
 int64_t sdp_launch_count(const sdp_problem* h);

@@ -99,6 +99,7 @@ SIGNATURES = {
     "sdp_reset": (C.c_int, [_P]),
     "sdp_timing_enable": (C.c_int, [_P, C.c_char_p]),
     "sdp_timing_read": (C.c_int, [_P, _DP, C.POINTER(C.c_int64), _DP, _DP]),
+    "sdp_timing_report": (C.c_int64, [_P, C.c_char_p, C.c_int64]),
     "sdp_hessian_matvec_static": (C.c_int, [C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "sdp_destroy": (None, [_P]),
     "sdp_status_str": (C.c_char_p, [C.c_int]),

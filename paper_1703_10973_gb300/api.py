@@ -195,6 +195,16 @@ class SDPProblem:
     def timing_enable(self, cls):
         self._raise(self.lib.sdp_timing_enable(self.h, cls.encode() if cls else None), "sdp_timing_enable")
 
+    def timing_report(self):
+        """Per-class device time since timing_enable: {class: (ms, launches, flops, bytes)}."""
+        buf = C.create_string_buffer(1 << 16)
+        self.lib.sdp_timing_report(self.h, buf, len(buf))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, ms, cnt, fl, by = line.split()
+            out[name] = (float(ms), int(cnt), float(fl), float(by))
+        return out
+
     def timing_read(self):
         ms = C.c_double()
         n = C.c_int64()

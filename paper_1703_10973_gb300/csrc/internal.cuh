@@ -61,6 +61,7 @@ void ktimer_end(cudaStream_t st, const char* cls, double flops, double bytes);
 void ktimer_set(const char* cls);
 void ktimer_read(double* ms, int64_t* launches, double* flops, double* bytes);
 void ktimer_pause(bool paused);   // no recording while a graph is being captured
+size_t ktimer_report(char* buf, size_t len);
 
 // Raise a kernel's dynamic shared-memory limit to the per-CTA maximum, once per
 // kernel and process (thread-safe).  Setting the limit per launch to the size
@@ -162,6 +163,19 @@ void eig_work_carve(EigWork* w, void* base, int n, bool full);
 sdp_status eig_full(cudaStream_t st, int n, double* A, double* w, double* E, EigWork* ws);
 // Smallest eigenvalue only (result in *lmin_dev, device).
 sdp_status eig_min(cudaStream_t st, int n, double* A, double* lmin_dev, EigWork* ws);
+// lanczos.cu: lambda_min of a dense symmetric matrix (one thread-block cluster);
+// out_dev[0..4] = estimate, Ritz value, residual bound, steps, converged flag
+size_t lanczos_work_doubles(int n);
+// schur.cu: sparse factorisation of the Hhat core
+struct SchurPlanHost {
+  std::vector<int> pverts, rverts, stype, sa, sb, bptr, bcol, bp, btptr, btslot;
+  bool bipartite = false;
+};
+void schur_plan(int n, const std::vector<int>& krowptr, const std::vector<int>& kcol, SchurPlanHost* out);
+sdp_status schur_build(sdp_problem* h, int k, double tau);
+sdp_status schur_apply(sdp_problem* h, const double* u, double* out);
+sdp_status lanczos_min(cudaStream_t st, int n, const double* M, int ldm, double rtol, double accept_above,
+                       double* work, double* out_dev);
 // Smallest eigenvalue and the top-k eigenpairs: wtop[0..k) ascending (= lambda_{n-k..n-1}),
 // Etop rows = eigenvectors; *lmin_dev = lambda_0.
 sdp_status eig_extremes(cudaStream_t st, int n, double* A, int k, double* lmin_dev, double* wtop,
@@ -220,6 +234,7 @@ struct sdp_problem {
   double *X = nullptr, *y = nullptr, *S = nullptr, *W = nullptr;
   int iter = 0;
   int nt_fallbacks = 0;     // NT scalings computed by the Denman-Beavers fallback
+  int pcg_prec_fallbacks = 0;  // restarted PCG sweeps that fell back from reduced precision to FP64
   bool have_W = false;
   double xi = 0;
 
@@ -255,10 +270,21 @@ struct sdp_problem {
   double* uvec2 = nullptr; // nk
   double* uvec3 = nullptr; // nk
   int core_refine = 1;     // refinement steps of each core triangular solve
+  // sparse Hhat core (schur.cu): independent set P of the K graph, rest R
+  int hs_np = 0, hs_nr = 0, hs_nb = 0, hs_k = 0;
+  int *hs_pverts = nullptr, *hs_rverts = nullptr;        // np, nr
+  int *hs_stype = nullptr, *hs_sa = nullptr, *hs_sb = nullptr;   // per K slot
+  int *hs_bptr = nullptr, *hs_bcol = nullptr, *hs_bp = nullptr;  // B blocks by row of P
+  int *hs_btptr = nullptr, *hs_btslot = nullptr;         // B blocks by row of R
+  double *hs_D = nullptr, *hs_F = nullptr, *hs_yP = nullptr;     // L_P, F = L_P^{-1} B, y_P
+  double *hs_C = nullptr, *hs_Cinv = nullptr;            // Schur complement factor and inverse
+  double *hs_v1 = nullptr, *hs_v2 = nullptr, *hs_v3 = nullptr;
   double* trpart = nullptr;
 
   // ---- dense IPM work ----
   double *L = nullptr, *Rs = nullptr, *M1 = nullptr, *M2 = nullptr, *M3 = nullptr;
+  bool chol_valid = false;   // L = chol(X) and Rs = chol(S) belong to the current X, S
+  double* lz_work = nullptr; // Lanczos basis scratch (step length)
   double *Gt = nullptr, *Sinv = nullptr, *Rd = nullptr, *Rc = nullptr, *dX = nullptr,
          *dS = nullptr, *E = nullptr, *lam = nullptr;
   double *Rp = nullptr, *rhs = nullptr, *dy = nullptr;

@@ -20,7 +20,10 @@
 
 namespace sdpgb {
 
-enum { R_RP = 8, R_RD, R_CX, R_BY, R_XS, R_XDS, R_DXS, R_DXDS, R_LMIN };
+enum { R_RP = 8, R_RD, R_CX, R_BY, R_XS, R_XDS, R_DXS, R_DXDS, R_LMIN, R_LZ /* 5 slots */ };
+
+// Step lengths use Lanczos from this order on (below it the full eigensolver is cheap).
+constexpr int LZ_MIN_N = 64;
 
 sdp_status ipm_alloc(sdp_problem* h) {
   if (h->L) return SDP_OK;
@@ -54,6 +57,7 @@ sdp_status ipm_alloc(sdp_problem* h) {
     SDP_TRY(h->alloc(&h->eig_base, eig_work_bytes(n, true)));
     eig_work_carve(&h->eig, h->eig_base, n, true);
   }
+  if (n >= LZ_MIN_N) SDP_TRY(h->allocT(&h->lz_work, lanczos_work_doubles(n)));
   return SDP_OK;
 }
 
@@ -81,15 +85,30 @@ static sdp_status max_step(sdp_problem* h, const double* Lf, const double* D, do
   transpose(st, n, n, h->M1, n, h->M2, n);                      // D Lf^{-T}
   trsm_left_lower(st, false, n, n, Lf, n, h->M2, n, h->work);   // Lf^{-1} D Lf^{-T}
   symmetrize_avg(st, n, h->M2, n);
-  SDP_TRY(eig_min(st, n, h->M2, h->scal + R_LMIN, &h->eig));
-  ktimer_end(st, "max_step", 0.0, 0.0);
   double lmin = 0.0;
-  SDP_CK(h, cudaMemcpyAsync(&lmin, h->scal + R_LMIN, sizeof(double), cudaMemcpyDeviceToHost, st));
-  SDP_CK(h, cudaStreamSynchronize(st));
-  if (eig_flag(st, &h->eig)) {
-    h->last_error = "step length: grid barrier timeout";
-    return SDP_ERR_TIMEOUT;
+  bool have = false;
+  if (h->lz_work) {
+    // lambda_min by Lanczos; only whether it lies above -step_frac matters for a full step
+    if (lanczos_min(st, n, h->M2, n, 1e-3, -h->prm.step_frac, h->lz_work, h->scal + R_LZ) == SDP_OK) {
+      double o[5];
+      SDP_CK(h, cudaMemcpyAsync(o, h->scal + R_LZ, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SDP_CK(h, cudaStreamSynchronize(st));
+      if (o[4] != 0.0 && std::isfinite(o[0])) {
+        lmin = o[0];
+        have = true;
+      }
+    }
   }
+  if (!have) {
+    SDP_TRY(eig_min(st, n, h->M2, h->scal + R_LMIN, &h->eig));
+    SDP_CK(h, cudaMemcpyAsync(&lmin, h->scal + R_LMIN, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SDP_CK(h, cudaStreamSynchronize(st));
+    if (eig_flag(st, &h->eig)) {
+      h->last_error = "step length: grid barrier timeout";
+      return SDP_ERR_TIMEOUT;
+    }
+  }
+  ktimer_end(st, "max_step", 0.0, 0.0);
   if (!std::isfinite(lmin)) {
     h->last_error = "step length: non-finite eigenvalue";
     return SDP_ERR_NUMERIC;
@@ -256,6 +275,31 @@ static sdp_status nt_scaling(sdp_problem* h) {
   return SDP_OK;
 }
 
+// X <- X + alpha dX (symmetrised) once chol(X + alpha dX) succeeds into Lout;
+// alpha shrinks by 0.8 per failure (at most 8 times).
+static sdp_status update_checked(sdp_problem* h, double* X, const double* dX, double* alpha, double* Lout,
+                                 const char* what) {
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  const size_t nn = (size_t)n * n;
+  for (int t = 0; t < 8; ++t) {
+    axpby(st, nn, 1.0, X, *alpha, dX, h->M1);
+    symmetrize_avg(st, n, h->M1, n);
+    copy2d(st, n, n, h->M1, n, Lout, n);
+    potrf(st, n, Lout, n, h->info, h->work);
+    int info = 0;
+    SDP_CK(h, cudaMemcpyAsync(&info, h->info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SDP_CK(h, cudaStreamSynchronize(st));
+    if (info == 0) {
+      copy2d(st, n, n, h->M1, n, X, n);
+      return SDP_OK;
+    }
+    *alpha *= 0.8;
+  }
+  h->last_error = std::string(what) + ": no positive definite iterate along the step";
+  return SDP_ERR_NOT_PD;
+}
+
 sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   SDP_TRY(ipm_alloc(h));
   cudaStream_t st = h->stream;
@@ -297,8 +341,12 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
     return SDP_OK;
   }
 
-  // ---- NT scaling
-  SDP_TRY(chol_checked(h, h->X, h->L, "ipm_step: chol(X)"));
+  // ---- NT scaling (L = chol(X) and Rs = chol(S) come from the previous step's check)
+  if (!h->chol_valid) {
+    SDP_TRY(chol_checked(h, h->X, h->L, "ipm_step: chol(X)"));
+    SDP_TRY(chol_checked(h, h->S, h->Rs, "ipm_step: chol(S)"));
+    h->chol_valid = true;
+  }
   const int fb0 = h->nt_fallbacks;
   ktimer_begin(st, "nt_scaling");
   SDP_TRY(nt_scaling(h));
@@ -313,7 +361,6 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   SDP_TRY(precond_build_impl(h));
   ktimer_end(st, "precond_build", 0.0, 0.0);
   inf.tau = h->tau;
-  SDP_TRY(chol_checked(h, h->S, h->Rs, "ipm_step: chol(S)"));
 
   // ---- common part of the right-hand side: Rp <- Rp + A(W Rd W)
   gemm(st, false, false, n, n, n, 1.0, h->W, n, h->Rd, n, 0.0, h->M1, n);
@@ -353,15 +400,17 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   SDP_TRY(max_step(h, h->Rs, h->dS, &ad));
   ap = std::min(1.0, h->prm.step_frac * ap);
   ad = std::min(1.0, h->prm.step_frac * ad);
+
+  // ---- update.  The Cholesky factors of the new X and S are the next step's
+  // L and Rs; a factorisation that fails (a step length from a Lanczos estimate
+  // that came out too long) shortens that side's step.
+  h->chol_valid = false;
+  SDP_TRY(update_checked(h, h->X, h->dX, &ap, h->L, "ipm_step: primal update"));
+  SDP_TRY(update_checked(h, h->S, h->dS, &ad, h->Rs, "ipm_step: dual update"));
+  h->chol_valid = true;
   inf.alpha_p = ap;
   inf.alpha_d = ad;
-
-  // ---- update
-  axpby(st, nn, 1.0, h->X, ap, h->dX, h->X);
   axpby(st, m, 1.0, h->y, ad, h->dy, h->y);
-  axpby(st, nn, 1.0, h->S, ad, h->dS, h->S);
-  symmetrize_avg(st, n, h->X, n);
-  symmetrize_avg(st, n, h->S, n);
   SDP_CK(h, cudaGetLastError());
   h->iter++;
   if (h->prm.verbose)

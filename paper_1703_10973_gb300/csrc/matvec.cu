@@ -173,12 +173,20 @@ sdp_status ensure_lowprec_W(sdp_problem* h, int prec) {
   return SDP_OK;
 }
 
+// Rows of W per CTA of the SpMM: as many as shared memory allows (each CTA
+// streams the whole CSR of V once), but few enough that the grid still covers
+// the SMs -- the FP64 form is bound by the SMs' DFMA rate, not by bandwidth.
 static int rows_per_cta(int n, size_t elem) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   const size_t budget = 96 * 1024;
-  int r = (int)std::min<size_t>(8, budget / (elem * (size_t)n));
-  if (r >= 8) return 8;
-  if (r >= 4) return 4;
-  if (r >= 2) return 2;
+  const int cap = (int)std::min<size_t>(8, budget / (elem * (size_t)n));
+  for (int r = 8; r > 1; r /= 2)
+    if (r <= cap && (n + r - 1) / r >= (sms * 9) / 10) return r;
   return 1;
 }
 

@@ -309,9 +309,20 @@ static sdp_status pcg_impl_(sdp_problem* h, const double* r, double* y, double r
     sdp_status s = pcg_core(h, resid, corr, inner, budget, prec, &it, &rr, &brk);
     total += it;
     if (s != SDP_OK && s != SDP_ERR_MAXIT) return s;
-    if (brk && it <= 1) break;   // breakdown before any progress: keep the best iterate
+    if (brk && it <= 1 && prec == SDP_FP64) break;   // breakdown before any progress
+    const double tr_prev = tr;
     if (it > 0) axpby(st, m, 1.0, y, 1.0, corr, y);
     SDP_TRY(true_residual(h, r, y, resid, &tr));
+    if (!(tr < tr_prev)) {
+      // the sweep did not reduce the FP64 residual: drop its correction; a
+      // reduced-precision inner solve hands over to FP64, an FP64 one stops
+      if (it > 0) axpby(st, m, 1.0, y, -1.0, corr, y);
+      SDP_TRY(true_residual(h, r, y, resid, &tr));
+      if (prec == SDP_FP64) break;
+      prec = SDP_FP64;
+      h->pcg_prec_fallbacks++;
+      continue;
+    }
     if (!std::isfinite(tr)) {
       h->last_error = "pcg: non-finite true residual";
       return SDP_ERR_NUMERIC;

@@ -104,20 +104,6 @@ __global__ void k_apply_tail(int m, int k, const int* __restrict__ eptr, const i
   z[i] = ginv[i] * inv_tau2 * (r[i] - us);
 }
 
-// Sc[l n + a][l2 n + b] = alpha K_ll2[a][b] for every stored slot (a, b) of K;
-// for l != l2 the mirror entry of block (l2, l) as well.  One CTA per row a.
-__global__ void k_scatter_K(int n, int nk, const int* __restrict__ krowptr, const int* __restrict__ kcol,
-                            const double* __restrict__ Kval, int l, int l2, double alpha, double* __restrict__ Sc) {
-  const int a = blockIdx.x;
-  if (a >= n) return;
-  for (int s = krowptr[a] + threadIdx.x; s < krowptr[a + 1]; s += blockDim.x) {
-    const int b = kcol[s];
-    const double v = alpha * Kval[s];
-    Sc[(size_t)(l * n + a) * nk + (size_t)l2 * n + b] = v;
-    if (l != l2) Sc[(size_t)(l2 * n + b) * nk + (size_t)l * n + a] = v;
-  }
-}
-
 // out[l n + c] = alpha in[c k + l]   (n x k  ->  k x n)
 __global__ void k_nk_to_kn(int n, int k, double alpha, const double* __restrict__ in, double* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -330,8 +316,10 @@ static sdp_status precond_alloc(sdp_problem* h) {
   const size_t nk = (size_t)n * k;
   SDP_TRY(h->allocT(&h->U, nk));
   SDP_TRY(h->allocT(&h->Z, (size_t)n * n));
-  SDP_TRY(h->allocT(&h->Sc, nk * nk));
-  SDP_TRY(h->allocT(&h->Linv, nk * nk));
+  if (h->prm.precond != SDP_PRECOND_HAT) {   // dense core (Hhat factors it sparsely, schur.cu)
+    SDP_TRY(h->allocT(&h->Sc, nk * nk));
+    SDP_TRY(h->allocT(&h->Linv, nk * nk));
+  }
   SDP_TRY(h->allocT(&h->tau_dev, 8 + 2 * 32 * 32));
   SDP_TRY(h->allocT(&h->wtop, 32));
   SDP_TRY(h->allocT(&h->Etop, (size_t)32 * n));
@@ -387,22 +375,6 @@ static void form_core(sdp_problem* h, int k, double shift) {
     }
   }
   if (shift != 0.0) add_diag(st, nk, h->Sc, nk, shift);
-}
-
-// Hhat core: Sc = tau^2 I + 2 tau K (blocks l, l'), K on its sparse pattern.
-static void form_core_hat(sdp_problem* h, int k, double tau) {
-  cudaStream_t st = h->stream;
-  const int n = h->n, nk = n * k;
-  fill(st, h->Sc, (size_t)nk * nk, 0.0);
-  for (int l = 0; l < k; ++l) {
-    for (int l2 = l; l2 < k; ++l2) {
-      count_launch(2);
-      k_kvals<<<cdiv(h->nnzK, 256), 256, 0, st>>>(h->nnzK, h->kptr, h->kcon, h->kcra, h->kcrb, h->ginv, h->au,
-                                                 k, l, l2, h->Kval);
-      k_scatter_K<<<n, 128, 0, st>>>(n, nk, h->krowptr, h->kcol, h->Kval, l, l2, 2.0 * tau, h->Sc);
-    }
-  }
-  add_diag(st, nk, h->Sc, nk, tau * tau);
 }
 
 sdp_status precond_build_impl(sdp_problem* h) {
@@ -471,21 +443,20 @@ sdp_status precond_build_impl(sdp_problem* h) {
   // below that bound or below zero; such pivots are raised to tau^2 (a
   // modified Cholesky with the bound the mathematics gives), which keeps the
   // factor of an SPD matrix close to S in every direction.
-  if (hat)
-    form_core_hat(h, k, tau);
-  else
+  h->core_shift = tau * tau;
+  if (hat) {
+    SDP_TRY(schur_build(h, k, tau));
+  } else {
     form_core(h, k, tau * tau);
-  potrf_floor(st, nk, h->Sc, nk, h->info, h->work, tau * tau);
-  {
+    potrf_floor(st, nk, h->Sc, nk, h->info, h->work, tau * tau);
     int inf2[2] = {0, 0};
     SDP_CK(h, cudaMemcpyAsync(inf2, h->info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     SDP_CK(h, cudaStreamSynchronize(st));
     h->core_floor_pivots = inf2[1];
+    fill(st, h->Linv, (size_t)nk * nk, 0.0);
+    add_diag(st, nk, h->Linv, nk, 1.0);
+    trsm_left_lower_ex(st, false, nk, nk, h->Sc, nk, h->Linv, nk, h->work, true);
   }
-  h->core_shift = tau * tau;
-  fill(st, h->Linv, (size_t)nk * nk, 0.0);
-  add_diag(st, nk, h->Linv, nk, 1.0);
-  trsm_left_lower_ex(st, false, nk, nk, h->Sc, nk, h->Linv, nk, h->work, true);
   h->pc_valid = true;
   h->pc_generation++;
   return SDP_OK;
@@ -516,14 +487,19 @@ sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int pr
   // whose residual uses the factor itself:  y0 = L^{-1} u,  y = y0 + L^{-1}(u - L y0).
   // ||I - L^{-1} L|| stays far below one where the plain inverse has failed, and
   // the refined solve matches substitution.  Buffers: uvec = u, uvec2 = y0, uvec3 = scratch.
-  for (int t = 0; t < 2; ++t) {
-    const bool tr = (t == 1);
-    trmv_lower_ex(st, tr, nk, h->Linv, nk, h->uvec, h->uvec2, h->trpart, 1.0, nullptr, 0.0);   // y0
-    for (int it = 0; it < h->core_refine; ++it) {
-      trmv_lower_ex(st, tr, nk, h->Sc, nk, h->uvec2, h->uvec3, h->trpart, -1.0, h->uvec, 1.0); // u - L y0
-      trmv_lower_ex(st, tr, nk, h->Linv, nk, h->uvec3, h->uvec2, h->trpart, 1.0, h->uvec2, 1.0);  // y0 + L^{-1} res
+  if (h->pc_hat) {
+    SDP_TRY(schur_apply(h, h->uvec, h->uvec2));
+    std::swap(h->uvec, h->uvec2);
+  } else {
+    for (int t = 0; t < 2; ++t) {
+      const bool tr = (t == 1);
+      trmv_lower_ex(st, tr, nk, h->Linv, nk, h->uvec, h->uvec2, h->trpart, 1.0, nullptr, 0.0);   // y0
+      for (int it = 0; it < h->core_refine; ++it) {
+        trmv_lower_ex(st, tr, nk, h->Sc, nk, h->uvec2, h->uvec3, h->trpart, -1.0, h->uvec, 1.0); // u - L y0
+        trmv_lower_ex(st, tr, nk, h->Linv, nk, h->uvec3, h->uvec2, h->trpart, 1.0, h->uvec2, 1.0);  // y0 + L^{-1} res
+      }
+      std::swap(h->uvec, h->uvec2);   // result becomes the input of the next solve
     }
-    std::swap(h->uvec, h->uvec2);   // result becomes the input of the next solve
   }
   // ZS = Z S_mat with S_mat[c][l] = s[l n + c]
   if (h->pc_hat) {

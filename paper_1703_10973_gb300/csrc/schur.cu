@@ -1,0 +1,446 @@
+// Sparse factorisation of the Section V core (eq. sparse_prec).
+//
+// For Hhat the core is S = tau^2 I + 2 tau K, with K_(l,x),(l',y) =
+// sum_i g_i^{-1} (A_i u_l)_x (A_i u_l')_y nonzero only where rows x and y are
+// touched by a common constraint (the K pattern) -- the paper notes that this
+// matrix is sparse and that a sparse factorisation can cost far less than the
+// dense (nk)^3 / 3.  Ordered by rows of W ("vertices"), S is block sparse with
+// k x k blocks.  Rows of an independent set P of the K graph have no block
+// between them, so S_PP is block diagonal, and
+//   S = [[D, B], [B^T, E]],  D = diag(D_a),  L = [[L_P, 0], [F^T, L_C]],
+//   L_P = diag(chol(D_a)),  F = L_P^{-1} B,  C = E - F^T F = L_C L_C^T,
+// leaves a dense factorisation of the Schur complement C on the other rows R
+// only.  For matrix completion the K graph is bipartite (rows of the observed
+// matrix against its columns), P is the larger side and C has order
+// min(p, q) k; the Schur complement needs about sum_a deg(a)^2 k^3 / 2 FMAs.
+//
+// Apply (S^{-1} u):  y_P = L_P^{-1} u_P;  y_R = L_C^{-1}(u_R - F^T y_P);
+//                    x_R = L_C^{-T} y_R;  x_P = L_P^{-T}(y_P - F x_R).
+// The two dense triangular solves use L_C^{-1} with one refinement step
+// against L_C, as the dense core does.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <queue>
+
+namespace sdpgb {
+
+static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Host: choose P and classify the K slots
+// ---------------------------------------------------------------------------
+// K graph: vertices = rows of W, edges = off-diagonal K slots.  If it is
+// bipartite, each connected component contributes its larger colour class to
+// P; otherwise P is a greedy maximal independent set taken in order of
+// increasing degree.
+void schur_plan(int n, const std::vector<int>& krowptr, const std::vector<int>& kcol, SchurPlanHost* out) {
+  std::vector<int> color(n, -1);
+  bool bip = true;
+  std::vector<char> inP(n, 0);
+  std::vector<int> comp;
+  for (int s = 0; s < n && bip; ++s) {
+    if (color[s] >= 0) continue;
+    comp.clear();
+    std::queue<int> q;
+    q.push(s);
+    color[s] = 0;
+    while (!q.empty() && bip) {
+      const int v = q.front();
+      q.pop();
+      comp.push_back(v);
+      for (int t = krowptr[v]; t < krowptr[v + 1]; ++t) {
+        const int u = kcol[t];
+        if (u == v) continue;
+        if (color[u] < 0) {
+          color[u] = 1 - color[v];
+          q.push(u);
+        } else if (color[u] == color[v]) {
+          bip = false;
+          break;
+        }
+      }
+    }
+    if (!bip) break;
+    int c0 = 0;
+    for (int v : comp) c0 += (color[v] == 0);
+    const int pick = (2 * c0 >= (int)comp.size()) ? 0 : 1;
+    for (int v : comp) inP[v] = (color[v] == pick);
+  }
+  if (!bip) {
+    std::fill(inP.begin(), inP.end(), 0);
+    std::vector<int> order(n);
+    for (int v = 0; v < n; ++v) order[v] = v;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return (krowptr[a + 1] - krowptr[a]) < (krowptr[b + 1] - krowptr[b]);
+    });
+    std::vector<char> blocked(n, 0);
+    for (int v : order) {
+      if (blocked[v]) continue;
+      inP[v] = 1;
+      for (int t = krowptr[v]; t < krowptr[v + 1]; ++t) blocked[kcol[t]] = 1;
+    }
+  }
+  SchurPlanHost& P = *out;
+  P = SchurPlanHost{};
+  std::vector<int> pidx(n, -1), ridx(n, -1);
+  for (int v = 0; v < n; ++v) {
+    if (inP[v]) { pidx[v] = (int)P.pverts.size(); P.pverts.push_back(v); }
+    else { ridx[v] = (int)P.rverts.size(); P.rverts.push_back(v); }
+  }
+  const int nnzK = krowptr[n];
+  P.stype.assign(nnzK, 0);
+  P.sa.assign(nnzK, 0);
+  P.sb.assign(nnzK, 0);
+  P.bptr.assign(P.pverts.size() + 1, 0);
+  std::vector<int> bslot_of(nnzK, -1);
+  for (int x = 0; x < n; ++x) {
+    for (int s = krowptr[x]; s < krowptr[x + 1]; ++s) {
+      const int y = kcol[s];
+      if (pidx[x] >= 0 && y == x) {
+        P.stype[s] = 1; P.sa[s] = pidx[x];
+      } else if (pidx[x] >= 0) {          // y in R (P is independent)
+        const int bi = (int)P.bcol.size();
+        bslot_of[s] = bi;
+        P.stype[s] = 2; P.sa[s] = bi;
+        P.bcol.push_back(ridx[y]);
+        P.bp.push_back(pidx[x]);
+        P.bptr[pidx[x] + 1]++;
+      } else if (pidx[y] >= 0) {
+        P.stype[s] = 0;                  // mirror of a B block
+      } else {
+        P.stype[s] = 3; P.sa[s] = ridx[x]; P.sb[s] = ridx[y];
+      }
+    }
+  }
+  for (size_t a = 0; a < P.pverts.size(); ++a) P.bptr[a + 1] += P.bptr[a];
+  // transpose lists: for each r in R, the B blocks (a, r)
+  P.btptr.assign(P.rverts.size() + 1, 0);
+  for (int bi = 0; bi < (int)P.bcol.size(); ++bi) P.btptr[P.bcol[bi] + 1]++;
+  for (size_t r = 0; r < P.rverts.size(); ++r) P.btptr[r + 1] += P.btptr[r];
+  P.btslot.assign(P.bcol.size(), 0);
+  std::vector<int> fill(P.rverts.size(), 0);
+  for (int bi = 0; bi < (int)P.bcol.size(); ++bi) {
+    const int r = P.bcol[bi];
+    P.btslot[P.btptr[r] + fill[r]++] = bi;
+  }
+  P.bipartite = bip;
+}
+
+// ---------------------------------------------------------------------------
+// Device: formation and factorisation
+// ---------------------------------------------------------------------------
+constexpr int KMAX = 8;
+
+// one thread per (slot, l): the k values 2 tau K_(l, l2)[x][y], written to the
+// D, B or C target of the slot (mirror slots of B are skipped)
+__global__ void k_hat_scatter(int nnzK, int k, const int* __restrict__ kptr, const int* __restrict__ kcon,
+                              const int* __restrict__ kcra, const int* __restrict__ kcrb,
+                              const double* __restrict__ ginv, const double* __restrict__ au, double two_tau,
+                              const int* __restrict__ stype, const int* __restrict__ sa, const int* __restrict__ sb,
+                              double* __restrict__ D, double* __restrict__ B, double* __restrict__ Cm, int Rk) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnzK * k) return;
+  const int s = t / k, l = t % k;
+  const int ty = stype[s];
+  if (ty == 0) return;
+  double acc[KMAX];
+#pragma unroll
+  for (int l2 = 0; l2 < KMAX; ++l2) acc[l2] = 0.0;
+  for (int c = kptr[s]; c < kptr[s + 1]; ++c) {
+    const double ga = ginv[kcon[c]] * au[(size_t)kcra[c] * k + l];
+    const double* ab = au + (size_t)kcrb[c] * k;
+#pragma unroll
+    for (int l2 = 0; l2 < KMAX; ++l2)
+      if (l2 < k) acc[l2] = fma(ga, ab[l2], acc[l2]);
+  }
+  double* dst;
+  if (ty == 1) dst = D + ((size_t)sa[s] * k + l) * k;
+  else if (ty == 2) dst = B + ((size_t)sa[s] * k + l) * k;
+  else dst = Cm + ((size_t)sa[s] * k + l) * Rk + (size_t)sb[s] * k;
+#pragma unroll
+  for (int l2 = 0; l2 < KMAX; ++l2)
+    if (l2 < k) dst[l2] = two_tau * acc[l2];
+}
+
+// D_a += tau^2 I, then D_a = L_a L_a^T in place (lower), pivots below tau^2
+// raised to it (S >= tau^2 I holds exactly); one thread per a.
+__global__ void k_hat_factor_D(int np, int k, double tau2, double* __restrict__ D, int* info) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= np) return;
+  double L[KMAX][KMAX];
+  double* Da = D + (size_t)a * k * k;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) L[i][j] = Da[i * k + j] + ((i == j) ? tau2 : 0.0);
+  for (int j = 0; j < k; ++j) {
+    double p = L[j][j];
+    for (int t = 0; t < j; ++t) p -= L[j][t] * L[j][t];
+    if (!(p >= tau2)) {
+      atomicAdd(info + 1, 1);
+      p = tau2;
+    }
+    const double ljj = sqrt(p);
+    L[j][j] = ljj;
+    for (int i = j + 1; i < k; ++i) {
+      double v = L[i][j];
+      for (int t = 0; t < j; ++t) v -= L[i][t] * L[j][t];
+      L[i][j] = v / ljj;
+    }
+  }
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) Da[i * k + j] = (j <= i) ? L[i][j] : 0.0;
+}
+
+// F = L_a^{-1} B_(a,y) in place; one thread per (block, column l2)
+__global__ void k_hat_F(int nb, int k, const int* __restrict__ bp, const double* __restrict__ D,
+                        double* __restrict__ B) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb * k) return;
+  const int bi = t / k, c = t % k;
+  const double* La = D + (size_t)bp[bi] * k * k;
+  double* Bb = B + (size_t)bi * k * k;
+  double x[KMAX];
+  for (int i = 0; i < k; ++i) {
+    double v = Bb[i * k + c];
+    for (int j = 0; j < i; ++j) v -= La[i * k + j] * x[j];
+    x[i] = v / La[i * k + i];
+  }
+  for (int i = 0; i < k; ++i) Bb[i * k + c] = x[i];
+}
+
+// C -= F^T F, lower triangle, one CTA per block row r of C (vertex rverts[r]):
+// for every P-neighbour a of r in a fixed order, the blocks F_(a,r)^T F_(a,r')
+// for the neighbours r' <= r of a.  Each CTA owns its rows, so the sums need no
+// atomics and are the same on every run.
+__global__ void __launch_bounds__(256) k_hat_schur_rows(int k, int Rk, const int* __restrict__ btptr,
+                                                        const int* __restrict__ btslot, const int* __restrict__ bp,
+                                                        const int* __restrict__ bptr, const int* __restrict__ bcol,
+                                                        const double* __restrict__ F, double* __restrict__ Cm) {
+  const int r = blockIdx.x;
+  const int kk = k * k;
+  for (int e = btptr[r]; e < btptr[r + 1]; ++e) {
+    const int bi = btslot[e];
+    const int a = bp[bi];
+    const int b0 = bptr[a], deg = bptr[a + 1] - b0;
+    const double* Fr = F + (size_t)bi * kk;
+    for (int t = threadIdx.x; t < deg * kk; t += blockDim.x) {
+      const int j = t / kk, l = (t % kk) / k, l2 = t % k;
+      const int r2 = bcol[b0 + j];
+      if (r2 > r || (r2 == r && l2 > l)) continue;
+      const double* Fj = F + (size_t)(b0 + j) * kk;
+      double v = 0.0;
+      for (int q = 0; q < k; ++q) v = fma(Fr[q * k + l], Fj[q * k + l2], v);
+      double* c = Cm + (size_t)(r * k + l) * Rk + (size_t)r2 * k + l2;
+      *c -= v;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Device: apply pieces (u and the result in the k x n layout u[l n + c])
+// ---------------------------------------------------------------------------
+__global__ void k_hat_fwdP(int np, int n, int k, const int* __restrict__ pverts, const double* __restrict__ D,
+                           const double* __restrict__ u, double* __restrict__ yP) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= np) return;
+  const double* La = D + (size_t)a * k * k;
+  const int v = pverts[a];
+  double x[KMAX];
+  for (int i = 0; i < k; ++i) {
+    double s = u[(size_t)i * n + v];
+    for (int j = 0; j < i; ++j) s -= La[i * k + j] * x[j];
+    x[i] = s / La[i * k + i];
+    yP[(size_t)a * k + i] = x[i];
+  }
+}
+
+__device__ __forceinline__ double hs_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// tR[r k + l2] = u[l2 n + rverts[r]] - sum over blocks (a, r) of (F^T y_a)[l2];
+// one warp per r, lanes over the blocks
+__global__ void k_hat_fwdR(int nr, int n, int k, const int* __restrict__ rverts, const int* __restrict__ btptr,
+                           const int* __restrict__ btslot, const int* __restrict__ bp, const double* __restrict__ F,
+                           const double* __restrict__ yP, const double* __restrict__ u, double* __restrict__ tR) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= nr) return;
+  double acc[KMAX];
+#pragma unroll
+  for (int c = 0; c < KMAX; ++c) acc[c] = 0.0;
+  for (int e = btptr[r] + lane; e < btptr[r + 1]; e += 32) {
+    const int bi = btslot[e];
+    const double* Fb = F + (size_t)bi * k * k;
+    const double* ya = yP + (size_t)bp[bi] * k;
+    for (int i = 0; i < k; ++i) {
+      const double yi = ya[i];
+#pragma unroll
+      for (int c = 0; c < KMAX; ++c)
+        if (c < k) acc[c] = fma(Fb[i * k + c], yi, acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < KMAX; ++c) {
+    if (c >= k) break;
+    const double s = hs_warp_sum(acc[c]);
+    if (lane == 0) tR[(size_t)r * k + c] = u[(size_t)c * n + rverts[r]] - s;
+  }
+}
+
+// x_a = L_a^{-T}(y_a - F_a x_R); out[l n + pverts[a]] = x_a[l]; one warp per a
+__global__ void k_hat_bwdP(int np, int n, int k, const int* __restrict__ pverts, const int* __restrict__ bptr,
+                           const int* __restrict__ bcol, const double* __restrict__ F, const double* __restrict__ D,
+                           const double* __restrict__ yP, const double* __restrict__ xR, double* __restrict__ out) {
+  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (a >= np) return;
+  double acc[KMAX];
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) acc[i] = 0.0;
+  for (int bi = bptr[a] + lane; bi < bptr[a + 1]; bi += 32) {
+    const double* Fb = F + (size_t)bi * k * k;
+    const double* xr = xR + (size_t)bcol[bi] * k;
+    for (int c = 0; c < k; ++c) {
+      const double xc = xr[c];
+#pragma unroll
+      for (int i = 0; i < KMAX; ++i)
+        if (i < k) acc[i] = fma(Fb[i * k + c], xc, acc[i]);
+    }
+  }
+  double z[KMAX];
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) z[i] = (i < k) ? yP[(size_t)a * k + i] - hs_warp_sum(acc[i]) : 0.0;
+  if (lane != 0) return;
+  const double* La = D + (size_t)a * k * k;
+  const int v = pverts[a];
+  for (int i = k - 1; i >= 0; --i) {
+    double s = z[i];
+    for (int j = i + 1; j < k; ++j) s -= La[j * k + i] * z[j];
+    z[i] = s / La[i * k + i];
+    out[(size_t)i * n + v] = z[i];
+  }
+}
+
+__global__ void k_hat_outR(int nr, int n, int k, const int* __restrict__ rverts, const double* __restrict__ xR,
+                           double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nr * k) return;
+  const int r = t / k, l = t % k;
+  out[(size_t)l * n + rverts[r]] = xR[t];
+}
+
+// ---------------------------------------------------------------------------
+// Host entry points
+// ---------------------------------------------------------------------------
+sdp_status schur_alloc(sdp_problem* h, int k) {
+  if (h->hs_D && h->hs_k == k) return SDP_OK;
+  const size_t np = h->hs_np, nb = h->hs_nb, Rk = (size_t)h->hs_nr * k;
+  SDP_TRY(h->allocT(&h->hs_D, std::max<size_t>(np * k * k, 1)));
+  SDP_TRY(h->allocT(&h->hs_F, std::max<size_t>(nb * k * k, 1)));
+  SDP_TRY(h->allocT(&h->hs_yP, std::max<size_t>(np * k, 1)));
+  SDP_TRY(h->allocT(&h->hs_C, std::max<size_t>(Rk * Rk, 1)));
+  SDP_TRY(h->allocT(&h->hs_Cinv, std::max<size_t>(Rk * Rk, 1)));
+  SDP_TRY(h->allocT(&h->hs_v1, std::max<size_t>(Rk, 1)));
+  SDP_TRY(h->allocT(&h->hs_v2, std::max<size_t>(Rk, 1)));
+  SDP_TRY(h->allocT(&h->hs_v3, std::max<size_t>(Rk, 1)));
+  const size_t wneed = std::max(potrf_work_doubles((int)Rk), trsm_work_doubles((int)Rk, (int)Rk));
+  if (wneed > h->work_doubles) {
+    SDP_TRY(h->allocT(&h->work, wneed));
+    h->work_doubles = wneed;
+  }
+  h->hs_k = k;   // trmv partials: h->trpart holds those of order n k >= R k
+  return SDP_OK;
+}
+
+// Core of Hhat (needs h->au = A_i u_l on the support rows) -> L_P, F, L_C, L_C^{-1}.
+sdp_status schur_build(sdp_problem* h, int k, double tau) {
+  if (k > KMAX) {
+    h->last_error = "precond_build: the sparse Hhat core supports k <= 8";
+    return SDP_ERR_UNSUPPORTED;
+  }
+  SDP_TRY(schur_alloc(h, k));
+  cudaStream_t st = h->stream;
+  const int np = h->hs_np, nr = h->hs_nr, nb = h->hs_nb, Rk = nr * k;
+  const double tau2 = tau * tau;
+  fill(st, h->hs_D, (size_t)np * k * k, 0.0);
+  if (Rk > 0) fill(st, h->hs_C, (size_t)Rk * Rk, 0.0);
+  cudaMemsetAsync(h->info, 0, 2 * sizeof(int), st);
+  count_launch();
+  k_hat_scatter<<<cdiv((size_t)h->nnzK * k, 128), 128, 0, st>>>(h->nnzK, k, h->kptr, h->kcon, h->kcra, h->kcrb,
+                                                               h->ginv, h->au, 2.0 * tau, h->hs_stype, h->hs_sa,
+                                                               h->hs_sb, h->hs_D, h->hs_F, h->hs_C, Rk);
+  if (np > 0) {
+    count_launch();
+    k_hat_factor_D<<<cdiv(np, 128), 128, 0, st>>>(np, k, tau2, h->hs_D, h->info);
+  }
+  if (nb > 0) {
+    count_launch(2);
+    k_hat_F<<<cdiv((size_t)nb * k, 128), 128, 0, st>>>(nb, k, h->hs_bp, h->hs_D, h->hs_F);
+    k_hat_schur_rows<<<nr, 256, 0, st>>>(k, Rk, h->hs_btptr, h->hs_btslot, h->hs_bp, h->hs_bptr, h->hs_bcol,
+                                         h->hs_F, h->hs_C);
+  }
+  int floored = 0;
+  if (Rk > 0) {
+    add_diag(st, Rk, h->hs_C, Rk, tau2);
+    // a Schur complement of S >= tau^2 I is >= tau^2 I as well
+    int inf0[2] = {0, 0};
+    SDP_CK(h, cudaMemcpyAsync(inf0, h->info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SDP_CK(h, cudaStreamSynchronize(st));
+    floored = inf0[1];
+    potrf_floor(st, Rk, h->hs_C, Rk, h->info, h->work, tau2);
+    fill(st, h->hs_Cinv, (size_t)Rk * Rk, 0.0);
+    add_diag(st, Rk, h->hs_Cinv, Rk, 1.0);
+    trsm_left_lower_ex(st, false, Rk, Rk, h->hs_C, Rk, h->hs_Cinv, Rk, h->work, true);
+  }
+  int inf2[2] = {0, 0};
+  SDP_CK(h, cudaMemcpyAsync(inf2, h->info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  SDP_CK(h, cudaStreamSynchronize(st));
+  h->core_floor_pivots = floored + inf2[1];
+  return SDP_OK;
+}
+
+// out = S^{-1} u  (both k x n, u[l n + c]); u is not modified.
+sdp_status schur_apply(sdp_problem* h, const double* u, double* out) {
+  cudaStream_t st = h->stream;
+  const int n = h->n, k = h->hs_k, np = h->hs_np, nr = h->hs_nr, Rk = nr * k;
+  if (np > 0) {
+    count_launch();
+    k_hat_fwdP<<<cdiv(np, 128), 128, 0, st>>>(np, n, k, h->hs_pverts, h->hs_D, u, h->hs_yP);
+  }
+  if (Rk > 0) {
+    count_launch();
+    k_hat_fwdR<<<cdiv((size_t)nr * 32, 256), 256, 0, st>>>(nr, n, k, h->hs_rverts, h->hs_btptr, h->hs_btslot,
+                                                            h->hs_bp, h->hs_F, h->hs_yP, u, h->hs_v1);
+    // y_R = L_C^{-1} t_R and x_R = L_C^{-T} y_R, each with one refinement step
+    double* in = h->hs_v1;
+    double* y0 = h->hs_v2;
+    double* res = h->hs_v3;
+    for (int t = 0; t < 2; ++t) {
+      const bool tr = (t == 1);
+      trmv_lower_ex(st, tr, Rk, h->hs_Cinv, Rk, in, y0, h->trpart, 1.0, nullptr, 0.0);
+      for (int it = 0; it < h->core_refine; ++it) {
+        trmv_lower_ex(st, tr, Rk, h->hs_C, Rk, y0, res, h->trpart, -1.0, in, 1.0);
+        trmv_lower_ex(st, tr, Rk, h->hs_Cinv, Rk, res, y0, h->trpart, 1.0, y0, 1.0);
+      }
+      std::swap(in, y0);   // result becomes the input of the next solve
+    }
+    // `in` holds x_R
+    count_launch();
+    k_hat_outR<<<cdiv(Rk, 128), 128, 0, st>>>(nr, n, k, h->hs_rverts, in, out);
+    if (np > 0) {
+      count_launch();
+      k_hat_bwdP<<<cdiv((size_t)np * 32, 256), 256, 0, st>>>(np, n, k, h->hs_pverts, h->hs_bptr, h->hs_bcol,
+                                                              h->hs_F, h->hs_D, h->hs_yP, in, out);
+    }
+  } else if (np > 0) {
+    count_launch();
+    k_hat_bwdP<<<cdiv((size_t)np * 32, 256), 256, 0, st>>>(np, n, k, h->hs_pverts, h->hs_bptr, h->hs_bcol,
+                                                            h->hs_F, h->hs_D, h->hs_yP, nullptr, out);
+  }
+  return SDP_OK;
+}
+
+}  // namespace sdpgb

@@ -239,6 +239,11 @@ static sdp_status build(sdp_problem* h, int64_t nnzC, const int32_t* Ci, const i
   h->ncr = (int)crrow.size();
   h->nnzK = (int)kcol.size();
   h->nkc = (int)kcon.size();
+  SchurPlanHost sp;
+  schur_plan(n, krowptr, kcol, &sp);
+  h->hs_np = (int)sp.pverts.size();
+  h->hs_nr = (int)sp.rverts.size();
+  h->hs_nb = (int)sp.bcol.size();
 
   // ---- dense C, b, norms, start point
   std::vector<double> Cd((size_t)n * n, 0.0);
@@ -291,6 +296,16 @@ static sdp_status build(sdp_problem* h, int64_t nnzC, const int32_t* Ci, const i
   SDP_TRY(upload(h, &h->kcon, kcon));
   SDP_TRY(upload(h, &h->kcra, kcra));
   SDP_TRY(upload(h, &h->kcrb, kcrb));
+  SDP_TRY(upload(h, &h->hs_pverts, sp.pverts));
+  SDP_TRY(upload(h, &h->hs_rverts, sp.rverts));
+  SDP_TRY(upload(h, &h->hs_stype, sp.stype));
+  SDP_TRY(upload(h, &h->hs_sa, sp.sa));
+  SDP_TRY(upload(h, &h->hs_sb, sp.sb));
+  SDP_TRY(upload(h, &h->hs_bptr, sp.bptr));
+  SDP_TRY(upload(h, &h->hs_bcol, sp.bcol));
+  SDP_TRY(upload(h, &h->hs_bp, sp.bp));
+  SDP_TRY(upload(h, &h->hs_btptr, sp.btptr));
+  SDP_TRY(upload(h, &h->hs_btslot, sp.btslot));
   SDP_TRY(upload(h, &h->C, Cd));
   std::vector<double> bv(b, b + m);
   SDP_TRY(upload(h, &h->b, bv));
@@ -375,6 +390,7 @@ extern "C" sdp_status sdp_set_state(sdp_problem* h, const double* X_host, const 
   SDP_CK(h, cudaMemcpyAsync(h->S, S_host, nn * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   SDP_CK(h, cudaStreamSynchronize(h->stream));
   h->iter = iter;
+  h->chol_valid = false;
   h->pc_valid = false;
   return SDP_OK;
 }
@@ -458,6 +474,7 @@ extern "C" sdp_status sdp_reset(sdp_problem* h) {
   add_diag(h->stream, h->n, h->S, h->n, h->xi);
   SDP_CK(h, cudaMemsetAsync(h->y, 0, h->m * sizeof(double), h->stream));
   h->iter = 0;
+  h->chol_valid = false;
   h->have_W = false;
   h->pc_valid = false;
   h->W32_valid = h->W16_valid = false;

@@ -3,7 +3,10 @@
 // recycled pool; nothing is recorded unless a class is enabled.
 #include "internal.cuh"
 
+#include <algorithm>
+#include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -14,13 +17,17 @@ namespace {
 struct Pending {
   cudaEvent_t a, b;
   double flops, bytes;
+  const char* cls;
+};
+struct Acc {
+  double ms = 0, flops = 0, bytes = 0;
+  int64_t count = 0;
 };
 std::mutex g_mu;
-std::string g_cls;
+std::string g_cls;                  // recorded class, or "*" for every class
 std::vector<cudaEvent_t> g_pool;
 std::vector<Pending> g_pending;
-double g_ms = 0, g_flops = 0, g_bytes = 0;
-int64_t g_count = 0;
+std::map<std::string, Acc> g_acc;   // per class
 
 cudaEvent_t take() {
   if (!g_pool.empty()) {
@@ -38,10 +45,11 @@ void drain() {
     float ms = 0.f;
     cudaEventSynchronize(p.b);
     cudaEventElapsedTime(&ms, p.a, p.b);
-    g_ms += ms;
-    g_flops += p.flops;
-    g_bytes += p.bytes;
-    g_count++;
+    Acc& a = g_acc[p.cls];
+    a.ms += ms;
+    a.flops += p.flops;
+    a.bytes += p.bytes;
+    a.count++;
     g_pool.push_back(p.a);
     g_pool.push_back(p.b);
   }
@@ -49,27 +57,30 @@ void drain() {
 }
 }  // namespace
 
-thread_local bool g_paused = false;   // per host thread: set while this thread captures a graph
-bool ktimer_on(const char* cls) { return !g_paused && !g_cls.empty() && g_cls == cls; }
+// per host thread: set while this thread captures a graph
+thread_local bool g_paused = false;
+bool ktimer_on(const char* cls) { return !g_paused && !g_cls.empty() && (g_cls == "*" || g_cls == cls); }
 void ktimer_pause(bool paused) { g_paused = paused; }
 
-// One open event per thread: launches of a class are not nested.
-thread_local cudaEvent_t t_open = nullptr;
+// Open regions of this thread (classes may nest when every class is recorded).
+thread_local std::vector<std::pair<const char*, cudaEvent_t>> t_open;
 
 void ktimer_begin(cudaStream_t st, const char* cls) {
   if (!ktimer_on(cls)) return;
   std::lock_guard<std::mutex> lk(g_mu);
-  t_open = take();
-  cudaEventRecord(t_open, st);
+  cudaEvent_t e = take();
+  cudaEventRecord(e, st);
+  t_open.push_back({cls, e});
 }
 
 void ktimer_end(cudaStream_t st, const char* cls, double flops, double bytes) {
-  if (!ktimer_on(cls) || !t_open) return;
+  if (!ktimer_on(cls) || t_open.empty()) return;
   std::lock_guard<std::mutex> lk(g_mu);
+  auto top = t_open.back();
+  t_open.pop_back();
   cudaEvent_t b = take();
   cudaEventRecord(b, st);
-  g_pending.push_back({t_open, b, flops, bytes});
-  t_open = nullptr;
+  g_pending.push_back({top.second, b, flops, bytes, cls});
   if (g_pending.size() > 4096) drain();
 }
 
@@ -82,12 +93,40 @@ void ktimer_set(const char* cls) {
 void ktimer_read(double* ms, int64_t* launches, double* flops, double* bytes) {
   std::lock_guard<std::mutex> lk(g_mu);
   drain();
-  if (ms) *ms = g_ms;
-  if (launches) *launches = g_count;
-  if (flops) *flops = g_flops;
-  if (bytes) *bytes = g_bytes;
-  g_ms = g_flops = g_bytes = 0;
-  g_count = 0;
+  Acc t;
+  for (auto& kv : g_acc) {
+    if (g_cls == "*" || kv.first == g_cls) {
+      t.ms += kv.second.ms;
+      t.flops += kv.second.flops;
+      t.bytes += kv.second.bytes;
+      t.count += kv.second.count;
+    }
+  }
+  if (ms) *ms = t.ms;
+  if (launches) *launches = t.count;
+  if (flops) *flops = t.flops;
+  if (bytes) *bytes = t.bytes;
+  g_acc.clear();
+}
+
+// "class ms launches flops bytes" per line, then clears the accumulators
+size_t ktimer_report(char* buf, size_t len) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  drain();
+  std::string s;
+  char line[256];
+  for (auto& kv : g_acc) {
+    snprintf(line, sizeof(line), "%s %.6f %lld %.6e %.6e\n", kv.first.c_str(), kv.second.ms,
+             (long long)kv.second.count, kv.second.flops, kv.second.bytes);
+    s += line;
+  }
+  g_acc.clear();
+  if (buf && len > 0) {
+    const size_t c = std::min(len - 1, s.size());
+    memcpy(buf, s.data(), c);
+    buf[c] = 0;
+  }
+  return s.size() + 1;
 }
 
 void allow_max_smem(const void* func) {
@@ -113,6 +152,12 @@ extern "C" sdp_status sdp_timing_enable(sdp_problem* h, const char* cls) {
   if (!h) return SDP_ERR_ARG;
   sdpgb::ktimer_set(cls);
   return SDP_OK;
+}
+
+extern "C" int64_t sdp_timing_report(sdp_problem* h, char* buf, int64_t len) {
+  if (!h) return -1;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  return (int64_t)sdpgb::ktimer_report(buf, len > 0 ? (size_t)len : 0);
 }
 
 extern "C" sdp_status sdp_timing_read(sdp_problem* h, double* ms, int64_t* launches, double* flops, double* bytes) {

@@ -329,3 +329,24 @@ def test_solve_general_sparse_planted():
     assert _rel(X, Xs) <= 1e-5 and _rel(X, ref.X) <= 1e-5
     cert = o.kkt_certificate(P, X, y, S)
     assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6 and cert["relgap"] <= 1e-6
+
+
+@pytest.mark.parametrize("idx", [3, 14])
+def test_solve_batched_instance_matches_oracle(idx):
+    """Batched-workload instances (n >= 64: Lanczos step lengths, Hhat preconditioner,
+    checked updates) reach the oracle's optimum and recover the planted matrix."""
+    s = si.batched_specs(256)[idx]
+    d = si.mc_instance(s["p"], s["q"], s["r"], s["m"], s["seed"])
+    P = o.Problem.from_data(d)
+    ref = o.ipm_solve(P)
+    assert ref.converged
+    with _prob(d) as prob:
+        res = prob.solve()
+        X, y, S = prob.get_solution()
+    assert res["converged"] and res["relgap"] <= 1e-6
+    assert abs(res["obj_p"] - ref.obj_p) <= 1e-6 * abs(ref.obj_p)
+    Z = o.mc_recovered(P, X)
+    assert _rel(Z, o.mc_recovered(P, ref.X)) <= 1e-4
+    assert _rel(Z, d.meta["M"]) <= 1e-4
+    cert = o.kkt_certificate(P, X, y, S)
+    assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6 and cert["relgap"] <= 1e-6
