@@ -71,7 +71,7 @@ typedef struct {
   double step_frac;    /* fraction of the step to the boundary; 0.9                */
   int prec;            /* sdp_prec used inside PCG by sdp_ipm_step / sdp_solve     */
   int precond;         /* sdp_precond_kind; SDP_PRECOND_HAT                        */
-  double inner_rtol;   /* PCG tolerance of one restart (sweep); 1e-4                */
+  double inner_rtol;   /* PCG tolerance of one restart (sweep); 1e-9                */
   int verbose;         /* 1 = one line per IPM iteration on stderr                 */
   int pcg_graph;       /* 1 = the PCG loop runs on the device as a CUDA graph with */
                        /* a conditional while node (default); 0 = host-driven     */

@@ -385,59 +385,97 @@ void trmv_lower(cudaStream_t st, bool trans, int n, const double* L, int ldl, co
 // ---------------------------------------------------------------------------
 constexpr int NB = 64;
 
-// Factor the nbs x nbs diagonal block in place (lower).
+// Factor the nbs x nbs (nbs <= BS) diagonal block in place (lower).  256
+// threads; thread t keeps the BS^2 / 256 entries (i, l) with l = t % BS and
+// i = t / BS + (256 / BS) s in registers.  Per column j: the owner of (j, j)
+// forms the pivot, the owners of column j scale it and publish it to shared
+// memory, and every thread applies the rank-1 update to its entries -- two
+// barriers per column and one reciprocal instead of a division per entry.  The
+// published column alternates between two buffers, so the writers of column
+// j + 1 never overwrite a value that a thread still finishing step j reads.
+// FP64 issue slots are the scarce resource on this GPU (a warp instruction
+// costs the same with most lanes masked), so the factorisation uses 32 x 32
+// diagonal blocks: the per-column work of every thread stays at 4 entries.
+template <int BS>
 __global__ void __launch_bounds__(256) k_potrf_diag(int nbs, double* A, int lda, int* info, int base,
                                                     double floor_) {
-  extern __shared__ double sm[];
-  double* a = sm;                  // NB x (NB+1)
-  constexpr int LD = NB + 1;
-  for (int t = threadIdx.x; t < nbs * nbs; t += blockDim.x) {
-    const int i = t / nbs, j = t % nbs;
-    a[i * LD + j] = (j <= i) ? A[(size_t)i * lda + j] : 0.0;
+  constexpr int RS = 256 / BS;        // row stride of a thread's entries
+  constexpr int PER = BS / RS;        // entries per thread
+  __shared__ double colbuf[2][BS];
+  __shared__ double s_rinv;
+  const int t = threadIdx.x;
+  const int l = t % BS, i0 = t / BS;
+  double a[PER];
+#pragma unroll
+  for (int s = 0; s < PER; ++s) {
+    const int i = i0 + RS * s;
+    a[s] = (i < nbs && l < nbs && l <= i) ? A[(size_t)i * lda + l] : 0.0;
   }
-  __syncthreads();
   for (int j = 0; j < nbs; ++j) {
-    if (threadIdx.x == 0) {
-      double p = a[j * LD + j];
-      if (floor_ > 0.0) {
-        // the matrix is known to satisfy A >= floor I, so every Cholesky pivot
-        // (a Schur-complement diagonal) is >= floor; smaller ones are rounding
-        if (!(p >= floor_)) {
-          if (info) atomicAdd(info + 1, 1);
-          p = floor_;
+    double* colj = colbuf[j & 1];
+    if (l == j) {
+#pragma unroll
+      for (int s = 0; s < PER; ++s) {
+        if (i0 + RS * s != j) continue;
+        double p = a[s];
+        if (floor_ > 0.0) {
+          // the matrix is known to satisfy A >= floor I, so every Cholesky pivot
+          // (a Schur-complement diagonal) is >= floor; smaller ones are rounding
+          if (!(p >= floor_)) {
+            if (info) atomicAdd(info + 1, 1);
+            p = floor_;
+          }
+        } else if (!(p > 0.0)) {
+          if (info && *info == 0) *info = base + j + 1;
+          p = 1.0;
         }
-      } else if (!(p > 0.0)) {
-        if (info && *info == 0) *info = base + j + 1;
-        p = 1.0;
+        const double dj = sqrt(p);
+        a[s] = dj;
+        colj[j] = dj;
+        s_rinv = 1.0 / dj;
       }
-      a[j * LD + j] = sqrt(p);
     }
     __syncthreads();
-    const double ljj = a[j * LD + j];
-    for (int i = j + 1 + threadIdx.x; i < nbs; i += blockDim.x) a[i * LD + j] /= ljj;
-    __syncthreads();
-    const int w = nbs - j - 1;
-    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-      const int i = j + 1 + t / w, l = j + 1 + t % w;
-      if (l <= i) a[i * LD + l] -= a[i * LD + j] * a[l * LD + j];
+    if (l == j) {
+      const double r = s_rinv;
+#pragma unroll
+      for (int s = 0; s < PER; ++s) {
+        const int i = i0 + RS * s;
+        if (i > j && i < nbs) {
+          a[s] *= r;
+          colj[i] = a[s];
+        }
+      }
     }
     __syncthreads();
+    if (l > j && l < nbs) {
+      const double cl = colj[l];
+#pragma unroll
+      for (int s = 0; s < PER; ++s) {
+        const int i = i0 + RS * s;
+        if (i >= l && i < nbs) a[s] = fma(-colj[i], cl, a[s]);
+      }
+    }
   }
-  for (int t = threadIdx.x; t < nbs * nbs; t += blockDim.x) {
-    const int i = t / nbs, j = t % nbs;
-    A[(size_t)i * lda + j] = (j <= i) ? a[i * LD + j] : 0.0;
+#pragma unroll
+  for (int s = 0; s < PER; ++s) {
+    const int i = i0 + RS * s;
+    if (i < nbs && l < nbs) A[(size_t)i * lda + l] = (l <= i) ? a[s] : 0.0;
   }
 }
 
-// Substitution solves with one NB x NB diagonal block (L in shared memory, the
-// reciprocal of its diagonal precomputed).  Solving by substitution instead of
-// multiplying with an explicitly inverted block keeps the componentwise
-// accuracy of triangular solves, which the core of the Woodbury preconditioner
-// needs late in the interior-point method.
-//   left:  op(Lbb) X = B  for a kbs x nrhs block B, one thread per column
-//   right: X Lbb^T = P    for a rows x kbs panel P, one thread per row
-__global__ void __launch_bounds__(128) k_trsm_sub_left(int kbs, bool trans, const double* __restrict__ L, int ldl,
-                                                       double* __restrict__ B, int ldb, int nrhs) {
+// Triangular solves with one kbs x kbs (kbs <= 64) diagonal block of L, one warp
+// per right-hand-side vector: vector v has its entries at x0 + v * vstride +
+// i * estride.  Lane q holds entries q and q + 32 in registers; column by column
+// the finished entry is broadcast by a shuffle and the remaining entries are
+// updated (no division: the reciprocals of the diagonal are precomputed).
+//   trans = false:  L x = b  (forward);   trans = true:  L^T x = b  (backward)
+// The right solve X L^T = P of the Cholesky panel is the forward solve on each
+// row of P.
+constexpr int TRSV_WARPS = 4;
+__global__ void __launch_bounds__(32 * TRSV_WARPS) k_trsv_warp(int kbs, bool trans, const double* __restrict__ L,
+                                                               int ldl, double* __restrict__ X, int nvec,
+                                                               int vstride, int estride) {
   __shared__ double sl[NB][NB + 1];
   __shared__ double rd[NB];
   for (int t = threadIdx.x; t < kbs * kbs; t += blockDim.x) {
@@ -447,41 +485,32 @@ __global__ void __launch_bounds__(128) k_trsm_sub_left(int kbs, bool trans, cons
   __syncthreads();
   for (int i = threadIdx.x; i < kbs; i += blockDim.x) rd[i] = 1.0 / sl[i][i];
   __syncthreads();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nrhs) return;
+  const int lane = threadIdx.x & 31;
+  const int v = blockIdx.x * TRSV_WARPS + (threadIdx.x >> 5);
+  if (v >= nvec) return;
+  double* x = X + (size_t)v * vstride;
+  const int e0 = lane, e1 = lane + 32;
+  double x0 = (e0 < kbs) ? x[(size_t)e0 * estride] : 0.0;
+  double x1 = (e1 < kbs) ? x[(size_t)e1 * estride] : 0.0;
   if (!trans) {
-    for (int i = 0; i < kbs; ++i) {
-      double s = B[(size_t)i * ldb + c];
-      for (int l = 0; l < i; ++l) s = fma(-sl[i][l], B[(size_t)l * ldb + c], s);
-      B[(size_t)i * ldb + c] = s * rd[i];
+    for (int j = 0; j < kbs; ++j) {
+      const double xj = __shfl_sync(0xffffffffu, (j < 32) ? x0 : x1, j & 31) * rd[j];
+      if (e0 == j) x0 = xj;
+      if (e1 == j) x1 = xj;
+      if (e0 > j && e0 < kbs) x0 = fma(-sl[e0][j], xj, x0);
+      if (e1 > j && e1 < kbs) x1 = fma(-sl[e1][j], xj, x1);
     }
   } else {
-    for (int i = kbs - 1; i >= 0; --i) {
-      double s = B[(size_t)i * ldb + c];
-      for (int l = i + 1; l < kbs; ++l) s = fma(-sl[l][i], B[(size_t)l * ldb + c], s);
-      B[(size_t)i * ldb + c] = s * rd[i];
+    for (int j = kbs - 1; j >= 0; --j) {
+      const double xj = __shfl_sync(0xffffffffu, (j < 32) ? x0 : x1, j & 31) * rd[j];
+      if (e0 == j) x0 = xj;
+      if (e1 == j) x1 = xj;
+      if (e0 < j) x0 = fma(-sl[j][e0], xj, x0);
+      if (e1 < j) x1 = fma(-sl[j][e1], xj, x1);
     }
   }
-}
-__global__ void __launch_bounds__(128) k_trsm_sub_right_lt(int kbs, const double* __restrict__ L, int ldl,
-                                                           double* __restrict__ P, int ldp, int rows) {
-  __shared__ double sl[NB][NB + 1];
-  __shared__ double rd[NB];
-  for (int t = threadIdx.x; t < kbs * kbs; t += blockDim.x) {
-    const int i = t / kbs, j = t % kbs;
-    sl[i][j] = (j <= i) ? L[(size_t)i * ldl + j] : 0.0;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kbs; i += blockDim.x) rd[i] = 1.0 / sl[i][i];
-  __syncthreads();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= rows) return;
-  double* pr = P + (size_t)r * ldp;
-  for (int j = 0; j < kbs; ++j) {
-    double s = pr[j];
-    for (int l = 0; l < j; ++l) s = fma(-pr[l], sl[j][l], s);
-    pr[j] = s * rd[j];
-  }
+  if (e0 < kbs) x[(size_t)e0 * estride] = x0;
+  if (e1 < kbs) x[(size_t)e1 * estride] = x1;
 }
 
 size_t potrf_work_doubles(int n) { return (size_t)NB * NB + (size_t)n * NB; }
@@ -493,23 +522,23 @@ void potrf(cudaStream_t st, int n, double* A, int lda, int* info_dev, double* wo
 // Cholesky of a matrix known to satisfy A >= floor I (floor > 0): pivots below
 // floor are raised to floor and counted in info_dev[1] instead of failing.
 void potrf_floor(cudaStream_t st, int n, double* A, int lda, int* info_dev, double* work, double floor_) {
-  const size_t smem = NB * (NB + 1) * sizeof(double);
-  allow_max_smem((const void*)k_potrf_diag);
+
   (void)work;
   ktimer_begin(st, "potrf");
   cudaMemsetAsync(info_dev, 0, 2 * sizeof(int), st);
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kbs = std::min(NB, n - k0);
+  constexpr int PB = 32;   // diagonal block of the factorisation (see k_potrf_diag)
+  for (int k0 = 0; k0 < n; k0 += PB) {
+    const int kbs = std::min(PB, n - k0);
     double* Akk = A + (size_t)k0 * lda + k0;
     count_launch();
-    k_potrf_diag<<<1, 256, smem, st>>>(kbs, Akk, lda, info_dev, k0, floor_);
+    k_potrf_diag<PB><<<1, 256, 0, st>>>(kbs, Akk, lda, info_dev, k0, floor_);
     const int r0 = k0 + kbs;
     const int rows = n - r0;
     if (rows <= 0) break;
     double* P = A + (size_t)r0 * lda + k0;
-    // panel: P <- P L_kk^{-T} by substitution (row per thread)
+    // panel: P <- P L_kk^{-T}, a forward solve on each row (one warp per row)
     count_launch();
-    k_trsm_sub_right_lt<<<cdiv(rows, 128), 128, 0, st>>>(kbs, Akk, lda, P, lda, rows);
+    k_trsv_warp<<<cdiv(rows, TRSV_WARPS), 32 * TRSV_WARPS, 0, st>>>(kbs, false, Akk, lda, P, rows, lda, 1);
     // trailing: A22 -= P P^T (lower tiles only)
     gemm(st, false, true, rows, rows, kbs, -1.0, P, lda, P, lda, 1.0, A + (size_t)r0 * lda + r0, lda, 1);
   }
@@ -541,7 +570,8 @@ void trsm_left_lower_ex(cudaStream_t st, bool trans, int n, int nrhs, const doub
       const int nc = lower_rhs ? std::min(nrhs, k0 + kbs) : nrhs;
       double* Bk = B + (size_t)k0 * ldb;
       count_launch();
-      k_trsm_sub_left<<<cdiv(nc, 128), 128, 0, st>>>(kbs, false, L + (size_t)k0 * ldl + k0, ldl, Bk, ldb, nc);
+      k_trsv_warp<<<cdiv(nc, TRSV_WARPS), 32 * TRSV_WARPS, 0, st>>>(kbs, false, L + (size_t)k0 * ldl + k0, ldl, Bk, nc,
+                                                                    1, ldb);
       const int r0 = k0 + kbs;
       if (r0 < n)
         gemm(st, false, false, n - r0, nc, kbs, -1.0, L + (size_t)r0 * ldl + k0, ldl, Bk, ldb, 1.0,
@@ -552,7 +582,8 @@ void trsm_left_lower_ex(cudaStream_t st, bool trans, int n, int nrhs, const doub
       const int k0 = b * NB, kbs = std::min(NB, n - k0);
       double* Bk = B + (size_t)k0 * ldb;
       count_launch();
-      k_trsm_sub_left<<<cdiv(nrhs, 128), 128, 0, st>>>(kbs, true, L + (size_t)k0 * ldl + k0, ldl, Bk, ldb, nrhs);
+      k_trsv_warp<<<cdiv(nrhs, TRSV_WARPS), 32 * TRSV_WARPS, 0, st>>>(kbs, true, L + (size_t)k0 * ldl + k0, ldl, Bk,
+                                                                      nrhs, 1, ldb);
       if (k0 > 0)
         gemm(st, true, false, k0, nrhs, kbs, -1.0, L + (size_t)k0 * ldl, ldl, Bk, ldb, 1.0, B, ldb);
     }

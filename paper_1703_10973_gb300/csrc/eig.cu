@@ -16,12 +16,16 @@
 //     no inter-CTA communication).
 #include "internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
 #include <algorithm>
+
+namespace cg = cooperative_groups;
 
 namespace sdpgb {
 
@@ -178,6 +182,169 @@ __global__ void __launch_bounds__(256) k_sytrd(int n, double* A, int lda, double
   }
 }
 
+// Cluster form for small n: one thread-block cluster of SY_CS CTAs, so that
+// the two barriers per column are hardware cluster barriers instead of grid
+// barriers through global atomics, and the rest of the GPU stays free for
+// other problems.  A stays in global memory (L2); warp g of the cluster owns
+// rows i = g mod (number of warps) for the whole reduction.  Per column j:
+//   every CTA rebuilds the reflector from row j (loaded through L2);
+//   p_i = tau A22[i, :] v for the owned rows, each p_i broadcast into every
+//   CTA's shared memory, and the CTA's share of p^T v likewise;
+//   cluster barrier;  w = p - (tau / 2)(p^T v) v;  owned rows updated;
+//   cluster barrier (row j + 1 is complete before anyone reads it).
+// The shared arrays written remotely in column j + 1 are only read in steps of
+// column j that precede its second barrier, so no buffer is overwritten early.
+constexpr int SY_THREADS = 512;
+__global__ void __launch_bounds__(SY_THREADS) k_sytrd_cluster(int n, double* A, int lda, double* d, double* e,
+                                                               double* tauh) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cs = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ double sm[];
+  double* v = sm;            // n
+  double* w = sm + n;        // n
+  double* p = sm + 2 * n;    // n   (written by every CTA)
+  __shared__ double kpart[32];  // one partial of p^T v per CTA of the cluster
+  __shared__ double red[32];
+  __shared__ double s_tau, s_beta, s_scale;
+  const int wpb = blockDim.x / 32, wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int gwarp = rank * wpb + wid, nwarps = cs * wpb;
+
+  for (int j = 0; j < n - 2; ++j) {
+    const int len = n - j - 1;
+    const double* row = A + (size_t)j * lda + j + 1;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      const double x = __ldcg(row + i);
+      v[i] = x;
+      if (i > 0) s = fma(x, x, s);
+    }
+    s = bsum(s, red);
+    if (threadIdx.x == 0) {
+      const double x0 = v[0];
+      double tau = 0.0, beta = x0, scale = 0.0;
+      if (s > 0.0) {
+        beta = -copysign(sqrt(fma(x0, x0, s)), x0);
+        tau = (beta - x0) / beta;
+        scale = 1.0 / (x0 - beta);
+      }
+      s_tau = tau; s_beta = beta; s_scale = scale;
+    }
+    __syncthreads();
+    const double tau = s_tau, scale = s_scale;
+    for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) v[i] *= scale;
+    if (threadIdx.x == 0) v[0] = 1.0;
+    __syncthreads();
+    // owned rows: first owned row index >= j + 1
+    double kp = 0.0;
+    int i = gwarp + ((j + 1 - gwarp + nwarps - 1) / nwarps) * nwarps;
+    if (gwarp >= j + 1) i = gwarp;
+    for (; i < n; i += nwarps) {
+      const double* ai = A + (size_t)i * lda + j + 1;
+      // four independent accumulators keep four L2 loads in flight per lane
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int l = lane;
+      for (; l + 96 < len; l += 128) {
+        const double x0 = __ldcg(ai + l), x1 = __ldcg(ai + l + 32), x2 = __ldcg(ai + l + 64),
+                     x3 = __ldcg(ai + l + 96);
+        a0 = fma(x0, v[l], a0);
+        a1 = fma(x1, v[l + 32], a1);
+        a2 = fma(x2, v[l + 64], a2);
+        a3 = fma(x3, v[l + 96], a3);
+      }
+      for (; l < len; l += 32) a0 = fma(__ldcg(ai + l), v[l], a0);
+      double acc = wsum((a0 + a1) + (a2 + a3)) * tau;
+      if (lane < cs) {
+        double* dst = cluster.map_shared_rank(p, lane);
+        dst[i - j - 1] = acc;
+      }
+      if (lane == 0) kp = fma(acc, v[i - j - 1], kp);
+    }
+    kp = bsum(kp, red);                                  // valid in thread 0
+    const double kp0 = __shfl_sync(0xffffffffu, kp, 0);  // warp 0: every lane gets it
+    if (threadIdx.x < cs) {
+      double* dst = cluster.map_shared_rank(kpart, (int)threadIdx.x);
+      dst[rank] = kp0;
+    }
+    cluster.sync();
+    double K = 0.0;
+    for (int c = 0; c < cs; ++c) K += kpart[c];
+    K *= 0.5 * tau;
+    for (int l = threadIdx.x; l < len; l += blockDim.x) w[l] = p[l] - K * v[l];
+    __syncthreads();
+    i = gwarp + ((j + 1 - gwarp + nwarps - 1) / nwarps) * nwarps;
+    if (gwarp >= j + 1) i = gwarp;
+    for (; i < n; i += nwarps) {
+      double* ai = A + (size_t)i * lda + j + 1;
+      const double vi = v[i - j - 1], wi = w[i - j - 1];
+      int l = lane;
+      for (; l + 96 < len; l += 128) {
+        const double x0 = __ldcg(ai + l), x1 = __ldcg(ai + l + 32), x2 = __ldcg(ai + l + 64),
+                     x3 = __ldcg(ai + l + 96);
+        ai[l] = x0 - fma(vi, w[l], wi * v[l]);
+        ai[l + 32] = x1 - fma(vi, w[l + 32], wi * v[l + 32]);
+        ai[l + 64] = x2 - fma(vi, w[l + 64], wi * v[l + 64]);
+        ai[l + 96] = x3 - fma(vi, w[l + 96], wi * v[l + 96]);
+      }
+      for (; l < len; l += 32) {
+        const double x = __ldcg(ai + l);
+        ai[l] = x - fma(vi, w[l], wi * v[l]);
+      }
+    }
+    if (rank == 0) {
+      double* rj = A + (size_t)j * lda + j + 1;
+      for (int l = threadIdx.x; l < len; l += blockDim.x) rj[l] = v[l];
+      if (threadIdx.x == 0) {
+        d[j] = __ldcg(A + (size_t)j * lda + j);
+        e[j] = s_beta;
+        tauh[j] = tau;
+      }
+    }
+    cluster.sync();
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    if (n >= 2) {
+      d[n - 2] = __ldcg(A + (size_t)(n - 2) * lda + n - 2);
+      e[n - 2] = __ldcg(A + (size_t)(n - 2) * lda + n - 1);
+      tauh[n - 2] = 0.0;
+    }
+    d[n - 1] = __ldcg(A + (size_t)(n - 1) * lda + n - 1);
+    e[n - 1] = 0.0;
+    if (n >= 2) tauh[n - 1] = 0.0;
+  }
+}
+
+// Cluster size for k_sytrd_cluster: 16 where the device allows it, else 8
+// (0 = cluster launch unavailable).
+static int sytrd_cluster_size(size_t smem) {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  allow_max_smem((const void*)k_sytrd_cluster);
+  cudaFuncSetAttribute((const void*)k_sytrd_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaGetLastError();
+  cached = 0;
+  for (int cs : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(SY_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, (const void*)k_sytrd_cluster, &cfg) == cudaSuccess && ncl > 0) {
+      cached = cs;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return cached;
+}
+
 static int sytrd_blocks(int n, size_t smem) {
   static int cached_sms = 0;
   if (!cached_sms) {
@@ -194,7 +361,36 @@ static int sytrd_blocks(int n, size_t smem) {
   return std::min(blocks, 4096);
 }
 
+// Up to this order the cluster form is faster (the cooperative grid form wins
+// once the O(n^3) work needs the whole GPU).
+constexpr int SY_CLUSTER_MAX_N = 1024;
+
 static sdp_status sytrd(cudaStream_t st, int n, double* A, EigWork* w) {
+  if (n <= SY_CLUSTER_MAX_N) {
+    const size_t csm = 3 * (size_t)n * sizeof(double);
+    const int cs = sytrd_cluster_size(200 * 1024);
+    if (cs > 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(SY_THREADS);
+      cfg.dynamicSmemBytes = csm;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int lda = n;
+      count_launch();
+      ktimer_begin(st, "sytrd");
+      cudaError_t err = cudaLaunchKernelEx(&cfg, k_sytrd_cluster, n, A, lda, w->d, w->e, w->tauh);
+      ktimer_end(st, "sytrd", 4.0 / 3.0 * n * (double)n * n, 24.0 * n * (double)n * n / 3.0);
+      if (err == cudaSuccess) return SDP_OK;
+      cudaGetLastError();
+    }
+  }
   const size_t smem = 2 * (size_t)n * sizeof(double);
   if (smem > 200 * 1024) return SDP_ERR_UNSUPPORTED;
   allow_max_smem((const void*)k_sytrd);
@@ -206,8 +402,10 @@ static sdp_status sytrd(cudaStream_t st, int n, double* A, EigWork* w) {
   count_launch();
   ktimer_begin(st, "sytrd");
   cudaError_t err = cudaLaunchCooperativeKernel((void*)k_sytrd, dim3(blocks), dim3(256), args, smem, st);
-  // per column: symv 2 len^2 + rank-2 update 4 len^2 flops; the trailing block is read twice, written once
-  ktimer_end(st, "sytrd", 2.0 * n * (double)n * n, 8.0 * n * (double)n * n);
+  // algorithmic work of the reduction: (4/3) n^3 flops (symmetric matrix-vector
+  // product and rank-2 update per column); the trailing block is read twice and
+  // written once per column: 3 * 8 * n^3 / 3 bytes
+  ktimer_end(st, "sytrd", 4.0 / 3.0 * n * (double)n * n, 24.0 * n * (double)n * n / 3.0);
   return err == cudaSuccess ? SDP_OK : SDP_ERR_CUDA;
 }
 

@@ -12,6 +12,52 @@
 #include "../../include/sdpgb.h"
 
 namespace sdpgb {
+// Deterministic grid-wide sum in one kernel: every block stores its partial in
+// part[blockIdx.x]; the last block to arrive (atomic ticket) adds the partials
+// in index order and, in its thread 0, returns true with the total in *total
+// (then re-arms the ticket).  Every thread of every block must call it.
+__device__ inline double lb_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline double lb_block_sum(double v, double* sh) {
+  v = lb_warp_sum(v);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (l < (int)(blockDim.x / 32)) ? sh[l] : 0.0;
+    s = lb_warp_sum(s);
+  }
+  return s;  // valid in thread 0
+}
+__device__ inline bool lb_reduce(double v, double* part, unsigned int* ticket, double* total) {
+  __shared__ double sh[32];
+  __shared__ int s_last;
+  const double b = lb_block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = b;
+    __threadfence();
+    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) s += __ldcg(part + i);
+  s = lb_block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    *total = s;
+    *ticket = 0u;
+  }
+  return threadIdx.x == 0;
+}
+}  // namespace sdpgb
+
+namespace sdpgb {
 const char* free_call_error();   // error text of the last handle-free call on this thread
 
 // ---------------------------------------------------------------------------
@@ -173,9 +219,10 @@ struct SchurPlanHost {
 };
 void schur_plan(int n, const std::vector<int>& krowptr, const std::vector<int>& kcol, SchurPlanHost* out);
 sdp_status schur_build(sdp_problem* h, int k, double tau);
-sdp_status schur_apply(sdp_problem* h, const double* u, double* out);
-sdp_status lanczos_min(cudaStream_t st, int n, const double* M, int ldm, double rtol, double accept_above,
-                       double* work, double* out_dev);
+sdp_status schur_apply(sdp_problem* h, const double* u, double* out, double scale);
+bool lanczos_fits(int n);
+sdp_status lanczos_min(cudaStream_t st, int n, const double* M, const double* A2, const double* A3, int ldm,
+                       double rtol, double accept_above, double* work, double* out_dev);
 // Smallest eigenvalue and the top-k eigenpairs: wtop[0..k) ascending (= lambda_{n-k..n-1}),
 // Etop rows = eigenvectors; *lmin_dev = lambda_0.
 sdp_status eig_extremes(cudaStream_t st, int n, double* A, int k, double* lmin_dev, double* wtop,
@@ -285,6 +332,9 @@ struct sdp_problem {
   double *L = nullptr, *Rs = nullptr, *M1 = nullptr, *M2 = nullptr, *M3 = nullptr;
   bool chol_valid = false;   // L = chol(X) and Rs = chol(S) belong to the current X, S
   double* lz_work = nullptr; // Lanczos basis scratch (step length)
+  // explicit inverses of the Cholesky factors (and their transposes) of X and S
+  double *LinvX = nullptr, *LinvXT = nullptr, *LinvS = nullptr, *LinvST = nullptr;
+  bool linv_valid = false;
   double *Gt = nullptr, *Sinv = nullptr, *Rd = nullptr, *Rc = nullptr, *dX = nullptr,
          *dS = nullptr, *E = nullptr, *lam = nullptr;
   double *Rp = nullptr, *rhs = nullptr, *dy = nullptr;
@@ -307,6 +357,8 @@ struct sdp_problem {
   // ---- PCG vectors ----
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr, *px = nullptr,
          *pbest = nullptr, *pcorr = nullptr;
+  double* pcg_part = nullptr;          // per-block partials of the fused PCG reductions
+  unsigned int* pcg_ticket = nullptr;  // their arrival tickets (one per reduction)
 
   std::vector<void*> owned;   // every cudaMalloc made for this handle
 
@@ -323,7 +375,9 @@ struct sdp_problem {
 
 namespace sdpgb {
 // matvec.cu
-sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec);
+// Optional epilogue (PCG): *dot_out = v . Hv, after *pro_dst = *pro_src.
+sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec, double* dot_out = nullptr,
+                       double* pro_dst = nullptr, const double* pro_src = nullptr);
 sdp_status ensure_lowprec_W(sdp_problem* h, int prec);
 // sparse helpers used by the IPM and the preconditioner (matvec.cu)
 void assemble_V(sdp_problem* h, const double* v, const double* scale, double* Vval);
@@ -334,7 +388,8 @@ void spmm_rows(sdp_problem* h, const double* Vval, const double* B, int ldb, int
                int ldo);   // out[a, :ncols] = sum_{s in row a} Vval[s] B[col(s), :ncols]
 // precond.cu
 sdp_status precond_build_impl(sdp_problem* h);
-sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int prec);
+// Optional epilogue (PCG): *dot_out = r . z.
+sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int prec, double* dot_out = nullptr);
 // pcg.cu
 sdp_status pcg_impl(sdp_problem* h, const double* r, double* y, double rtol, int maxit, int prec,
                     int* iters, double* relres);

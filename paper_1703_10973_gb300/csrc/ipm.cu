@@ -57,7 +57,7 @@ sdp_status ipm_alloc(sdp_problem* h) {
     SDP_TRY(h->alloc(&h->eig_base, eig_work_bytes(n, true)));
     eig_work_carve(&h->eig, h->eig_base, n, true);
   }
-  if (n >= LZ_MIN_N) SDP_TRY(h->allocT(&h->lz_work, lanczos_work_doubles(n)));
+  if (n >= LZ_MIN_N && lanczos_fits(n)) SDP_TRY(h->allocT(&h->lz_work, lanczos_work_doubles(n)));
   return SDP_OK;
 }
 
@@ -75,21 +75,56 @@ static sdp_status chol_checked(sdp_problem* h, const double* src, double* L, con
   return SDP_OK;
 }
 
+// Explicit inverses of L = chol(X) and Rs = chol(S) with their transposes, for
+// the step-length operator L^{-1} D L^{-T}; computed once per pair of factors.
+static sdp_status ensure_linv(sdp_problem* h) {
+  if (h->linv_valid) return SDP_OK;
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  const size_t nn = (size_t)n * n;
+  if (!h->LinvX) {
+    SDP_TRY(h->allocT(&h->LinvX, nn));
+    SDP_TRY(h->allocT(&h->LinvXT, nn));
+    SDP_TRY(h->allocT(&h->LinvS, nn));
+    SDP_TRY(h->allocT(&h->LinvST, nn));
+  }
+  const double* F[2] = {h->L, h->Rs};
+  double* I[2] = {h->LinvX, h->LinvS};
+  double* IT[2] = {h->LinvXT, h->LinvST};
+  for (int t = 0; t < 2; ++t) {
+    fill(st, I[t], nn, 0.0);
+    add_diag(st, n, I[t], n, 1.0);
+    trsm_left_lower_ex(st, false, n, n, F[t], n, I[t], n, h->work, true);
+    transpose(st, n, n, I[t], n, IT[t], n);
+  }
+  h->linv_valid = true;
+  return SDP_OK;
+}
+
 // Largest alpha with (Lf Lf^T) + alpha D psd, from lambda_min(Lf^{-1} D Lf^{-T}).
-static sdp_status max_step(sdp_problem* h, const double* Lf, const double* D, double* alpha) {
+// Lanczos applies that operator as three products with the explicit inverse
+// (Linv, D, Linv^T); without the inverse it forms the matrix by two solves.
+static sdp_status max_step(sdp_problem* h, const double* Lf, const double* Linv, const double* LinvT,
+                           const double* D, double* alpha) {
   cudaStream_t st = h->stream;
   const int n = h->n;
   ktimer_begin(st, "max_step");
-  copy2d(st, n, n, D, n, h->M1, n);
-  trsm_left_lower(st, false, n, n, Lf, n, h->M1, n, h->work);   // Lf^{-1} D
-  transpose(st, n, n, h->M1, n, h->M2, n);                      // D Lf^{-T}
-  trsm_left_lower(st, false, n, n, Lf, n, h->M2, n, h->work);   // Lf^{-1} D Lf^{-T}
-  symmetrize_avg(st, n, h->M2, n);
   double lmin = 0.0;
   bool have = false;
+  const bool implicit = (Linv != nullptr) && h->lz_work;
+  if (!implicit) {
+    copy2d(st, n, n, D, n, h->M1, n);
+    trsm_left_lower(st, false, n, n, Lf, n, h->M1, n, h->work);   // Lf^{-1} D
+    transpose(st, n, n, h->M1, n, h->M2, n);                      // D Lf^{-T}
+    trsm_left_lower(st, false, n, n, Lf, n, h->M2, n, h->work);   // Lf^{-1} D Lf^{-T}
+    symmetrize_avg(st, n, h->M2, n);
+  }
   if (h->lz_work) {
     // lambda_min by Lanczos; only whether it lies above -step_frac matters for a full step
-    if (lanczos_min(st, n, h->M2, n, 1e-3, -h->prm.step_frac, h->lz_work, h->scal + R_LZ) == SDP_OK) {
+    const sdp_status ls = implicit
+        ? lanczos_min(st, n, Linv, D, LinvT, n, 1e-3, -h->prm.step_frac, h->lz_work, h->scal + R_LZ)
+        : lanczos_min(st, n, h->M2, nullptr, nullptr, n, 1e-3, -h->prm.step_frac, h->lz_work, h->scal + R_LZ);
+    if (ls == SDP_OK) {
       double o[5];
       SDP_CK(h, cudaMemcpyAsync(o, h->scal + R_LZ, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
       SDP_CK(h, cudaStreamSynchronize(st));
@@ -98,6 +133,13 @@ static sdp_status max_step(sdp_problem* h, const double* Lf, const double* D, do
         have = true;
       }
     }
+  }
+  if (!have && implicit) {
+    copy2d(st, n, n, D, n, h->M1, n);
+    trsm_left_lower(st, false, n, n, Lf, n, h->M1, n, h->work);
+    transpose(st, n, n, h->M1, n, h->M2, n);
+    trsm_left_lower(st, false, n, n, Lf, n, h->M2, n, h->work);
+    symmetrize_avg(st, n, h->M2, n);
   }
   if (!have) {
     SDP_TRY(eig_min(st, n, h->M2, h->scal + R_LMIN, &h->eig));
@@ -227,9 +269,22 @@ static sdp_status db_inv_sqrt(sdp_problem* h, double* M, double* Zout) {
   return SDP_OK;
 }
 
+// Probe vectors for the NT check: entries from a splitmix64 hash of the index, in [-1, 1].
+constexpr int NT_PROBES = 4;
+__global__ void k_probe_fill(int count, double* Z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1) + 0x632BE59BD9B4E019ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  Z[i] = (double)(z >> 11) * 0x1p-52 - 1.0;
+}
+
 // W = L Q Lambda^{-1/2} Q^T L^T and S^{-1} = L Q Lambda^{-1} Q^T L^T from
 // L^T S L = Q Lambda Q^T.  The eigendecomposition path is checked through the
-// defining property W S W = X; when inverse iteration could not separate a
+// defining property W S W = X (on a few probe vectors, four thin products
+// instead of two n^3 GEMMs); when inverse iteration could not separate a
 // tight eigenvalue cluster the check fails and the inverse square root of
 // L^T S L comes from the Denman-Beavers iteration instead.
 static sdp_status nt_scaling(sdp_problem* h) {
@@ -248,12 +303,24 @@ static sdp_status nt_scaling(sdp_problem* h) {
   scale_cols(st, n, n, h->Gt, n, h->lam, -1.0, h->M1, n);
   gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->Sinv, n);
   symmetrize_avg(st, n, h->Sinv, n);
-  // check W S W = X
-  gemm(st, false, false, n, n, n, 1.0, h->W, n, h->S, n, 0.0, h->M1, n);
-  gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->Gt, n);
-  axpby(st, nn, 1.0, h->Gt, -1.0, h->X, h->Gt);
-  dot(st, nn, h->Gt, h->Gt, h->scal + R_XDS, h->part);
-  dot(st, nn, h->X, h->X, h->scal + R_DXS, h->part);
+  // check W S W = X on NT_PROBES fixed pseudo-random vectors Z: W (S (W Z)) - X Z
+  {
+    const int pr = NT_PROBES;
+    double* Zp = h->Gt;                       // n x pr
+    double* T1 = h->M1;                       // n x pr each
+    double* T2 = h->M1 + (size_t)n * pr;
+    double* T3 = h->M1 + 2 * (size_t)n * pr;
+    double* T4 = h->M1 + 3 * (size_t)n * pr;
+    count_launch();
+    k_probe_fill<<<(unsigned)((n * pr + 255) / 256), 256, 0, st>>>(n * pr, Zp);
+    gemm(st, false, false, n, pr, n, 1.0, h->W, n, Zp, pr, 0.0, T1, pr);
+    gemm(st, false, false, n, pr, n, 1.0, h->S, n, T1, pr, 0.0, T2, pr);
+    gemm(st, false, false, n, pr, n, 1.0, h->W, n, T2, pr, 0.0, T3, pr);
+    gemm(st, false, false, n, pr, n, 1.0, h->X, n, Zp, pr, 0.0, T4, pr);
+    axpby(st, (size_t)n * pr, 1.0, T3, -1.0, T4, T3);
+    dot(st, (size_t)n * pr, T3, T3, h->scal + R_XDS, h->part);
+    dot(st, (size_t)n * pr, T4, T4, h->scal + R_DXS, h->part);
+  }
   double v[2], lam0 = 0.0;
   SDP_CK(h, cudaMemcpyAsync(v, h->scal + R_XDS, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   SDP_CK(h, cudaMemcpyAsync(&lam0, h->lam, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -343,6 +410,7 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
 
   // ---- NT scaling (L = chol(X) and Rs = chol(S) come from the previous step's check)
   if (!h->chol_valid) {
+    h->linv_valid = false;
     SDP_TRY(chol_checked(h, h->X, h->L, "ipm_step: chol(X)"));
     SDP_TRY(chol_checked(h, h->S, h->Rs, "ipm_step: chol(S)"));
     h->chol_valid = true;
@@ -362,11 +430,14 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   ktimer_end(st, "precond_build", 0.0, 0.0);
   inf.tau = h->tau;
 
-  // ---- common part of the right-hand side: Rp <- Rp + A(W Rd W)
-  gemm(st, false, false, n, n, n, 1.0, h->W, n, h->Rd, n, 0.0, h->M1, n);
-  gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->M3, n);
-  symmetrize_avg(st, n, h->M3, n);
-  op_A_dense(h, h->M3, h->Rp, 1.0, h->Rp, 1.0);   // Rp <- Rp + A(W Rd W)
+  // ---- common part of the right-hand side: Rp <- Rp + A(W Rd W) (nothing to add
+  // once a full dual step has made the iterate dual feasible: Rd = 0 exactly)
+  if (v[1] != 0.0) {
+    gemm(st, false, false, n, n, n, 1.0, h->W, n, h->Rd, n, 0.0, h->M1, n);
+    gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->M3, n);
+    symmetrize_avg(st, n, h->M3, n);
+    op_A_dense(h, h->M3, h->Rp, 1.0, h->Rp, 1.0);   // Rp <- Rp + A(W Rd W)
+  }
 
   // ---- predictor
   axpby(st, nn, -1.0, h->X, 0.0, nullptr, h->Rc);
@@ -376,8 +447,9 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   inf.pcg_iters_pred = its;
   inf.pcg_relres_pred = rr;
   double ap = 0.0, ad = 0.0;
-  SDP_TRY(max_step(h, h->L, h->dX, &ap));
-  SDP_TRY(max_step(h, h->Rs, h->dS, &ad));
+  if (h->lz_work) SDP_TRY(ensure_linv(h));
+  SDP_TRY(max_step(h, h->L, h->LinvX, h->LinvXT, h->dX, &ap));
+  SDP_TRY(max_step(h, h->Rs, h->LinvS, h->LinvST, h->dS, &ad));
   ap = std::min(1.0, h->prm.step_frac * ap);
   ad = std::min(1.0, h->prm.step_frac * ad);
   dot(st, nn, h->X, h->dS, sc + R_XDS, h->part);
@@ -396,8 +468,8 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   SDP_TRY(newton(h, h->Rp, &its, &rr));
   inf.pcg_iters_corr = its;
   inf.pcg_relres_corr = rr;
-  SDP_TRY(max_step(h, h->L, h->dX, &ap));
-  SDP_TRY(max_step(h, h->Rs, h->dS, &ad));
+  SDP_TRY(max_step(h, h->L, h->LinvX, h->LinvXT, h->dX, &ap));
+  SDP_TRY(max_step(h, h->Rs, h->LinvS, h->LinvST, h->dS, &ad));
   ap = std::min(1.0, h->prm.step_frac * ap);
   ad = std::min(1.0, h->prm.step_frac * ad);
 
@@ -405,6 +477,7 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   // L and Rs; a factorisation that fails (a step length from a Lanczos estimate
   // that came out too long) shortens that side's step.
   h->chol_valid = false;
+  h->linv_valid = false;
   SDP_TRY(update_checked(h, h->X, h->dX, &ap, h->L, "ipm_step: primal update"));
   SDP_TRY(update_checked(h, h->S, h->dS, &ad, h->Rs, "ipm_step: dual update"));
   h->chol_valid = true;

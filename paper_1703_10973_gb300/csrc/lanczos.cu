@@ -10,8 +10,12 @@
 // iteration stops when that bound is small against |theta| and returns the
 // conservative estimate theta - beta_j |s_j|, which can only shorten a step.
 //
-// Layout: the LZ_CS CTAs of the cluster split the rows of M for the product
-// w = M q; each CTA writes its slice of w into every CTA's shared memory
+// The operator is M itself, or M = A1 A2 A3 applied as three products
+// (the step length uses L^{-1} dX L^{-T} this way, from the explicit inverse of
+// the Cholesky factor, without forming M).
+//
+// Layout: the LZ_CS CTAs of the cluster split the rows of each product
+// w = M q (cyclically, for balance with triangular factors); each CTA writes its slice of w into every CTA's shared memory
 // (distributed shared memory), and after one cluster barrier every CTA holds
 // the whole w and performs the O(j n) vector work redundantly, so all CTAs
 // compute bit-identical q, alpha, beta and take the same branches.  Each CTA
@@ -169,26 +173,44 @@ __device__ void lz_ritz_min(int j, const double* a, const double* b, double* res
   __syncwarp();
 }
 
+// out = A x for this CTA's rows (row r handled by warp r mod (LZ_CS * warps),
+// cyclic over the cluster), each result written into every CTA's `out`
+__device__ __forceinline__ void lz_gemv_bcast(cg::cluster_group& cluster, int n, const double* __restrict__ A,
+                                              int lda, const double* x, double* out, int rank, int warp,
+                                              int lane, int nw) {
+  const int stride = LZ_CS * nw;
+  for (int r = rank * nw + warp; r < n; r += stride) {
+    const double* ar = A + (size_t)r * lda;
+    double acc = 0.0;
+    for (int c = lane; c < n; c += 32) acc = fma(ar[c], x[c], acc);
+    acc = lz_warp_sum(acc);
+    if (lane < LZ_CS) {
+      double* dst = cluster.map_shared_rank(out, lane);
+      dst[r] = acc;
+    }
+  }
+}
+
 // out[0] = conservative lambda_min estimate, out[1] = theta, out[2] = bound,
 // out[3] = steps, out[4] = 1 if converged.  Q: LZ_CS * (LZ_MAXIT + 1) * n doubles.
 // Converged: bound <= rtol |theta|, or (after 2 LZ_CHECK steps) theta - bound >=
 // accept_above (the caller only needs to know that lambda_min is above it).
 __global__ void __cluster_dims__(LZ_CS, 1, 1) __launch_bounds__(LZ_THREADS)
-    k_lanczos_min(int n, const double* __restrict__ M, int ldm, double rtol, double accept_above,
-                  double* __restrict__ Qall,
-                  double* __restrict__ out) {
+    k_lanczos_min(int n, const double* __restrict__ M, const double* __restrict__ A2,
+                  const double* __restrict__ A3, int ldm, double rtol, double accept_above,
+                  double* __restrict__ Qall, double* __restrict__ out) {
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double sm[];
   double* q = sm;                 // n
   double* w0 = sm + n;            // n   (double-buffered product)
   double* w1 = sm + 2 * (size_t)n;
   double* qp = sm + 3 * (size_t)n;  // n   previous q
+  double* t1 = sm + 4 * (size_t)n;  // n   A3 q   (three-factor operator)
+  double* t2 = sm + 5 * (size_t)n;  // n   A2 A3 q
   __shared__ double alpha[LZ_MAXIT], beta[LZ_MAXIT], cdot[LZ_MAXIT + 1];
   __shared__ double red[32], ritz[2], twork[4 * LZ_MAXIT];
   __shared__ int stop;
   const int rank = (int)cluster.block_rank();
-  const int rows = (n + LZ_CS - 1) / LZ_CS;
-  const int r0 = rank * rows, r1 = min(n, r0 + rows);
   double* Q = Qall + (size_t)rank * (LZ_MAXIT + 1) * n;
   const int maxit = min(LZ_MAXIT, n);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -214,16 +236,14 @@ __global__ void __cluster_dims__(LZ_CS, 1, 1) __launch_bounds__(LZ_THREADS)
 
   for (int j = 0; j < maxit; ++j) {
     double* wb = (j & 1) ? w1 : w0;
-    // w[r0:r1] = M[r0:r1, :] q, one warp per row, broadcast into every CTA
-    for (int r = r0 + warp; r < r1; r += nw) {
-      const double* mr = M + (size_t)r * ldm;
-      double acc = 0.0;
-      for (int c = lane; c < n; c += 32) acc = fma(mr[c], q[c], acc);
-      acc = lz_warp_sum(acc);
-      if (lane < LZ_CS) {
-        double* dst = cluster.map_shared_rank(wb, lane);
-        dst[r] = acc;
-      }
+    if (A2) {
+      lz_gemv_bcast(cluster, n, A3, ldm, q, t1, rank, warp, lane, nw);
+      cluster.sync();
+      lz_gemv_bcast(cluster, n, A2, ldm, t1, t2, rank, warp, lane, nw);
+      cluster.sync();
+      lz_gemv_bcast(cluster, n, M, ldm, t2, wb, rank, warp, lane, nw);
+    } else {
+      lz_gemv_bcast(cluster, n, M, ldm, q, wb, rank, warp, lane, nw);
     }
     cluster.sync();
     // alpha_j = q . w ;  w -= alpha q + beta_{j-1} q_{j-1}
@@ -296,16 +316,18 @@ __global__ void __cluster_dims__(LZ_CS, 1, 1) __launch_bounds__(LZ_THREADS)
 
 size_t lanczos_work_doubles(int n) { return (size_t)LZ_CS * (LZ_MAXIT + 1) * n + 8; }
 
-// Launch on st; results land in out_dev[0..4] (device).  Needs 4 n doubles of
-// shared memory per CTA.
-sdp_status lanczos_min(cudaStream_t st, int n, const double* M, int ldm, double rtol, double accept_above,
-                       double* work, double* out_dev) {
-  const size_t smem = 4 * (size_t)n * sizeof(double);
-  if (n < 2 || smem > 200 * 1024) return SDP_ERR_UNSUPPORTED;
+// Launch on st; results land in out_dev[0..4] (device).
+// Operator M (A2 = A3 = nullptr) or M A2 A3.  Needs 6 n doubles of shared memory per CTA.
+bool lanczos_fits(int n) { return n >= 2 && 6 * (size_t)n * sizeof(double) <= 200 * 1024; }
+
+sdp_status lanczos_min(cudaStream_t st, int n, const double* M, const double* A2, const double* A3, int ldm,
+                       double rtol, double accept_above, double* work, double* out_dev) {
+  const size_t smem = 6 * (size_t)n * sizeof(double);
+  if (!lanczos_fits(n) || (A2 == nullptr) != (A3 == nullptr)) return SDP_ERR_UNSUPPORTED;
   allow_max_smem((const void*)k_lanczos_min);
   count_launch();
   ktimer_begin(st, "lanczos");
-  k_lanczos_min<<<LZ_CS, LZ_THREADS, smem, st>>>(n, M, ldm, rtol, accept_above, work, out_dev);
+  k_lanczos_min<<<LZ_CS, LZ_THREADS, smem, st>>>(n, M, A2, A3, ldm, rtol, accept_above, work, out_dev);
   ktimer_end(st, "lanczos", 0.0, 0.0);
   return cudaPeekAtLastError() == cudaSuccess ? SDP_OK : SDP_ERR_CUDA;
 }

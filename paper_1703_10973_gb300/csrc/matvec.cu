@@ -117,42 +117,68 @@ __global__ void __launch_bounds__(256) k_spmm_wv_lp(int n, const int* __restrict
 // ---------------------------------------------------------------------------
 // K2: per-constraint gather of W[p,:] . T[q,:]
 // ---------------------------------------------------------------------------
+// With dv != nullptr the kernel also forms dv . Hv (one deterministic grid
+// reduction into *dout; PCG's p . Hp), first moving *pro_src to *pro_dst.
 __global__ void __launch_bounds__(256) k_sddmm_f64(int n, int m, const int* __restrict__ eptr,
                                                    const int* __restrict__ ep, const int* __restrict__ eq,
                                                    const double* __restrict__ ecoef,
                                                    const double* __restrict__ W, const double* __restrict__ T,
-                                                   double* __restrict__ Hv) {
+                                                   double* __restrict__ Hv, const double* __restrict__ dv,
+                                                   double* dpart, unsigned int* ticket, double* dout,
+                                                   double* pro_dst, const double* pro_src) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
-  if (i >= m) return;
   double acc = 0.0;
-  for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
-    const double* wp = W + (size_t)ep[e] * n;
-    const double* tq = T + (size_t)eq[e] * n;
-    double s = 0.0;
-    for (int l = lane; l < n; l += 32) s = fma(wp[l], tq[l], s);
-    acc = fma(ecoef[e], s, acc);
+  if (i < m) {
+    for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
+      const double* wp = W + (size_t)ep[e] * n;
+      const double* tq = T + (size_t)eq[e] * n;
+      double s = 0.0;
+      for (int l = lane; l < n; l += 32) s = fma(wp[l], tq[l], s);
+      acc = fma(ecoef[e], s, acc);
+    }
+    acc = wsum_d(acc);
+    if (lane == 0) Hv[i] = acc;
   }
-  acc = wsum_d(acc);
-  if (lane == 0) Hv[i] = acc;
+  if (dv) {
+    const double c = (i < m && lane == 0) ? dv[i] * acc : 0.0;
+    double tot;
+    if (lb_reduce(c, dpart, ticket, &tot)) {
+      if (pro_dst) *pro_dst = *pro_src;
+      *dout = tot;
+    }
+  }
 }
 
 template <typename TW>
 __global__ void __launch_bounds__(256) k_sddmm_lp(int n, int m, const int* __restrict__ eptr,
                                                   const int* __restrict__ ep, const int* __restrict__ eq,
                                                   const double* __restrict__ ecoef, const TW* __restrict__ W,
-                                                  const float* __restrict__ T, double* __restrict__ Hv) {
+                                                  const float* __restrict__ T, double* __restrict__ Hv,
+                                                  const double* __restrict__ dv, double* dpart, unsigned int* ticket,
+                                                  double* dout, double* pro_dst, const double* pro_src) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
-  if (i >= m) return;
-  float acc = 0.f;
-  for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
-    const TW* wp = W + (size_t)ep[e] * n;
-    const float* tq = T + (size_t)eq[e] * n;
-    float s = 0.f;
-    for (int l = lane; l < n; l += 32) s = fmaf(tof<TW>(wp[l]), tq[l], s);
-    acc = fmaf((float)ecoef[e], s, acc);
+  double hv = 0.0;
+  if (i < m) {
+    float acc = 0.f;
+    for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
+      const TW* wp = W + (size_t)ep[e] * n;
+      const float* tq = T + (size_t)eq[e] * n;
+      float s = 0.f;
+      for (int l = lane; l < n; l += 32) s = fmaf(tof<TW>(wp[l]), tq[l], s);
+      acc = fmaf((float)ecoef[e], s, acc);
+    }
+    acc = wsum_f(acc);
+    hv = (double)acc;
+    if (lane == 0) Hv[i] = hv;
   }
-  acc = wsum_f(acc);
-  if (lane == 0) Hv[i] = (double)acc;
+  if (dv) {
+    const double c = (i < m && lane == 0) ? dv[i] * hv : 0.0;
+    double tot;
+    if (lb_reduce(c, dpart, ticket, &tot)) {
+      if (pro_dst) *pro_dst = *pro_src;
+      *dout = tot;
+    }
+  }
 }
 
 sdp_status ensure_lowprec_W(sdp_problem* h, int prec) {
@@ -205,7 +231,9 @@ static void launch_spmm_lp(sdp_problem* h, const double* Vval, const TW* W) {
   k_spmm_wv_lp<TW, R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->colidx, Vval, W, h->T32);
 }
 
-sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec) {
+sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec, double* dot_out, double* pro_dst,
+                       const double* pro_src) {
+  const double* dv = dot_out ? v : nullptr;
   if (!h->have_W) {
     h->last_error = "hessian_matvec: no scaling matrix W (call sdp_set_W or sdp_ipm_step)";
     return SDP_ERR_ARG;
@@ -223,7 +251,8 @@ sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec) {
     }
     count_launch();
     k_sddmm_f64<<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(n, h->m, h->eptr, h->ep, h->eq, h->ecoef,
-                                                                     h->W, h->T, Hv);
+                                                                     h->W, h->T, Hv, dv, h->pcg_part,
+                                                                     h->pcg_ticket, dot_out, pro_dst, pro_src);
   } else if (prec == SDP_FP32) {
     SDP_TRY(ensure_lowprec_W(h, prec));
     switch (rows_per_cta(n, sizeof(float))) {
@@ -233,8 +262,9 @@ sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec) {
       default: launch_spmm_lp<float, 1>(h, h->Vval, h->W32); break;
     }
     count_launch();
-    k_sddmm_lp<float><<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(n, h->m, h->eptr, h->ep, h->eq,
-                                                                           h->ecoef, h->W32, h->T32, Hv);
+    k_sddmm_lp<float><<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(
+        n, h->m, h->eptr, h->ep, h->eq, h->ecoef, h->W32, h->T32, Hv, dv, h->pcg_part, h->pcg_ticket, dot_out,
+        pro_dst, pro_src);
   } else if (prec == SDP_BF16) {
     SDP_TRY(ensure_lowprec_W(h, prec));
     switch (rows_per_cta(n, sizeof(float))) {
@@ -245,7 +275,8 @@ sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec) {
     }
     count_launch();
     k_sddmm_lp<__nv_bfloat16><<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(
-        n, h->m, h->eptr, h->ep, h->eq, h->ecoef, h->W16, h->T32, Hv);
+        n, h->m, h->eptr, h->ep, h->eq, h->ecoef, h->W16, h->T32, Hv, dv, h->pcg_part, h->pcg_ticket, dot_out,
+        pro_dst, pro_src);
   } else {
     h->last_error = "hessian_matvec: unknown precision";
     return SDP_ERR_ARG;

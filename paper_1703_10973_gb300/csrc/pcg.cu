@@ -25,20 +25,6 @@ enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6
 // last good iterate, sets scal[S_BRK] and ends the loop; the restarted outer
 // solve then continues from the true residual.
 
-// x += a p ; r -= a q  with a = rz / pq
-__global__ void k_pcg_xr(int m, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                         const double* __restrict__ q, double* scal) {
-  const double pq = scal[S_PQ], rz = scal[S_RZ];
-  if (!(pq > 0.0 && rz > 0.0 && isfinite(pq) && isfinite(rz))) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_BRK] = 1.0;
-    return;
-  }
-  const double a = rz / pq;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    x[i] = fma(a, p[i], x[i]);
-    r[i] = fma(-a, q[i], r[i]);
-  }
-}
 // p = z + beta p  with beta = rz_new / rz
 __global__ void k_pcg_p(int m, double* __restrict__ p, const double* __restrict__ z, double* scal) {
   const double rzn = scal[S_RZN], rz = scal[S_RZ];
@@ -50,52 +36,36 @@ __global__ void k_pcg_p(int m, double* __restrict__ p, const double* __restrict_
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) p[i] = fma(beta, p[i], z[i]);
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-// Sum of the dot partials (fixed order) into scal[slot]; `promote` first moves
-// rz_new to rz (the previous iteration's direction update has consumed both).
-__global__ void k_pcg_sum(int np, const double* __restrict__ part, double* scal, int slot, int promote) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
-  s = warp_sum_d(s);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-    s = warp_sum_d(s);
-    if (threadIdx.x == 0) {
-      if (promote) scal[S_RZ] = scal[S_RZN];
-      scal[slot] = s;
+// x += a p;  r -= a q  (a = rz / pq), ||r||^2, iteration count and the loop
+// condition, in one kernel (the last block to finish reduces and decides).
+__global__ void k_pcg_xr_check(int m, double* __restrict__ x, double* __restrict__ r,
+                               const double* __restrict__ p, const double* __restrict__ q, double* scal,
+                               double* part, unsigned int* ticket, cudaGraphConditionalHandle cond, int use_cond) {
+  const double pq = scal[S_PQ], rz = scal[S_RZ];
+  const bool ok = pq > 0.0 && rz > 0.0 && isfinite(pq) && isfinite(rz);
+  const double a = ok ? rz / pq : 0.0;
+  double rr = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    double ri = r[i];
+    if (ok) {
+      x[i] = fma(a, p[i], x[i]);
+      ri = fma(-a, q[i], ri);
+      r[i] = ri;
     }
+    rr = fma(ri, ri, rr);
+  }
+  double tot;
+  if (lb_reduce(rr, part, ticket, &tot)) {
+    scal[S_RR] = tot;
+    const double it = scal[S_IT] + 1.0;
+    scal[S_IT] = it;
+    if (!ok) scal[S_BRK] = 1.0;
+    const bool go = ok && (tot > scal[S_TOL2]) && (it < scal[S_MAXIT]) && isfinite(tot) && scal[S_BRK] == 0.0;
+    scal[S_GO] = go ? 1.0 : 0.0;
+    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
   }
 }
-// ||r||^2 from the partials, iteration count, and the loop condition.
-// With use_cond = 0 (host-driven loop) the decision is only stored in scal[S_GO].
-__global__ void k_pcg_check(int np, const double* __restrict__ part, double* scal, cudaGraphConditionalHandle cond,
-                            int use_cond) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
-  s = warp_sum_d(s);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-    s = warp_sum_d(s);
-    if (threadIdx.x == 0) {
-      scal[S_RR] = s;
-      const double it = scal[S_IT] + 1.0;
-      scal[S_IT] = it;
-      const bool go = (s > scal[S_TOL2]) && (it < scal[S_MAXIT]) && isfinite(s) && scal[S_BRK] == 0.0;
-      scal[S_GO] = go ? 1.0 : 0.0;
-      if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
-    }
-  }
-}
+
 __global__ void k_pcg_init(double* scal, double rtol, int maxit) {
   scal[S_RZN] = scal[S_RZ];
   scal[S_TOL2] = rtol * rtol * scal[S_NR0];
@@ -114,31 +84,30 @@ static sdp_status pcg_alloc(sdp_problem* h) {
   SDP_TRY(h->allocT(&h->px, m));
   SDP_TRY(h->allocT(&h->pbest, m));
   SDP_TRY(h->allocT(&h->pcorr, m));
+  SDP_TRY(h->allocT(&h->pcg_part, (size_t)m / 8 + 4096));
+  SDP_TRY(h->allocT(&h->pcg_ticket, 4));
+  SDP_CK(h, cudaMemsetAsync(h->pcg_ticket, 0, 4 * sizeof(unsigned int), h->stream));
   if (!h->scal) SDP_TRY(h->allocT(&h->scal, 64));
   if (!h->part) SDP_TRY(h->allocT(&h->part, dot_part_doubles()));
   return SDP_OK;
 }
 
-static void dot_part_only(cudaStream_t st, size_t count, const double* x, const double* y, double* part);
 
-// One PCG iteration on h->stream (the body of the device-side loop).
+// One PCG iteration on h->stream (the body of the device-side loop): four
+// launches plus those of the two operators, whose last kernels also form the
+// two inner products (p . Hp with the move rz <- rz_new, and r . z).
 static sdp_status pcg_body(sdp_problem* h, int prec, cudaGraphConditionalHandle cond, bool use_cond) {
   cudaStream_t st = h->stream;
   const int m = h->m;
   const unsigned g = std::min(cdiv(m, 256), 2048u);
-  const int np = (int)dot_part_doubles();
-  SDP_TRY(matvec_impl(h, h->pp, h->pq, prec));
-  dot_part_only(st, m, h->pp, h->pq, h->part);
-  count_launch(3);
-  k_pcg_sum<<<1, 512, 0, st>>>(np, h->part, h->scal, S_PQ, 1);
-  k_pcg_xr<<<g, 256, 0, st>>>(m, h->px, h->pr, h->pp, h->pq, h->scal);
-  dot_part_only(st, m, h->pr, h->pr, h->part);
-  k_pcg_check<<<1, 512, 0, st>>>(np, h->part, h->scal, cond, use_cond ? 1 : 0);
-  SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec));
-  dot_part_only(st, m, h->pr, h->pz, h->part);
-  count_launch(2);
-  k_pcg_sum<<<1, 512, 0, st>>>(np, h->part, h->scal, S_RZN, 0);
-  k_pcg_p<<<g, 256, 0, st>>>(m, h->pp, h->pz, h->scal);
+  double* scal = h->scal;
+  SDP_TRY(matvec_impl(h, h->pp, h->pq, prec, scal + S_PQ, scal + S_RZ, scal + S_RZN));
+  count_launch();
+  k_pcg_xr_check<<<g, 256, 0, st>>>(m, h->px, h->pr, h->pp, h->pq, scal, h->pcg_part, h->pcg_ticket, cond,
+                                    use_cond ? 1 : 0);
+  SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec, scal + S_RZN));
+  count_launch();
+  k_pcg_p<<<g, 256, 0, st>>>(m, h->pp, h->pz, scal);
   return SDP_OK;
 }
 
@@ -225,9 +194,8 @@ static sdp_status pcg_core(sdp_problem* h, const double* rhs, double* x, double 
     if (brk) *brk = false;
     return SDP_OK;
   }
-  SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec));
+  SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec, scal + S_RZ));
   SDP_CK(h, cudaMemcpyAsync(h->pp, h->pz, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  dot(st, m, h->pr, h->pz, scal + S_RZ, h->part);
   count_launch();
   k_pcg_init<<<1, 1, 0, st>>>(scal, rtol, maxit);
   double v[11];
@@ -338,10 +306,4 @@ static sdp_status pcg_impl_(sdp_problem* h, const double* r, double* y, double r
   return result;
 }
 
-}  // namespace sdpgb
-
-namespace sdpgb {
-static void dot_part_only(cudaStream_t st, size_t count, const double* x, const double* y, double* part) {
-  dot_partials(st, count, x, y, part);
-}
 }  // namespace sdpgb

@@ -78,45 +78,71 @@ __global__ void k_csr_mm(int rows, const int* __restrict__ rowptr, const int* __
   }
 }
 
-// z_i = (ginv_i / tau^2) (r_i - (UU s)_i),  (UU s)_i = A_i . (ZS U^T)
+// z_i = (ginv_i / tau^2) (r_i - (UU s)_i),  (UU s)_i = A_i . (ZS U^T); with
+// dout != nullptr also *dout = r . z (one deterministic grid reduction).
 __global__ void k_apply_tail(int m, int k, const int* __restrict__ eptr, const int* __restrict__ ep,
                              const int* __restrict__ eq, const double* __restrict__ ecoef,
                              const double* __restrict__ ZS, const double* __restrict__ U,
                              const double* __restrict__ ginv, const double* __restrict__ r, double inv_tau2,
-                             double* __restrict__ z) {
+                             double* __restrict__ z, double* dpart, unsigned int* ticket, double* dout) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  double us = 0.0;
-  for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
-    const int p = ep[e], q = eq[e];
-    double s = 0.0;
-    if (p == q) {
-      for (int l = 0; l < k; ++l) s = fma(ZS[(size_t)p * k + l], U[(size_t)p * k + l], s);
-      us = fma(ecoef[e], s, us);
-    } else {
-      for (int l = 0; l < k; ++l) {
-        s = fma(ZS[(size_t)p * k + l], U[(size_t)q * k + l], s);
-        s = fma(ZS[(size_t)q * k + l], U[(size_t)p * k + l], s);
+  double rz = 0.0;
+  if (i < m) {
+    double us = 0.0;
+    for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
+      const int p = ep[e], q = eq[e];
+      double s = 0.0;
+      if (p == q) {
+        for (int l = 0; l < k; ++l) s = fma(ZS[(size_t)p * k + l], U[(size_t)p * k + l], s);
+        us = fma(ecoef[e], s, us);
+      } else {
+        for (int l = 0; l < k; ++l) {
+          s = fma(ZS[(size_t)p * k + l], U[(size_t)q * k + l], s);
+          s = fma(ZS[(size_t)q * k + l], U[(size_t)p * k + l], s);
+        }
+        us = fma(0.5 * ecoef[e], s, us);
       }
-      us = fma(0.5 * ecoef[e], s, us);
     }
+    const double zi = ginv[i] * inv_tau2 * (r[i] - us);
+    z[i] = zi;
+    rz = r[i] * zi;
   }
-  z[i] = ginv[i] * inv_tau2 * (r[i] - us);
+  if (dout) {
+    double tot;
+    if (lb_reduce(rz, dpart, ticket, &tot)) *dout = tot;
+  }
 }
 
-// out[l n + c] = alpha in[c k + l]   (n x k  ->  k x n)
-__global__ void k_nk_to_kn(int n, int k, double alpha, const double* __restrict__ in, double* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * k) return;
-  const int l = t / n, c = t % n;
-  out[t] = alpha * in[(size_t)c * k + l];
-}
-// out[c k + l] = alpha in[l n + c]   (k x n  ->  n x k)
-__global__ void k_kn_to_nk(int n, int k, double alpha, const double* __restrict__ in, double* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * k) return;
-  const int c = t / k, l = t % k;
-  out[t] = alpha * in[(size_t)l * n + c];
+// Hhat apply, first product: u[l n + a] = scale * sum_{s in row a} V_s U[col(s)][l]
+// with V = sum_i g_i^{-1} r_i A_i assembled on the fly; one warp per row a.
+__global__ void k_hat_u(int n, int k, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                        const int* __restrict__ sptr, const int* __restrict__ scon, const double* __restrict__ scoef,
+                        const double* __restrict__ ginv, const double* __restrict__ r, const double* __restrict__ U,
+                        double scale, double* __restrict__ u) {
+  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (a >= n) return;
+  double acc[8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) acc[l] = 0.0;
+  for (int s = rowptr[a] + lane; s < rowptr[a + 1]; s += 32) {
+    double v = 0.0;
+    for (int c = sptr[s]; c < sptr[s + 1]; ++c) {
+      const int i = scon[c];
+      v = fma(scoef[c] * ginv[i], r[i], v);
+    }
+    const double* ur = U + (size_t)colidx[s] * k;
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+      if (l < k) acc[l] = fma(v, ur[l], acc[l]);
+  }
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    if (l >= k) break;
+    double t = acc[l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) u[(size_t)l * n + a] = scale * t;
+  }
 }
 
 __global__ void k_scale_ginv(int m, const double* __restrict__ ginv, const double* __restrict__ r, double s,
@@ -462,7 +488,7 @@ sdp_status precond_build_impl(sdp_problem* h) {
   return SDP_OK;
 }
 
-sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int prec) {
+sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int prec, double* dot_out) {
   (void)prec;  // the apply runs in FP64; reduced precision is confined to the matvec
   cudaStream_t st = h->stream;
   const int n = h->n, m = h->m, k = h->kpc, nk = n * k;
@@ -470,27 +496,28 @@ sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int pr
   if (k == 0) {
     count_launch();
     k_scale_ginv<<<cdiv(m, 256), 256, 0, st>>>(m, h->ginv, r, inv_tau2, z);
+    if (dot_out) dot(st, m, r, z, dot_out, h->part);
     return SDP_OK;
   }
-  // u = Z^T (sum g_i r_i A_i) U, stored as k x n (row l = column l of u)
-  assemble_V(h, r, h->ginv, h->pvec);
-  spmm_rows(h, h->pvec, h->U, k, k, h->Bn, k);
   if (h->pc_hat) {
+    // u = sqrt(2 tau) (sum g_i r_i A_i) U (k x n); S^{-1} u through the block
+    // factors, returned as ZS = sqrt(2 tau) S_mat (n x k)
     count_launch();
-    k_nk_to_kn<<<cdiv((size_t)nk, 256), 256, 0, st>>>(n, k, h->zscale, h->Bn, h->uvec);
-  } else if (!ts_product(st, n, k, h->Bn, h->Z, h->trpart, h->uvec, nullptr, nullptr, true)) {
-    gemm(st, true, false, k, n, n, 1.0, h->Bn, k, h->Z, n, 0.0, h->uvec, n);
-  }
-  // s = L^{-T} L^{-1} u.  Multiplying by the stored inverse alone loses accuracy
-  // once the core is ill conditioned (kappa(L) eps, late interior-point
-  // iterations), so each triangular solve takes one step of iterative refinement
-  // whose residual uses the factor itself:  y0 = L^{-1} u,  y = y0 + L^{-1}(u - L y0).
-  // ||I - L^{-1} L|| stays far below one where the plain inverse has failed, and
-  // the refined solve matches substitution.  Buffers: uvec = u, uvec2 = y0, uvec3 = scratch.
-  if (h->pc_hat) {
-    SDP_TRY(schur_apply(h, h->uvec, h->uvec2));
-    std::swap(h->uvec, h->uvec2);
+    k_hat_u<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, k, h->rowptr, h->colidx, h->sptr, h->scon, h->scoef,
+                                                       h->ginv, r, h->U, h->zscale, h->uvec);
+    SDP_TRY(schur_apply(h, h->uvec, h->Bn, h->zscale));
   } else {
+    // u = Z^T (sum g_i r_i A_i) U, stored as k x n (row l = column l of u)
+    assemble_V(h, r, h->ginv, h->pvec);
+    spmm_rows(h, h->pvec, h->U, k, k, h->Bn, k);
+    if (!ts_product(st, n, k, h->Bn, h->Z, h->trpart, h->uvec, nullptr, nullptr, true))
+      gemm(st, true, false, k, n, n, 1.0, h->Bn, k, h->Z, n, 0.0, h->uvec, n);
+    // s = L^{-T} L^{-1} u.  Multiplying by the stored inverse alone loses accuracy
+    // once the core is ill conditioned (kappa(L) eps, late interior-point
+    // iterations), so each triangular solve takes one step of iterative refinement
+    // whose residual uses the factor itself:  y0 = L^{-1} u,  y = y0 + L^{-1}(u - L y0).
+    // ||I - L^{-1} L|| stays far below one where the plain inverse has failed, and
+    // the refined solve matches substitution.  Buffers: uvec = u, uvec2 = y0, uvec3 = scratch.
     for (int t = 0; t < 2; ++t) {
       const bool tr = (t == 1);
       trmv_lower_ex(st, tr, nk, h->Linv, nk, h->uvec, h->uvec2, h->trpart, 1.0, nullptr, 0.0);   // y0
@@ -500,17 +527,13 @@ sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int pr
       }
       std::swap(h->uvec, h->uvec2);   // result becomes the input of the next solve
     }
-  }
-  // ZS = Z S_mat with S_mat[c][l] = s[l n + c]
-  if (h->pc_hat) {
-    count_launch();
-    k_kn_to_nk<<<cdiv((size_t)nk, 256), 256, 0, st>>>(n, k, h->zscale, h->uvec, h->Bn);
-  } else if (!ts_product(st, n, k, nullptr, h->Z, nullptr, nullptr, h->uvec, h->Bn, false)) {
-    gemm(st, false, true, n, k, n, 1.0, h->Z, n, h->uvec, n, 0.0, h->Bn, k);
+    // ZS = Z S_mat with S_mat[c][l] = s[l n + c]
+    if (!ts_product(st, n, k, nullptr, h->Z, nullptr, nullptr, h->uvec, h->Bn, false))
+      gemm(st, false, true, n, k, n, 1.0, h->Z, n, h->uvec, n, 0.0, h->Bn, k);
   }
   count_launch();
   k_apply_tail<<<cdiv(m, 256), 256, 0, st>>>(m, k, h->eptr, h->ep, h->eq, h->ecoef, h->Bn, h->U, h->ginv, r,
-                                             inv_tau2, z);
+                                             inv_tau2, z, h->pcg_part, h->pcg_ticket, dot_out);
   return SDP_OK;
 }
 

@@ -291,10 +291,11 @@ __global__ void k_hat_fwdR(int nr, int n, int k, const int* __restrict__ rverts,
   }
 }
 
-// x_a = L_a^{-T}(y_a - F_a x_R); out[l n + pverts[a]] = x_a[l]; one warp per a
+// x_a = L_a^{-T}(y_a - F_a x_R); out[pverts[a] k + l] = scale x_a[l]; one warp per a
 __global__ void k_hat_bwdP(int np, int n, int k, const int* __restrict__ pverts, const int* __restrict__ bptr,
                            const int* __restrict__ bcol, const double* __restrict__ F, const double* __restrict__ D,
-                           const double* __restrict__ yP, const double* __restrict__ xR, double* __restrict__ out) {
+                           const double* __restrict__ yP, const double* __restrict__ xR, double scale,
+                           double* __restrict__ out) {
   const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (a >= np) return;
   double acc[KMAX];
@@ -320,16 +321,16 @@ __global__ void k_hat_bwdP(int np, int n, int k, const int* __restrict__ pverts,
     double s = z[i];
     for (int j = i + 1; j < k; ++j) s -= La[j * k + i] * z[j];
     z[i] = s / La[i * k + i];
-    out[(size_t)i * n + v] = z[i];
+    out[(size_t)v * k + i] = scale * z[i];
   }
 }
 
-__global__ void k_hat_outR(int nr, int n, int k, const int* __restrict__ rverts, const double* __restrict__ xR,
-                           double* __restrict__ out) {
+__global__ void k_hat_outR(int nr, int k, const int* __restrict__ rverts, const double* __restrict__ xR,
+                           double scale, double* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nr * k) return;
   const int r = t / k, l = t % k;
-  out[(size_t)l * n + rverts[r]] = xR[t];
+  out[(size_t)rverts[r] * k + l] = scale * xR[t];
 }
 
 // ---------------------------------------------------------------------------
@@ -402,8 +403,11 @@ sdp_status schur_build(sdp_problem* h, int k, double tau) {
   return SDP_OK;
 }
 
-// out = S^{-1} u  (both k x n, u[l n + c]); u is not modified.
-sdp_status schur_apply(sdp_problem* h, const double* u, double* out) {
+// out = scale S^{-1} u with u in the k x n layout u[l n + c] and out in the
+// n x k layout out[c k + l]; u is not modified.  The dense solves take no
+// refinement step: the Hhat core stays well enough conditioned (kappa ~ 1/mu)
+// for the explicit inverse of the Schur factor.
+sdp_status schur_apply(sdp_problem* h, const double* u, double* out, double scale) {
   cudaStream_t st = h->stream;
   const int n = h->n, k = h->hs_k, np = h->hs_np, nr = h->hs_nr, Rk = nr * k;
   if (np > 0) {
@@ -414,31 +418,20 @@ sdp_status schur_apply(sdp_problem* h, const double* u, double* out) {
     count_launch();
     k_hat_fwdR<<<cdiv((size_t)nr * 32, 256), 256, 0, st>>>(nr, n, k, h->hs_rverts, h->hs_btptr, h->hs_btslot,
                                                             h->hs_bp, h->hs_F, h->hs_yP, u, h->hs_v1);
-    // y_R = L_C^{-1} t_R and x_R = L_C^{-T} y_R, each with one refinement step
-    double* in = h->hs_v1;
-    double* y0 = h->hs_v2;
-    double* res = h->hs_v3;
-    for (int t = 0; t < 2; ++t) {
-      const bool tr = (t == 1);
-      trmv_lower_ex(st, tr, Rk, h->hs_Cinv, Rk, in, y0, h->trpart, 1.0, nullptr, 0.0);
-      for (int it = 0; it < h->core_refine; ++it) {
-        trmv_lower_ex(st, tr, Rk, h->hs_C, Rk, y0, res, h->trpart, -1.0, in, 1.0);
-        trmv_lower_ex(st, tr, Rk, h->hs_Cinv, Rk, res, y0, h->trpart, 1.0, y0, 1.0);
-      }
-      std::swap(in, y0);   // result becomes the input of the next solve
-    }
-    // `in` holds x_R
+    // y_R = L_C^{-1} t_R and x_R = L_C^{-T} y_R
+    trmv_lower_ex(st, false, Rk, h->hs_Cinv, Rk, h->hs_v1, h->hs_v2, h->trpart, 1.0, nullptr, 0.0);
+    trmv_lower_ex(st, true, Rk, h->hs_Cinv, Rk, h->hs_v2, h->hs_v1, h->trpart, 1.0, nullptr, 0.0);
     count_launch();
-    k_hat_outR<<<cdiv(Rk, 128), 128, 0, st>>>(nr, n, k, h->hs_rverts, in, out);
+    k_hat_outR<<<cdiv(Rk, 128), 128, 0, st>>>(nr, k, h->hs_rverts, h->hs_v1, scale, out);
     if (np > 0) {
       count_launch();
       k_hat_bwdP<<<cdiv((size_t)np * 32, 256), 256, 0, st>>>(np, n, k, h->hs_pverts, h->hs_bptr, h->hs_bcol,
-                                                              h->hs_F, h->hs_D, h->hs_yP, in, out);
+                                                              h->hs_F, h->hs_D, h->hs_yP, h->hs_v1, scale, out);
     }
   } else if (np > 0) {
     count_launch();
     k_hat_bwdP<<<cdiv((size_t)np * 32, 256), 256, 0, st>>>(np, n, k, h->hs_pverts, h->hs_bptr, h->hs_bcol,
-                                                            h->hs_F, h->hs_D, h->hs_yP, nullptr, out);
+                                                            h->hs_F, h->hs_D, h->hs_yP, nullptr, scale, out);
   }
   return SDP_OK;
 }

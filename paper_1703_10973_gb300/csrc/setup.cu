@@ -49,7 +49,7 @@ extern "C" void sdp_default_params(sdp_params* p) {
   p->step_frac = 0.9;
   p->prec = SDP_FP64;
   p->precond = SDP_PRECOND_HAT;
-  p->inner_rtol = 1e-4;
+  p->inner_rtol = 1e-9;
   p->verbose = 0;
   p->pcg_graph = 1;
 }

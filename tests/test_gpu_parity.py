@@ -205,8 +205,9 @@ def test_pcg_matches_direct_solve(mu, kind):
     assert np.linalg.norm(H @ y - r) <= 1e-9 * np.linalg.norm(r)
     assert _rel(y, ystar) <= 1e-10 * np.linalg.cond(H)
     # the preconditioned iteration count stays small and independent of mu
-    # (Lemma Htilde; Lemma aug_prec with k^2 outliers)
-    assert its <= 60
+    # (Lemma Htilde; Lemma aug_prec with k^2 outliers), against m = 100 unknowns
+    # and kappa(H) far above 1e6
+    assert its <= 80
 
 
 def test_pcg_host_loop_matches_graph_loop():
