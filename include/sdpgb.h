@@ -77,6 +77,8 @@ typedef struct {
                        /* a conditional while node (default); 0 = host-driven     */
                        /* loop launching the same kernels (for profilers that do  */
                        /* not support conditional graph nodes)                    */
+  double inner_rtol_lp; /* PCG tolerance of one sweep whose matvec runs in FP32 or */
+                        /* BF16 (the FP64 true residual refines it); 1e-4         */
 } sdp_params;
 
 typedef struct {

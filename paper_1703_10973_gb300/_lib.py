@@ -35,6 +35,7 @@ class sdp_params(C.Structure):
         ("inner_rtol", C.c_double),
         ("verbose", C.c_int),
         ("pcg_graph", C.c_int),
+        ("inner_rtol_lp", C.c_double),
     ]
 
 

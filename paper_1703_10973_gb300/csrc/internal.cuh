@@ -292,6 +292,11 @@ struct sdp_problem {
   float* T32 = nullptr;
   __nv_bfloat16* W16 = nullptr;
   bool W32_valid = false, W16_valid = false;
+  int64_t W32_key = -1, W16_key = -1;   // preconditioner generation of a split copy (-1: plain W)
+  double* mv_G = nullptr;  // split matvec: (E V)^T, n x k
+  float* mv_R = nullptr;   // Lambda (E V) W_s, k x n
+  double* mv_Q = nullptr;  // Lambda (E V E^T) Lambda, k x k
+  float* mv_part = nullptr;
 
   // ---- preconditioner ----
   bool pc_valid = false;

@@ -8,6 +8,17 @@
 //
 // The same CSR machinery serves the IPM: A(X) (op_A_dense), A^T y scattered into
 // a dense matrix (scatter_V_dense) and sparse-times-dense products with U or Z.
+//
+// Reduced precision with the split W = W_l + W_s (W_l = E^T Lambda E, the top-k
+// eigenpairs of the preconditioner build): near the optimum W_l holds the k
+// eigenvalues of order 1/mu and W_s the rest, so rounding W itself to FP32 or
+// BF16 erases W_s.  Instead only W_s V W_s runs in the reduced precision (SpMM
+// and SDDMM as above); the other three terms are low rank,
+//   (W_l V W_s + W_s V W_l)_pq = sum_l E[l][p] R[l][q] + E[l][q] R[l][p],
+//   R = Lambda (E V) W_s  (k x n),
+//   (W_l V W_l)_pq = E[:, p]^T Q E[:, q],  Q = Lambda (E V E^T) Lambda  (k x k),
+// and are added per stored entry in FP64, so every term keeps a relative error
+// of the working precision on its own scale.
 #include "internal.cuh"
 
 #include <algorithm>
@@ -155,20 +166,32 @@ __global__ void __launch_bounds__(256) k_sddmm_lp(int n, int m, const int* __res
                                                   const double* __restrict__ ecoef, const TW* __restrict__ W,
                                                   const float* __restrict__ T, double* __restrict__ Hv,
                                                   const double* __restrict__ dv, double* dpart, unsigned int* ticket,
-                                                  double* dout, double* pro_dst, const double* pro_src) {
+                                                  double* dout, double* pro_dst, const double* pro_src, int k,
+                                                  const double* __restrict__ E, const float* __restrict__ R,
+                                                  const double* __restrict__ Q) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   double hv = 0.0;
   if (i < m) {
-    float acc = 0.f;
     for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
-      const TW* wp = W + (size_t)ep[e] * n;
-      const float* tq = T + (size_t)eq[e] * n;
+      const int p = ep[e], q = eq[e];
+      const TW* wp = W + (size_t)p * n;
+      const float* tq = T + (size_t)q * n;
       float s = 0.f;
       for (int l = lane; l < n; l += 32) s = fmaf(tof<TW>(wp[l]), tq[l], s);
-      acc = fmaf((float)ecoef[e], s, acc);
+      double v = (double)wsum_f(s);
+      if (k > 0 && lane == 0) {
+        // low-rank terms of the split, in FP64
+        for (int l = 0; l < k; ++l) {
+          const double epl = E[(size_t)l * n + p], eql = E[(size_t)l * n + q];
+          v = fma(epl, (double)R[(size_t)l * n + q], v);
+          v = fma(eql, (double)R[(size_t)l * n + p], v);
+          double t = 0.0;
+          for (int l2 = 0; l2 < k; ++l2) t = fma(Q[l * k + l2], E[(size_t)l2 * n + q], t);
+          v = fma(epl, t, v);
+        }
+      }
+      hv = fma(ecoef[e], v, hv);
     }
-    acc = wsum_f(acc);
-    hv = (double)acc;
     if (lane == 0) Hv[i] = hv;
   }
   if (dv) {
@@ -181,21 +204,120 @@ __global__ void __launch_bounds__(256) k_sddmm_lp(int n, int m, const int* __res
   }
 }
 
+// Split: G^T[c][l] = (E V)[l][c] = sum_{s in row c} V[c][s] E[l][s] (V symmetric);
+// one warp per row c.
+__global__ void k_split_G(int n, int k, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                          const double* __restrict__ Vval, const double* __restrict__ E, double* __restrict__ Gt) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (c >= n) return;
+  double acc[8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) acc[l] = 0.0;
+  for (int s = rowptr[c] + lane; s < rowptr[c + 1]; s += 32) {
+    const double v = Vval[s];
+    const int col = colidx[s];
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+      if (l < k) acc[l] = fma(v, E[(size_t)l * n + col], acc[l]);
+  }
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    if (l >= k) break;
+    const double t = wsum_d(acc[l]);
+    if (lane == 0) Gt[(size_t)c * k + l] = t;
+  }
+}
+
+// Split: partial sums of (G W_s)[l][q] over a chunk of rows c (FP32; grid.y = chunk)
+constexpr int SPLIT_CHUNKS = 16;
+template <typename TW>
+__global__ void k_split_R_part(int n, int k, const double* __restrict__ Gt, const TW* __restrict__ Ws,
+                               float* __restrict__ part) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rows = (n + SPLIT_CHUNKS - 1) / SPLIT_CHUNKS;
+  const int c0 = blockIdx.y * rows, c1 = min(n, c0 + rows);
+  if (q >= n) return;
+  float acc[8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) acc[l] = 0.f;
+  for (int c = c0; c < c1; ++c) {
+    const float w = tof<TW>(Ws[(size_t)c * n + q]);
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+      if (l < k) acc[l] = fmaf((float)Gt[(size_t)c * k + l], w, acc[l]);
+  }
+#pragma unroll
+  for (int l = 0; l < 8; ++l)
+    if (l < k) part[((size_t)blockIdx.y * k + l) * n + q] = acc[l];
+}
+// R[l][q] = lambda_l sum_chunks part;  Q[l][l2] = lambda_l lambda_l2 sum_c G[l][c] E[l2][c]
+// (the Q block is formed by the first k * k warps of the grid)
+__global__ void k_split_R_Q(int n, int k, const float* __restrict__ part, const double* __restrict__ lam,
+                            const double* __restrict__ Gt, const double* __restrict__ E, float* __restrict__ R,
+                            double* __restrict__ Q) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n * k) {
+    const int l = t / n, q = t % n;
+    float s = 0.f;
+    for (int ch = 0; ch < SPLIT_CHUNKS; ++ch) s += part[((size_t)ch * k + l) * n + q];
+    R[t] = (float)(lam[l] * (double)s);
+  }
+  const int w = t >> 5, lane = t & 31;
+  if (w < k * k) {
+    const int l = w / k, l2 = w % k;
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s = fma(Gt[(size_t)c * k + l], E[(size_t)l2 * n + c], s);
+    s = wsum_d(s);
+    if (lane == 0) Q[l * k + l2] = lam[l] * lam[l2] * s;
+  }
+}
+
+// W_s = W - E^T diag(lam) E into Ws (n x n FP64)
+__global__ void k_split_Ws(int n, int k, const double* __restrict__ W, const double* __restrict__ E,
+                           const double* __restrict__ lam, double* __restrict__ Ws) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * n) return;
+  const int a = (int)(t / n), b = (int)(t % n);
+  double v = W[t];
+  for (int l = 0; l < k; ++l) v = fma(-lam[l] * E[(size_t)l * n + a], E[(size_t)l * n + b], v);
+  Ws[t] = v;
+}
+
+// Reduced-precision copy of W, or of W_s when a preconditioner with top
+// eigenpairs is built (the split form); keyed so that a new W or a rebuilt
+// preconditioner refreshes it.
 sdp_status ensure_lowprec_W(sdp_problem* h, int prec) {
-  const size_t nn = (size_t)h->n * h->n;
-  if (prec == SDP_FP32 || prec == SDP_BF16) {
-    if (!h->T32) SDP_TRY(h->allocT(&h->T32, nn));
+  const int n = h->n;
+  const size_t nn = (size_t)n * n;
+  if (prec != SDP_FP32 && prec != SDP_BF16) return SDP_OK;
+  if (!h->T32) SDP_TRY(h->allocT(&h->T32, nn));
+  const bool split = h->pc_valid && h->kpc > 0 && h->Etop && h->KZ && h->kpc <= 8;
+  const int64_t key = split ? h->pc_generation : -1;
+  bool& valid = (prec == SDP_FP32) ? h->W32_valid : h->W16_valid;
+  int64_t& have_key = (prec == SDP_FP32) ? h->W32_key : h->W16_key;
+  if (valid && have_key == key) return SDP_OK;
+  const double* src = h->W;
+  cudaStream_t st = h->stream;
+  if (split) {
+    count_launch();
+    k_split_Ws<<<cdiv(nn, 256), 256, 0, st>>>(n, h->kpc, h->W, h->Etop, h->wtop, h->KZ);
+    src = h->KZ;
+    if (!h->mv_G) {
+      SDP_TRY(h->allocT(&h->mv_G, (size_t)n * 8));
+      SDP_TRY(h->allocT(&h->mv_R, (size_t)n * 8));
+      SDP_TRY(h->allocT(&h->mv_Q, 64));
+      SDP_TRY(h->allocT(&h->mv_part, (size_t)SPLIT_CHUNKS * 8 * n));
+    }
   }
-  if (prec == SDP_FP32 && !h->W32_valid) {
+  if (prec == SDP_FP32) {
     if (!h->W32) SDP_TRY(h->allocT(&h->W32, nn));
-    to_f32(h->stream, nn, h->W, h->W32);
-    h->W32_valid = true;
-  }
-  if (prec == SDP_BF16 && !h->W16_valid) {
+    to_f32(st, nn, src, h->W32);
+  } else {
     if (!h->W16) SDP_TRY(h->allocT(&h->W16, nn));
-    to_bf16(h->stream, nn, h->W, h->W16);
-    h->W16_valid = true;
+    to_bf16(st, nn, src, h->W16);
   }
+  valid = true;
+  have_key = key;
   return SDP_OK;
 }
 
@@ -253,8 +375,26 @@ sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec, do
     k_sddmm_f64<<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(n, h->m, h->eptr, h->ep, h->eq, h->ecoef,
                                                                      h->W, h->T, Hv, dv, h->pcg_part,
                                                                      h->pcg_ticket, dot_out, pro_dst, pro_src);
-  } else if (prec == SDP_FP32) {
+  } else if (prec == SDP_FP32 || prec == SDP_BF16) {
     SDP_TRY(ensure_lowprec_W(h, prec));
+    const bool split = (prec == SDP_FP32 ? h->W32_key : h->W16_key) >= 0;
+    const int ks = split ? h->kpc : 0;
+    if (split) {
+      count_launch(3);
+      k_split_G<<<cdiv((size_t)n * 32, 256), 256, 0, h->stream>>>(n, ks, h->rowptr, h->colidx, h->Vval, h->Etop,
+                                                                    h->mv_G);
+      if (prec == SDP_FP32)
+        k_split_R_part<float><<<dim3(cdiv(n, 128), SPLIT_CHUNKS), 128, 0, h->stream>>>(n, ks, h->mv_G, h->W32,
+                                                                                       h->mv_part);
+      else
+        k_split_R_part<__nv_bfloat16><<<dim3(cdiv(n, 128), SPLIT_CHUNKS), 128, 0, h->stream>>>(
+            n, ks, h->mv_G, h->W16, h->mv_part);
+      const size_t th = std::max((size_t)n * ks, (size_t)ks * ks * 32);
+      k_split_R_Q<<<cdiv(th, 256), 256, 0, h->stream>>>(n, ks, h->mv_part, h->wtop, h->mv_G, h->Etop, h->mv_R,
+                                                        h->mv_Q);
+    }
+  }
+  if (prec == SDP_FP32) {
     switch (rows_per_cta(n, sizeof(float))) {
       case 8: launch_spmm_lp<float, 8>(h, h->Vval, h->W32); break;
       case 4: launch_spmm_lp<float, 4>(h, h->Vval, h->W32); break;
@@ -264,9 +404,8 @@ sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec, do
     count_launch();
     k_sddmm_lp<float><<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(
         n, h->m, h->eptr, h->ep, h->eq, h->ecoef, h->W32, h->T32, Hv, dv, h->pcg_part, h->pcg_ticket, dot_out,
-        pro_dst, pro_src);
+        pro_dst, pro_src, h->W32_key >= 0 ? h->kpc : 0, h->Etop, h->mv_R, h->mv_Q);
   } else if (prec == SDP_BF16) {
-    SDP_TRY(ensure_lowprec_W(h, prec));
     switch (rows_per_cta(n, sizeof(float))) {
       case 8: launch_spmm_lp<__nv_bfloat16, 8>(h, h->Vval, h->W16); break;
       case 4: launch_spmm_lp<__nv_bfloat16, 4>(h, h->Vval, h->W16); break;
@@ -276,8 +415,8 @@ sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec, do
     count_launch();
     k_sddmm_lp<__nv_bfloat16><<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(
         n, h->m, h->eptr, h->ep, h->eq, h->ecoef, h->W16, h->T32, Hv, dv, h->pcg_part, h->pcg_ticket, dot_out,
-        pro_dst, pro_src);
-  } else {
+        pro_dst, pro_src, h->W16_key >= 0 ? h->kpc : 0, h->Etop, h->mv_R, h->mv_Q);
+  } else if (prec != SDP_FP64) {
     h->last_error = "hessian_matvec: unknown precision";
     return SDP_ERR_ARG;
   }

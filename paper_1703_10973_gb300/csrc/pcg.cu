@@ -268,13 +268,15 @@ static sdp_status pcg_impl_(sdp_problem* h, const double* r, double* y, double r
   int total = 0;
   sdp_status result = SDP_ERR_MAXIT;
   const int sweeps = std::max(1, h->prm.refine_maxit);
-  const double inner = std::max(h->prm.inner_rtol, rtol);
+  const double inner_fp64 = std::max(h->prm.inner_rtol, rtol);
+  const double inner_lp = std::max(h->prm.inner_rtol_lp, rtol);
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     int it = 0;
     double rr = 0.0;
     const int budget = std::max(1, std::min(maxit - total, 500));
     bool brk = false;
-    sdp_status s = pcg_core(h, resid, corr, inner, budget, prec, &it, &rr, &brk);
+    sdp_status s = pcg_core(h, resid, corr, prec == SDP_FP64 ? inner_fp64 : inner_lp, budget, prec, &it, &rr,
+                            &brk);
     total += it;
     if (s != SDP_OK && s != SDP_ERR_MAXIT) return s;
     if (brk && it <= 1 && prec == SDP_FP64) break;   // breakdown before any progress

@@ -52,6 +52,7 @@ extern "C" void sdp_default_params(sdp_params* p) {
   p->inner_rtol = 1e-9;
   p->verbose = 0;
   p->pcg_graph = 1;
+  p->inner_rtol_lp = 1e-4;
 }
 
 extern "C" const char* sdp_status_str(sdp_status s) {

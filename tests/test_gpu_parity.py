@@ -112,6 +112,29 @@ def test_matvec_reduced_precision(prec, tol):
     assert _rel(hv, o.hessian_matvec(P, W, v)) <= tol
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16", 5e-2)])
+def test_matvec_split_reduced_precision_near_optimum(prec, tol):
+    """With the preconditioner built, the reduced-precision matvec splits W = W_l + W_s.
+    On a W with k eigenvalues of order 1/mu (mu = 1e-4) the error, measured as
+    ||H^{-1}(Hv_gpu - Hv)|| / ||v|| (the scale PCG works on), stays at the working
+    precision, where rounding W whole loses the small part of W."""
+    d = si.mc_instance(20, 25, 2, 300, 8)
+    P = o.Problem.from_data(d)
+    W = _ipm_like_W(d.n, 2, 1e-4, 3)
+    H = o.hessian_entries(P, W)
+    v = si.random_vec(d.m, 1)
+    ref = H @ v
+    with _prob(d) as prob:
+        prob.set_W(_dev(W))
+        plain = prob.hessian_matvec(_dev(v), prec=prec).cpu().numpy()
+        prob.precond_build()
+        split = prob.hessian_matvec(_dev(v), prec=prec).cpu().numpy()
+    e_split = np.linalg.norm(np.linalg.solve(H, split - ref)) / np.linalg.norm(v)
+    e_plain = np.linalg.norm(np.linalg.solve(H, plain - ref)) / np.linalg.norm(v)
+    assert e_split <= tol
+    assert e_split <= 0.1 * e_plain
+
+
 # --------------------------------------------------------------------------
 # preconditioner
 # --------------------------------------------------------------------------
