@@ -392,13 +392,67 @@ def run(args):
     return 0
 
 
+def run_serving(args):
+    """Poisson request stream (the serving specs: p, q log-uniform, r in 1..5), continuous
+    batching with admission by a device-memory budget; the arrival rate is swept as
+    fractions of the capacity measured with every request present at time 0."""
+    import torch
+    import sdp_inputs as si
+    from paper_1703_10973_gb300 import _build, load
+    from paper_1703_10973_gb300.serve import Request, Server, cuda_solver
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    load()
+    specs = [s for s in si.serving_specs(2000) if s["p"] + s["q"] <= args.serve_max_n][:args.requests]
+    insts = [si.mc_instance(s["p"], s["q"], s["r"], s["m"], s["seed"]) for s in specs]
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    solver = cuda_solver()
+
+    def once(arrivals):
+        srv = Server(budget_bytes=budget, slots=args.streams, solver=solver)
+        res = srv.run([Request(rid=i, data=d, arrival=float(a)) for i, (d, a) in enumerate(zip(insts, arrivals))])
+        return srv.stats, res
+
+    once([0.0] * len(insts))                         # warm-up (module load, first allocations)
+    with Clocks(local) as clk:
+        cap_stats, cap_res = once([0.0] * len(insts))
+        cap = cap_stats["solves_per_s"]
+        sweep = [dict(rate="all at t=0", **{k: cap_stats[k] for k in ("solves_per_s", "p50_ms", "p99_ms",
+                                                                       "max_concurrent")})]
+        for f in [float(x) for x in args.rates.split(",") if x]:
+            rate = f * cap
+            arr = si.serving_arrivals(len(insts), rate)
+            st, _ = once(arr)
+            sweep.append(dict(rate=rate, rate_frac=f, **{k: st[k] for k in ("solves_per_s", "p50_ms", "p99_ms",
+                                                                             "max_concurrent")}))
+    if rank == 0:
+        line = {"metric": METRIC, "value": cap, "unit": UNIT, "n_gpus": ws, "steps": len(sweep),
+                "warmup": 1, "ms_per_step": 1e3 * len(insts) / cap if cap else None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"serving: first {len(insts)} of the 2000 served requests with n <= "
+                                       f"{args.serve_max_n} (p, q log-uniform in [50, 3000], r in 1..5, seeds 5000+)",
+                           "slots": args.streams, "budget_bytes": budget,
+                           "converged": all(r.converged for r in cap_res if r.ok),
+                           "completed": cap_stats["completed"]},
+                "latency_ms": {"p50": cap_stats["p50_ms"], "p99": cap_stats["p99_ms"]},
+                "serving_sweep": sweep, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "C2"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "C2", "serving"])
+    ap.add_argument("--requests", type=int, default=24, help="serving: requests per arrival rate")
+    ap.add_argument("--serve-max-n", type=int, default=800, help="serving: largest SDP order admitted to the sample")
+    ap.add_argument("--rates", default="0.25,0.5,1,1.5", help="serving: arrival rates as fractions of capacity")
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--streams", type=int, default=4)
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16"])
@@ -411,6 +465,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run(args)
 
 

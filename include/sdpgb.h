@@ -221,6 +221,11 @@ sdp_status sdp_timing_read(sdp_problem* h, double* ms, int64_t* launches, double
  * accumulators and returns the length the full report needs. */
 int64_t sdp_timing_report(sdp_problem* h, char* buf, int64_t len);
 
+/* Device memory held by the handle (bytes of its allocations; buffers are
+ * allocated on first use, so this grows during the first IPM iteration).
+ * Serving admission compares estimates against it. */
+int64_t sdp_device_bytes(const sdp_problem* h);
+
 /* Number of kernel launches issued by this handle since setup (for accounting). */
 int64_t sdp_launch_count(const sdp_problem* h);
 

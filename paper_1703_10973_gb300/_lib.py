@@ -97,6 +97,7 @@ SIGNATURES = {
     "sdp_precond_info": (C.c_int, [_P, _DP, C.POINTER(C.c_int)]),
     "sdp_sizes": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "sdp_launch_count": (C.c_int64, [_P]),
+    "sdp_device_bytes": (C.c_int64, [_P]),
     "sdp_reset": (C.c_int, [_P]),
     "sdp_timing_enable": (C.c_int, [_P, C.c_char_p]),
     "sdp_timing_read": (C.c_int, [_P, _DP, C.POINTER(C.c_int64), _DP, _DP]),

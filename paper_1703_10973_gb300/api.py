@@ -186,6 +186,9 @@ class SDPProblem:
         self._raise(self.lib.sdp_sizes(self.h, C.byref(n), C.byref(m), C.byref(k), C.byref(nnz)), "sdp_sizes")
         return n.value, m.value, k.value, nnz.value
 
+    def device_bytes(self):
+        return int(self.lib.sdp_device_bytes(self.h))
+
     def launch_count(self):
         return int(self.lib.sdp_launch_count(self.h))
 

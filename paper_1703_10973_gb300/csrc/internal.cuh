@@ -366,6 +366,7 @@ struct sdp_problem {
   unsigned int* pcg_ticket = nullptr;  // their arrival tickets (one per reduction)
 
   std::vector<void*> owned;   // every cudaMalloc made for this handle
+  int64_t device_bytes = 0;   // their total size
 
   void set_error(sdp_status s, const std::string& msg) {
     (void)s;

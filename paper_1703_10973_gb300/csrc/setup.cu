@@ -34,6 +34,7 @@ sdp_status sdp_problem::alloc(void** p, size_t bytes) {
     return SDP_ERR_OOM;
   }
   owned.push_back(*p);
+  device_bytes += (int64_t)bytes;
   return SDP_OK;
 }
 
@@ -69,6 +70,8 @@ extern "C" const char* sdp_status_str(sdp_status s) {
   }
   return "unknown status";
 }
+
+extern "C" int64_t sdp_device_bytes(const sdp_problem* h) { return h ? h->device_bytes : -1; }
 
 extern "C" const char* sdp_last_error(const sdp_problem* h) {
   return h ? h->last_error.c_str() : sdpgb::free_call_error();
