@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_sytrd(int n, double* A, int lda, double
       const double vi = v[i - j - 1], wi = w[i - j - 1];
       for (int l = lane; l < len; l += 32) {
         const double x = __ldcg(ai + l);
-        ai[l] = x - fma(vi, w[l], wi * v[l]);
+        ai[l] = fma(-vi, w[l], fma(-wi, v[l], x));
       }
     }
     if (blockIdx.x == 0) {
@@ -281,14 +281,14 @@ __global__ void __launch_bounds__(SY_THREADS) k_sytrd_cluster(int n, double* A, 
       for (; l + 96 < len; l += 128) {
         const double x0 = __ldcg(ai + l), x1 = __ldcg(ai + l + 32), x2 = __ldcg(ai + l + 64),
                      x3 = __ldcg(ai + l + 96);
-        ai[l] = x0 - fma(vi, w[l], wi * v[l]);
-        ai[l + 32] = x1 - fma(vi, w[l + 32], wi * v[l + 32]);
-        ai[l + 64] = x2 - fma(vi, w[l + 64], wi * v[l + 64]);
-        ai[l + 96] = x3 - fma(vi, w[l + 96], wi * v[l + 96]);
+        ai[l] = fma(-vi, w[l], fma(-wi, v[l], x0));
+        ai[l + 32] = fma(-vi, w[l + 32], fma(-wi, v[l + 32], x1));
+        ai[l + 64] = fma(-vi, w[l + 64], fma(-wi, v[l + 64], x2));
+        ai[l + 96] = fma(-vi, w[l + 96], fma(-wi, v[l + 96], x3));
       }
       for (; l < len; l += 32) {
         const double x = __ldcg(ai + l);
-        ai[l] = x - fma(vi, w[l], wi * v[l]);
+        ai[l] = fma(-vi, w[l], fma(-wi, v[l], x));
       }
     }
     if (rank == 0) {
