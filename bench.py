@@ -242,14 +242,33 @@ def run(args):
     insts, desc = workload(args.workload, args.batch, rank, ws)
     kk = 8 if args.workload == "C2" else 0
     params = default_params(prec=args.prec, k=kk, pcg_maxit=args.pcg_maxit, pcg_graph=args.pcg_graph)
-    nstreams = min(args.streams, len(insts))
+    nstreams = len(insts) if args.batched_launch else min(args.streams, len(insts))
     streams = [torch.cuda.Stream() for _ in range(nstreams)]
     probs = [SDPProblem.from_data(d, params=params, stream=streams[i % nstreams].cuda_stream)
              for i, d in enumerate(insts)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    batch = None
+    if args.batched_launch:
+        from paper_1703_10973_gb300 import SDPBatch
+        bstream = torch.cuda.Stream()
+        batch = SDPBatch(probs, stream=bstream.cuda_stream)
+
     def run_batch(start_event=None):
         """Solve every instance once; stream s handles instances s, s+S, ...  Returns per-solve ms."""
+        if batch is not None:   # lockstep: one launch per PCG step for all problems
+            if start_event is not None:
+                bstream.wait_event(start_event)
+                for st in streams:
+                    st.wait_event(start_event)
+            torch.cuda.synchronize()
+            for p in probs:
+                p.reset()
+            t0b = time.perf_counter()
+            res_b = batch.solve(allow_maxit=True)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0b) * 1e3
+            return [ms] * len(probs), res_b
         if start_event is not None:
             for st in streams:
                 st.wait_event(start_event)
@@ -373,6 +392,18 @@ def run(args):
                 except Exception as e:
                     errs.append(e)
 
+            if args.batched_launch:   # set up all, solve in lockstep, copy every solution back
+                from paper_1703_10973_gb300 import SDPBatch
+                ps = [SDPProblem.from_data(insts[i], params=params, stream=streams[i].cuda_stream)
+                      for i in range(len(insts))]
+                with SDPBatch(ps, stream=bstream.cuda_stream) as b2:
+                    b2.solve(allow_maxit=True)
+                for i, p2 in enumerate(ps):
+                    X, y = outs[i]
+                    st = p2.lib.sdp_get_solution(p2.h, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data), None)
+                    assert st == 0
+                    p2.close()
+                continue
             th = [threading.Thread(target=e2e_worker, args=(s,)) for s in range(nstreams)]
             for t in th:
                 t.start()
@@ -399,6 +430,7 @@ def run(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else args.prec,
                 "data": "synthetic",
                 "config": {"workload": desc, "instances": len(insts), "streams": nstreams, "prec": args.prec, "pcg_loop": "graph" if args.pcg_graph else "host",
+                           "batched_launch": bool(args.batched_launch),
                            "parallelism": f"replicas{ws}", "l2_flush": True, "converged": converged,
                            "ipm_iters_mean": float(np.mean(ipm_iters)),
                            "pcg_iters_per_solve_mean": float(np.mean(pcg_iters)),
@@ -408,6 +440,8 @@ def run(args):
                 "clocks": clk.summary(),
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
+    if batch is not None:
+        batch.close()
     for p in probs:
         p.close()
     if dist is not None:
@@ -484,6 +518,8 @@ def main():
                     help="kernel class for the roofline object; auto = the one with the most device time")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-launch", action="store_true",
+                    help="solve the batch in lockstep with one launch per PCG step for all problems")
     ap.add_argument("--pcg-graph", type=int, default=1, choices=[0, 1],
                     help="0: host-driven PCG loop (same kernels; for profilers without conditional-graph support)")
     args = ap.parse_args()

@@ -230,6 +230,27 @@ int64_t sdp_device_bytes(const sdp_problem* h);
 int64_t sdp_launch_count(const sdp_problem* h);
 
 /*
+ * Batched solves (SURVEY pattern "batched": many uneven problems advanced
+ * together).  sdp_batch_create groups count set-up problems (each keeps its own
+ * stream, data and state; all must use SDP_FP64 and SDP_PRECOND_HAT, 1 <= k <= 8).
+ * sdp_batch_solve runs their interior-point iterations in lockstep: the dense
+ * per-problem phases on each problem's stream (one host thread per problem),
+ * and every PCG iteration of all their Newton systems as one sequence of
+ * batched launches on cuda_stream, captured once as a CUDA graph that loops on
+ * the device while any problem's PCG is running.  A problem's iterates are the
+ * same in a batch as alone.  results: count entries (NULL allowed).  Returns
+ * SDP_OK when every problem converged, SDP_ERR_MAXIT when some hit an
+ * iteration limit, else the first error (sdp_batch_last_error).  Problems
+ * start from their current iterate (sdp_reset for the start point).  The batch
+ * does not own the problems; destroy the batch before them.
+ */
+typedef struct sdp_batch sdp_batch;
+sdp_status sdp_batch_create(sdp_problem* const* problems, int count, void* cuda_stream, sdp_batch** out);
+sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results);
+const char* sdp_batch_last_error(const sdp_batch* b);
+void sdp_batch_destroy(sdp_batch* b);
+
+/*
  * sdp_hessian_matvec_static -- handle-free, allocation-free variant of
  * sdp_hessian_matvec.  This call is an addition of this library for callers
  * that cannot allocate device memory; the paper has no counterpart.

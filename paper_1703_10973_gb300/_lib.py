@@ -103,6 +103,10 @@ SIGNATURES = {
     "sdp_timing_read": (C.c_int, [_P, _DP, C.POINTER(C.c_int64), _DP, _DP]),
     "sdp_timing_report": (C.c_int64, [_P, C.c_char_p, C.c_int64]),
     "sdp_hessian_matvec_static": (C.c_int, [C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "sdp_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, _P, C.POINTER(_P)]),
+    "sdp_batch_solve": (C.c_int, [_P, C.POINTER(sdp_result)]),
+    "sdp_batch_last_error": (C.c_char_p, [_P]),
+    "sdp_batch_destroy": (None, [_P]),
     "sdp_destroy": (None, [_P]),
     "sdp_status_str": (C.c_char_p, [C.c_int]),
     "sdp_last_error": (C.c_char_p, [_P]),

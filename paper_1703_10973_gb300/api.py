@@ -245,3 +245,45 @@ def hessian_matvec_static(n, m, Ak, Ai, Aj, Av, W, v, out=None, stream=None):
         raise L.SDPError(st, f"sdp_hessian_matvec_static: {lib.sdp_status_str(st).decode()}: "
                              f"{lib.sdp_last_error(None).decode()}")
     return out
+
+
+class SDPBatch:
+    """sdp_batch_*: solve several SDPProblem objects in lockstep with batched PCG launches."""
+
+    def __init__(self, problems, stream=None):
+        self.lib = L.load()
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        b = C.c_void_p()
+        st = self.lib.sdp_batch_create(arr, len(self.problems), C.c_void_p(stream) if stream else None, C.byref(b))
+        if st != L.SDP_OK:
+            raise L.SDPError(st, f"sdp_batch_create: {self.lib.sdp_status_str(st).decode()}")
+        self.b = b
+
+    def solve(self, allow_maxit=False):
+        res = (L.sdp_result * len(self.problems))()
+        st = self.lib.sdp_batch_solve(self.b, res)
+        ok = (L.SDP_OK, L.SDP_ERR_MAXIT) if allow_maxit else (L.SDP_OK,)
+        if st not in ok:
+            raise L.SDPError(st, f"sdp_batch_solve: {self.lib.sdp_status_str(st).decode()}: "
+                                 f"{self.lib.sdp_batch_last_error(self.b).decode()}")
+        return [{f: getattr(r, f) for f, _ in L.sdp_result._fields_} for r in res]
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.sdp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,336 @@
+// Batched solves: many SDPs advanced in lockstep, with every PCG iteration of
+// all their Newton systems run as one sequence of launches over all problems.
+//
+// sdp_batch_solve runs the interior-point iterations of every problem of the
+// batch together.  The dense per-problem phases (NT scaling, preconditioner,
+// step lengths, update: ipm_phase_a/b/c) run on each problem's own stream from
+// one host thread per problem.  The two Newton systems of an iteration are
+// solved for all problems at once: each PCG iteration is one fixed sequence of
+// batched kernels (assemble, SpMM, SDDMM with p.Hp, x/r update with the loop
+// test, the Hhat apply, direction update), each launch covering every problem
+// -- the grid is the concatenation of the problems' own grids, and a block
+// finds its problem from a table of block offsets.  The sequence is captured
+// once as a CUDA graph whose conditional while node runs until no problem is
+// active; a problem leaves the active set when its own loop test fails, and its
+// blocks then return at once.  Every batched kernel runs the same device code
+// over the same block partition as the single-problem kernel, so a problem's
+// iterates are bitwise the same in a batch and alone.
+//
+// The restarted outer loop (refinement on the FP64 true residual) is the
+// single-problem PcgSweeps state machine, stepped for all problems together.
+// Supported: FP64 matvec and the Hhat preconditioner (the defaults).
+#include "internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace sdpgb {
+
+static inline int cdivi(int a, int b) { return (a + b - 1) / b; }
+
+enum { BK_ASM, BK_SPMM, BK_SDDMM, BK_VEC, BK_HATU, BK_TAIL, BK_FWDP, BK_FWDR, BK_GEMV, BK_OUTR, BK_BWDP, BK_COUNT };
+
+}  // namespace sdpgb
+
+struct sdp_batch {
+  std::vector<sdp_problem*> hs;
+  cudaStream_t stream = nullptr;      // the batched launches
+  cudaStream_t capture = nullptr;     // capture stream for the graph
+  sdpgb::BDesc* ddesc = nullptr;
+  int* doff = nullptr;                // BK_COUNT x (N + 1) block offsets
+  std::vector<int> off;               // host copy
+  int total[sdpgb::BK_COUNT] = {};
+  int nmax = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t body_launches = 0;
+  std::string last_error;
+};
+
+namespace sdpgb {
+
+static bool batch_supported(sdp_problem* h, std::string* why) {
+  if (h->prm.prec != SDP_FP64) { *why = "batched solves run the FP64 matvec (params.prec = SDP_FP64)"; return false; }
+  if (h->prm.precond != SDP_PRECOND_HAT) { *why = "batched solves use the Hhat preconditioner"; return false; }
+  const int k = std::min(h->k, std::max(h->n - 1, 0));
+  if (k < 1 || k > 8) { *why = "batched solves need 1 <= k <= 8"; return false; }
+  return true;
+}
+
+// Block offsets of every batched kernel (sizes only, fixed for the batch).
+static void batch_offsets(sdp_batch* b) {
+  const int N = (int)b->hs.size();
+  b->off.assign((size_t)BK_COUNT * (N + 1), 0);
+  b->nmax = 0;
+  for (int i = 0; i < N; ++i) {
+    sdp_problem* h = b->hs[i];
+    const int k = std::min(h->k, h->n - 1), Rk = h->hs_nr * k;
+    const int cnt[BK_COUNT] = {batch_blocks_assemble(h->nnzV), batch_blocks_spmm(h->n), batch_blocks_sddmm(h->m),
+                               batch_blocks_vec(h->m),         batch_blocks_hat_u(h->n), batch_blocks_tail(h->m),
+                               batch_blocks_fwdP(h->hs_np),    batch_blocks_warp_rows(h->hs_nr),
+                               batch_blocks_warp_rows(Rk),     batch_blocks_outR(Rk),
+                               batch_blocks_warp_rows(h->hs_np)};
+    for (int kd = 0; kd < BK_COUNT; ++kd)
+      b->off[(size_t)kd * (N + 1) + i + 1] = b->off[(size_t)kd * (N + 1) + i] + cnt[kd];
+    b->nmax = std::max(b->nmax, h->n);
+  }
+  for (int kd = 0; kd < BK_COUNT; ++kd) b->total[kd] = b->off[(size_t)kd * (N + 1) + N];
+}
+
+static BDesc make_desc(sdp_problem* h, int active) {
+  BDesc D{};
+  D.n = h->n; D.m = h->m; D.k = h->kpc; D.np = h->hs_np; D.nr = h->hs_nr; D.Rk = h->hs_nr * h->kpc;
+  D.nnzV = h->nnzV;
+  D.active = active;
+  D.zscale = h->zscale;
+  D.inv_tau2 = 1.0 / (h->tau * h->tau);
+  D.rowptr = h->rowptr; D.colidx = h->colidx; D.sptr = h->sptr; D.scon = h->scon;
+  D.eptr = h->eptr; D.ep = h->ep; D.eq = h->eq;
+  D.scoef = h->scoef; D.ecoef = h->ecoef; D.ginv = h->ginv;
+  D.W = h->W; D.U = h->U; D.T = h->T; D.Vval = h->Vval;
+  D.pverts = h->hs_pverts; D.rverts = h->hs_rverts; D.btptr = h->hs_btptr; D.btslot = h->hs_btslot;
+  D.bp = h->hs_bp; D.bptr = h->hs_bptr; D.bcol = h->hs_bcol;
+  D.D = h->hs_D; D.F = h->hs_F; D.Cinv = h->hs_Cinv; D.CinvT = h->hs_CinvT;
+  D.yP = h->hs_yP; D.v1 = h->hs_v1; D.v2 = h->hs_v2; D.uvec = h->uvec; D.Bn = h->Bn;
+  D.px = h->px; D.pr = h->pr; D.pp = h->pp; D.pq = h->pq; D.pz = h->pz;
+  D.scal = h->scal; D.part = h->pcg_part; D.ticket = h->pcg_ticket;
+  return D;
+}
+
+// One PCG iteration of every active problem (the body of the batched loop).
+static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle cond) {
+  const int N = (int)b->hs.size();
+  const int* o = b->doff;
+  auto off = [&](int kd) { return o + (size_t)kd * (N + 1); };
+  batch_launch_matvec(st, b->ddesc, off(BK_ASM), off(BK_SPMM), off(BK_SDDMM), N, b->total[BK_ASM],
+                      b->total[BK_SPMM], b->total[BK_SDDMM], b->nmax);
+  batch_launch_xr(st, b->ddesc, off(BK_VEC), N, b->total[BK_VEC]);
+  batch_launch_hat_u(st, b->ddesc, off(BK_HATU), N, b->total[BK_HATU]);
+  batch_launch_core_solve(st, b->ddesc, N, off(BK_FWDP), b->total[BK_FWDP], off(BK_FWDR), b->total[BK_FWDR],
+                          off(BK_GEMV), b->total[BK_GEMV], off(BK_OUTR), b->total[BK_OUTR], off(BK_BWDP),
+                          b->total[BK_BWDP]);
+  batch_launch_tail(st, b->ddesc, off(BK_TAIL), N, b->total[BK_TAIL]);
+  batch_launch_p(st, b->ddesc, off(BK_VEC), N, b->total[BK_VEC]);
+  batch_launch_any(st, b->ddesc, N, cond);
+}
+
+static sdp_status batch_prepare(sdp_batch* b) {
+  if (b->exec) return SDP_OK;
+  const int N = (int)b->hs.size();
+  batch_offsets(b);
+  if (cudaMalloc(&b->ddesc, sizeof(BDesc) * N) != cudaSuccess ||
+      cudaMalloc(&b->doff, sizeof(int) * b->off.size()) != cudaSuccess) {
+    cudaGetLastError();
+    b->last_error = "sdp_batch: device allocation failed";
+    return SDP_ERR_OOM;
+  }
+  cudaMemcpy(b->doff, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice);
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle cond;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess || cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    b->last_error = "sdp_batch: graph creation failed";
+    return SDP_ERR_CUDA;
+  }
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    b->last_error = "sdp_batch: conditional node failed";
+    return SDP_ERR_CUDA;
+  }
+  const int64_t l0 = t_launches;
+  ktimer_pause(true);
+  cudaError_t e = cudaStreamBeginCaptureToGraph(b->capture, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) batch_body(b, b->capture, cond);
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b->capture, &out);
+  ktimer_pause(false);
+  b->body_launches = t_launches - l0;
+  g_launches.fetch_sub(b->body_launches);
+  t_launches = l0;
+  if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    b->last_error = std::string("sdp_batch: graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+    return SDP_ERR_CUDA;
+  }
+  b->graph = g;
+  return SDP_OK;
+}
+
+// The Newton systems H dy = rhs of the listed problems, solved together.
+static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::vector<int>& its,
+                               std::vector<double>& rr, std::vector<sdp_status>& st) {
+  const int N = (int)b->hs.size();
+  std::vector<PcgSweeps> S(N);
+  std::vector<char> live(N, 0);
+  for (int i : idx) {
+    sdp_problem* h = b->hs[i];
+    st[i] = pcg_sweeps_init(h, &S[i], h->rhs, h->dy, h->prm.pcg_rtol, h->prm.pcg_maxit, SDP_FP64);
+    live[i] = (st[i] == SDP_OK);
+  }
+  SDP_TRY(batch_prepare(b));
+  std::vector<BDesc> hd(N);
+  for (;;) {
+    std::vector<int> running;
+    for (int i : idx) {
+      if (!live[i]) continue;
+      bool run = false;
+      st[i] = pcg_sweep_begin(b->hs[i], &S[i], false, &run);
+      if (st[i] != SDP_OK) { live[i] = 0; continue; }
+      if (run) running.push_back(i);
+      else live[i] = 0;
+    }
+    if (running.empty()) break;
+    for (int i = 0; i < N; ++i) hd[i] = make_desc(b->hs[i], 0);
+    for (int i : running) {
+      cudaStreamSynchronize(b->hs[i]->stream);
+      hd[i].active = 1;
+    }
+    if (cudaMemcpyAsync(b->ddesc, hd.data(), sizeof(BDesc) * N, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaGraphLaunch(b->exec, b->stream) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+      b->last_error = std::string("sdp_batch: batched PCG failed: ") + cudaGetErrorString(cudaGetLastError());
+      return SDP_ERR_CUDA;
+    }
+    int max_it = 0;
+    for (int i : running) {
+      const int before = S[i].total;
+      st[i] = pcg_sweep_end(b->hs[i], &S[i]);
+      max_it = std::max(max_it, S[i].total - before);
+      if (st[i] != SDP_OK) live[i] = 0;
+    }
+    g_launches.fetch_add((int64_t)max_it * b->body_launches);
+  }
+  for (int i : idx) {
+    its[i] = S[i].total;
+    rr[i] = S[i].tr;
+    if (st[i] == SDP_OK && S[i].result != SDP_OK) st[i] = SDP_OK;   // MAXIT: keep the best iterate
+  }
+  return SDP_OK;
+}
+
+// Runs fn(i) for every listed problem on its own host thread.
+template <typename F>
+static void parallel_for(const std::vector<int>& idx, F fn) {
+  std::vector<std::thread> th;
+  th.reserve(idx.size());
+  for (int i : idx) th.emplace_back([&fn, i] { fn(i); });
+  for (auto& t : th) t.join();
+}
+
+}  // namespace sdpgb
+
+using namespace sdpgb;
+
+extern "C" sdp_status sdp_batch_create(sdp_problem* const* hs, int count, void* cuda_stream, sdp_batch** out) {
+  if (!out || !hs || count < 1) return SDP_ERR_ARG;
+  *out = nullptr;
+  std::string why;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return SDP_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return SDP_ERR_ARG;
+    if (!batch_supported(hs[i], &why)) return SDP_ERR_UNSUPPORTED;
+  }
+  sdp_batch* b = new sdp_batch();
+  b->hs.assign(hs, hs + count);
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return SDP_ERR_CUDA;
+  }
+  *out = b;
+  return SDP_OK;
+}
+
+extern "C" sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results) {
+  if (!b) return SDP_ERR_ARG;
+  const int N = (int)b->hs.size();
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<IpmStepState> s(N);
+  std::vector<sdp_status> st(N, SDP_OK);
+  std::vector<char> done(N, 0);
+  std::vector<int> pcg_total(N, 0), its(N, 0);
+  std::vector<double> rr(N, 0.0);
+  int ipm_maxit = 0;
+  for (auto* h : b->hs) ipm_maxit = std::max(ipm_maxit, h->prm.ipm_maxit);
+  for (int it = 0; it <= ipm_maxit; ++it) {
+    std::vector<int> act;
+    for (int i = 0; i < N; ++i)
+      if (!done[i] && st[i] == SDP_OK && it <= b->hs[i]->prm.ipm_maxit) act.push_back(i);
+    if (act.empty()) break;
+    std::vector<char> conv(N, 0);
+    parallel_for(act, [&](int i) {
+      bool d = false;
+      st[i] = ipm_phase_a(b->hs[i], &s[i], &d);
+      conv[i] = d;
+    });
+    std::vector<int> solve;
+    for (int i : act) {
+      if (st[i] != SDP_OK) continue;
+      if (conv[i]) done[i] = 1;
+      else if (it < b->hs[i]->prm.ipm_maxit) solve.push_back(i);
+      else done[i] = 2;   // iteration limit
+    }
+    if (solve.empty()) continue;
+    SDP_TRY(batch_newton(b, solve, its, rr, st));
+    std::vector<int> nxt;
+    for (int i : solve) if (st[i] == SDP_OK) nxt.push_back(i);
+    parallel_for(nxt, [&](int i) {
+      pcg_total[i] += its[i];
+      st[i] = ipm_phase_b(b->hs[i], &s[i], its[i], rr[i]);
+    });
+    std::vector<int> nxt2;
+    for (int i : nxt) if (st[i] == SDP_OK) nxt2.push_back(i);
+    SDP_TRY(batch_newton(b, nxt2, its, rr, st));
+    std::vector<int> nxt3;
+    for (int i : nxt2) if (st[i] == SDP_OK) nxt3.push_back(i);
+    parallel_for(nxt3, [&](int i) {
+      pcg_total[i] += its[i];
+      st[i] = ipm_phase_c(b->hs[i], &s[i], its[i], rr[i]);
+    });
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  sdp_status worst = SDP_OK;
+  for (int i = 0; i < N; ++i) {
+    sdp_result r{};
+    r.obj_p = s[i].inf.obj_p;
+    r.obj_d = s[i].inf.obj_d;
+    r.relgap = s[i].inf.relgap;
+    r.pinf = s[i].inf.pinf;
+    r.dinf = s[i].inf.dinf;
+    r.iters = b->hs[i]->iter;
+    r.pcg_iters_total = pcg_total[i];
+    r.converged = (done[i] == 1) ? 1 : 0;
+    r.seconds = secs;
+    if (results) results[i] = r;
+    if (st[i] != SDP_OK && worst == SDP_OK) {
+      worst = st[i];
+      b->last_error = "problem " + std::to_string(i) + ": " + b->hs[i]->last_error;
+    }
+    if (st[i] == SDP_OK && !r.converged && worst == SDP_OK) worst = SDP_ERR_MAXIT;
+  }
+  return worst;
+}
+
+extern "C" const char* sdp_batch_last_error(const sdp_batch* b) { return b ? b->last_error.c_str() : ""; }
+
+extern "C" void sdp_batch_destroy(sdp_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->ddesc) cudaFree(b->ddesc);
+  if (b->doff) cudaFree(b->doff);
+  delete b;
+}

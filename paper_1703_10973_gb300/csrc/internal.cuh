@@ -34,26 +34,65 @@ __device__ inline double lb_block_sum(double v, double* sh) {
   }
   return s;  // valid in thread 0
 }
-__device__ inline bool lb_reduce(double v, double* part, unsigned int* ticket, double* total) {
+// Block b of a group of nb blocks (a whole grid, or one problem's share of a
+// batched grid) stores its partial in part[b]; the last block of the group to
+// arrive (atomic ticket) adds the partials in index order and, in its thread 0,
+// returns true with the total in *total (then re-arms the ticket).
+__device__ inline bool lb_reduce(double v, double* part, unsigned int* ticket, double* total, int b, int nb) {
   __shared__ double sh[32];
   __shared__ int s_last;
-  const double b = lb_block_sum(v, sh);
+  const double s0 = lb_block_sum(v, sh);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = b;
+    part[b] = s0;
     __threadfence();
-    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+    s_last = (atomicAdd(ticket, 1u) == (unsigned)nb - 1u) ? 1 : 0;
   }
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
   double s = 0.0;
-  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) s += __ldcg(part + i);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += __ldcg(part + i);
   s = lb_block_sum(s, sh);
   if (threadIdx.x == 0) {
     *total = s;
     *ticket = 0u;
   }
   return threadIdx.x == 0;
+}
+
+// Scalar slots of a PCG run (device array scal[])
+enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6, S_IT = 7, S_MAXIT = 8,
+       S_BRK = 9, S_GO = 10 };
+
+// One problem of a batched PCG launch (FP64 matvec, Hhat preconditioner): the
+// device pointers and sizes the batched kernels read, refreshed by the host
+// before every batched solve.
+struct BDesc {
+  int n, m, k, np, nr, Rk, nnzV;
+  int active;                       // the problem's PCG loop is still running
+  double zscale, inv_tau2;
+  const int *rowptr, *colidx, *sptr, *scon, *eptr, *ep, *eq;
+  const double *scoef, *ecoef, *ginv;
+  const double *W, *U;
+  double *T, *Vval;
+  const int *pverts, *rverts, *btptr, *btslot, *bp, *bptr, *bcol;
+  const double *D, *F, *Cinv, *CinvT;
+  double *yP, *v1, *v2, *uvec, *Bn;
+  double *px, *pr, *pp, *pq, *pz;
+  double *scal, *part;
+  unsigned int* ticket;
+};
+
+// Finds the problem that owns block b of a batched grid: off[0..N] are the
+// first blocks of each problem (off[N] = total).
+__device__ inline int batch_find(const int* off, int N, int b) {
+  int lo = 0, hi = N;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
 }
 }  // namespace sdpgb
 
@@ -329,7 +368,7 @@ struct sdp_problem {
   int *hs_bptr = nullptr, *hs_bcol = nullptr, *hs_bp = nullptr;  // B blocks by row of P
   int *hs_btptr = nullptr, *hs_btslot = nullptr;         // B blocks by row of R
   double *hs_D = nullptr, *hs_F = nullptr, *hs_yP = nullptr;     // L_P, F = L_P^{-1} B, y_P
-  double *hs_C = nullptr, *hs_Cinv = nullptr;            // Schur complement factor and inverse
+  double *hs_C = nullptr, *hs_Cinv = nullptr, *hs_CinvT = nullptr;   // Schur factor, inverse, its transpose
   double *hs_v1 = nullptr, *hs_v2 = nullptr, *hs_v3 = nullptr;
   double* trpart = nullptr;
 
@@ -401,5 +440,46 @@ sdp_status pcg_impl(sdp_problem* h, const double* r, double* y, double rtol, int
                     int* iters, double* relres);
 // ipm.cu
 sdp_status ipm_alloc(sdp_problem* h);
+// Batched PCG pieces (one launch for all problems of a batch; block offsets per problem)
+int batch_blocks_assemble(int nnzV);
+int batch_blocks_spmm(int n);
+int batch_blocks_sddmm(int m);
+int batch_blocks_vec(int m);
+int batch_blocks_hat_u(int n);
+int batch_blocks_tail(int m);
+int batch_blocks_fwdP(int np);
+int batch_blocks_warp_rows(int rows);
+int batch_blocks_outR(int Rk);
+void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm, const int* off_spmm,
+                         const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax);
+void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb);
+void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
+void batch_launch_any(cudaStream_t st, const BDesc* desc, int N, cudaGraphConditionalHandle cond);
+void batch_launch_hat_u(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
+void batch_launch_tail(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
+void batch_launch_core_solve(cudaStream_t st, const BDesc* desc, int N, const int* off_fwdP, int nb_fwdP,
+                             const int* off_fwdR, int nb_fwdR, const int* off_gemv, int nb_gemv,
+                             const int* off_outR, int nb_outR, const int* off_bwdP, int nb_bwdP);
+// Restarted PCG as a state machine (pcg.cu), shared by single solves and batches
+struct PcgSweeps {
+  const double* r = nullptr;
+  double* y = nullptr;
+  double rtol = 0, inner_fp64 = 0, inner_lp = 0, tr = 1, nr0sq = 0;
+  int maxit = 0, prec = 0, sweeps = 1, sweep = 0, total = 0, budget = 0;
+  bool finished = false, graph = false;
+  sdp_status result = SDP_ERR_MAXIT;
+};
+sdp_status pcg_sweeps_init(sdp_problem* h, PcgSweeps* S, const double* r, double* y, double rtol, int maxit,
+                           int prec);
+sdp_status pcg_sweep_begin(sdp_problem* h, PcgSweeps* S, bool graph, bool* run);
+sdp_status pcg_sweep_end(sdp_problem* h, PcgSweeps* S);
+// One IPM iteration split around its two Newton solves (H dy = h->rhs into h->dy)
+struct IpmStepState {
+  sdp_ipm_info inf{};
+  double mu = 0, xs = 0;
+};
+sdp_status ipm_phase_a(sdp_problem* h, IpmStepState* s, bool* done);
+sdp_status ipm_phase_b(sdp_problem* h, IpmStepState* s, int pcg_its, double pcg_rr);
+sdp_status ipm_phase_c(sdp_problem* h, IpmStepState* s, int pcg_its, double pcg_rr);
 sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info);
 }  // namespace sdpgb

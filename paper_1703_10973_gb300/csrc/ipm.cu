@@ -159,14 +159,15 @@ static sdp_status max_step(sdp_problem* h, const double* Lf, const double* Linv,
   return SDP_OK;
 }
 
-// dy from H dy = rhs0 - A(Rc); then dS, dX.  Returns PCG stats.
-static sdp_status newton(sdp_problem* h, const double* rhs0, int* its, double* relres) {
-  cudaStream_t st = h->stream;
-  const int n = h->n, m = h->m;
-  const size_t nn = (size_t)n * n;
+// Newton system (eq. hesseqn2): rhs = rhs0 - A(Rc), then dy from H dy = rhs,
+// then dS = Rd - A^T dy and dX = Rc - W dS W.
+static void newton_rhs(sdp_problem* h, const double* rhs0) {
   op_A_dense(h, h->Rc, h->rhs, -1.0, rhs0, 1.0);
-  sdp_status s = pcg_impl(h, h->rhs, h->dy, h->prm.pcg_rtol, h->prm.pcg_maxit, h->prm.prec, its, relres);
-  if (s != SDP_OK && s != SDP_ERR_MAXIT) return s;
+}
+static sdp_status newton_post(sdp_problem* h) {
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  const size_t nn = (size_t)n * n;
   // dS = Rd - A^T dy
   SDP_CK(h, cudaMemcpyAsync(h->dS, h->Rd, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
   assemble_V(h, h->dy, nullptr, h->Vval);
@@ -176,7 +177,6 @@ static sdp_status newton(sdp_problem* h, const double* rhs0, int* its, double* r
   gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->M2, n);
   axpby(st, nn, 1.0, h->Rc, -1.0, h->M2, h->dX);
   symmetrize_avg(st, n, h->dX, n);
-  (void)m;
   return SDP_OK;
 }
 
@@ -367,13 +367,21 @@ static sdp_status update_checked(sdp_problem* h, double* X, const double* dX, do
   return SDP_ERR_NOT_PD;
 }
 
-sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
+// One IPM iteration in three phases around the two Newton solves, so that a
+// batch can solve the Newton systems of many problems together (batch.cu):
+//   A: residuals, stopping test, NT scaling, preconditioner, predictor rhs
+//   (solve)  B: predictor direction, step lengths, centering, corrector rhs
+//   (solve)  C: corrector direction, step lengths, checked update
+// Phase A sets *done when the iterate already meets the tolerances.
+sdp_status ipm_phase_a(sdp_problem* h, IpmStepState* s, bool* done) {
   SDP_TRY(ipm_alloc(h));
   cudaStream_t st = h->stream;
   const int n = h->n, m = h->m;
   const size_t nn = (size_t)n * n;
   double* sc = h->scal;
-  sdp_ipm_info inf{};
+  *done = false;
+  s->inf = sdp_ipm_info{};
+  sdp_ipm_info& inf = s->inf;
   inf.iter = h->iter;
 
   // ---- residuals and scalars
@@ -391,6 +399,8 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   SDP_CK(h, cudaStreamSynchronize(st));
   const double cx = v[2], by = v[3], xs = v[4];
   const double mu = xs / n;
+  s->mu = mu;
+  s->xs = xs;
   inf.mu = mu;
   inf.obj_p = cx;
   inf.obj_d = by;
@@ -399,12 +409,11 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   inf.dinf = std::sqrt(v[1]) / (1.0 + h->normC);
   if (!std::isfinite(cx) || !std::isfinite(by) || !std::isfinite(xs)) {
     h->last_error = "ipm_step: non-finite iterate";
-    if (info) *info = inf;
     return SDP_ERR_NUMERIC;
   }
   if (inf.relgap <= h->prm.gap_tol && inf.pinf <= h->prm.infeas_tol && inf.dinf <= h->prm.infeas_tol) {
     inf.converged = 1;
-    if (info) *info = inf;
+    *done = true;
     return SDP_OK;
   }
 
@@ -439,13 +448,21 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
     op_A_dense(h, h->M3, h->Rp, 1.0, h->Rp, 1.0);   // Rp <- Rp + A(W Rd W)
   }
 
-  // ---- predictor
+  // ---- predictor right-hand side
   axpby(st, nn, -1.0, h->X, 0.0, nullptr, h->Rc);
-  int its = 0;
-  double rr = 0.0;
-  SDP_TRY(newton(h, h->Rp, &its, &rr));
+  newton_rhs(h, h->Rp);
+  return SDP_OK;
+}
+
+sdp_status ipm_phase_b(sdp_problem* h, IpmStepState* s, int its, double rr) {
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  const size_t nn = (size_t)n * n;
+  double* sc = h->scal;
+  sdp_ipm_info& inf = s->inf;
   inf.pcg_iters_pred = its;
   inf.pcg_relres_pred = rr;
+  SDP_TRY(newton_post(h));
   double ap = 0.0, ad = 0.0;
   if (h->lz_work) SDP_TRY(ensure_linv(h));
   SDP_TRY(max_step(h, h->L, h->LinvX, h->LinvXT, h->dX, &ap));
@@ -458,16 +475,24 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   double w3[3];
   SDP_CK(h, cudaMemcpyAsync(w3, sc + R_XDS, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   SDP_CK(h, cudaStreamSynchronize(st));
-  const double mu_aff = (xs + ad * w3[0] + ap * w3[1] + ap * ad * w3[2]) / n;
-  const double ratio = std::min(1.0, std::max(0.0, mu_aff / mu));
+  const double mu_aff = (s->xs + ad * w3[0] + ap * w3[1] + ap * ad * w3[2]) / n;
+  const double ratio = std::min(1.0, std::max(0.0, mu_aff / s->mu));
   const double sigma = ratio * ratio * ratio;
   inf.sigma = sigma;
+  // ---- corrector right-hand side
+  axpby(st, nn, sigma * s->mu, h->Sinv, -1.0, h->X, h->Rc);
+  newton_rhs(h, h->Rp);
+  return SDP_OK;
+}
 
-  // ---- corrector
-  axpby(st, nn, sigma * mu, h->Sinv, -1.0, h->X, h->Rc);
-  SDP_TRY(newton(h, h->Rp, &its, &rr));
+sdp_status ipm_phase_c(sdp_problem* h, IpmStepState* s, int its, double rr) {
+  cudaStream_t st = h->stream;
+  const int m = h->m;
+  sdp_ipm_info& inf = s->inf;
   inf.pcg_iters_corr = its;
   inf.pcg_relres_corr = rr;
+  SDP_TRY(newton_post(h));
+  double ap = 0.0, ad = 0.0;
   SDP_TRY(max_step(h, h->L, h->LinvX, h->LinvXT, h->dX, &ap));
   SDP_TRY(max_step(h, h->Rs, h->LinvS, h->LinvST, h->dS, &ad));
   ap = std::min(1.0, h->prm.step_frac * ap);
@@ -488,10 +513,30 @@ sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
   h->iter++;
   if (h->prm.verbose)
     fprintf(stderr, "ipm %3d mu %.3e gap %.3e pinf %.3e dinf %.3e ap %.3f ad %.3f sig %.3e pcg %d/%d rel %.1e/%.1e\n",
-            inf.iter, inf.mu, inf.relgap, inf.pinf, inf.dinf, ap, ad, sigma, inf.pcg_iters_pred,
+            inf.iter, inf.mu, inf.relgap, inf.pinf, inf.dinf, ap, ad, inf.sigma, inf.pcg_iters_pred,
             inf.pcg_iters_corr, inf.pcg_relres_pred, inf.pcg_relres_corr);
-  if (info) *info = inf;
   return SDP_OK;
+}
+
+static sdp_status newton_solve(sdp_problem* h, int* its, double* rr) {
+  sdp_status s = pcg_impl(h, h->rhs, h->dy, h->prm.pcg_rtol, h->prm.pcg_maxit, h->prm.prec, its, rr);
+  return (s == SDP_OK || s == SDP_ERR_MAXIT) ? SDP_OK : s;
+}
+
+sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info) {
+  IpmStepState s;
+  bool done = false;
+  sdp_status st = ipm_phase_a(h, &s, &done);
+  if (st == SDP_OK && !done) {
+    int its = 0;
+    double rr = 0.0;
+    st = newton_solve(h, &its, &rr);
+    if (st == SDP_OK) st = ipm_phase_b(h, &s, its, rr);
+    if (st == SDP_OK) st = newton_solve(h, &its, &rr);
+    if (st == SDP_OK) st = ipm_phase_c(h, &s, its, rr);
+  }
+  if (info) *info = s.inf;
+  return st;
 }
 
 }  // namespace sdpgb

@@ -45,10 +45,10 @@ __device__ __forceinline__ float wsum_f(float v) {
 // ---------------------------------------------------------------------------
 // K0: V values from v (gather form, no atomics)
 // ---------------------------------------------------------------------------
-__global__ void k_assemble(int nnzV, const int* __restrict__ sptr, const int* __restrict__ scon,
-                           const double* __restrict__ scoef, const double* __restrict__ v,
-                           const double* __restrict__ scale, double* __restrict__ Vval) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void assemble_body(int s, int nnzV, const int* __restrict__ sptr,
+                                              const int* __restrict__ scon, const double* __restrict__ scoef,
+                                              const double* __restrict__ v, const double* __restrict__ scale,
+                                              double* __restrict__ Vval) {
   if (s >= nnzV) return;
   double acc = 0.0;
   for (int c = sptr[s]; c < sptr[s + 1]; ++c) {
@@ -57,6 +57,11 @@ __global__ void k_assemble(int nnzV, const int* __restrict__ sptr, const int* __
     acc = fma(scoef[c] * f, v[k], acc);
   }
   Vval[s] = acc;
+}
+__global__ void k_assemble(int nnzV, const int* __restrict__ sptr, const int* __restrict__ scon,
+                           const double* __restrict__ scoef, const double* __restrict__ v,
+                           const double* __restrict__ scale, double* __restrict__ Vval) {
+  assemble_body(blockIdx.x * blockDim.x + threadIdx.x, nnzV, sptr, scon, scoef, v, scale, Vval);
 }
 
 void assemble_V(sdp_problem* h, const double* v, const double* scale, double* Vval) {
@@ -68,12 +73,10 @@ void assemble_V(sdp_problem* h, const double* v, const double* scale, double* Vv
 // K1: T = W V, R rows of W per CTA staged in shared memory
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(256) k_spmm_wv_f64(int n, const int* __restrict__ rowptr,
-                                                     const int* __restrict__ colidx,
-                                                     const double* __restrict__ Vval,
-                                                     const double* __restrict__ W, double* __restrict__ T) {
-  extern __shared__ double wsh[];  // R x n
-  const int r0 = blockIdx.x * R;
+__device__ __forceinline__ void spmm_f64_body(int blk, int n, const int* __restrict__ rowptr,
+                                              const int* __restrict__ colidx, const double* __restrict__ Vval,
+                                              const double* __restrict__ W, double* __restrict__ T, double* wsh) {
+  const int r0 = blk * R;
   for (int t = threadIdx.x; t < R * n; t += blockDim.x) {
     const int rr = t / n, c = t % n;
     wsh[t] = (r0 + rr < n) ? W[(size_t)(r0 + rr) * n + c] : 0.0;
@@ -94,6 +97,14 @@ __global__ void __launch_bounds__(256) k_spmm_wv_f64(int n, const int* __restric
     for (int rr = 0; rr < R; ++rr)
       if (r0 + rr < n) T[(size_t)(r0 + rr) * n + l] = acc[rr];
   }
+}
+template <int R>
+__global__ void __launch_bounds__(256) k_spmm_wv_f64(int n, const int* __restrict__ rowptr,
+                                                     const int* __restrict__ colidx,
+                                                     const double* __restrict__ Vval,
+                                                     const double* __restrict__ W, double* __restrict__ T) {
+  extern __shared__ double wsh[];  // R x n
+  spmm_f64_body<R>(blockIdx.x, n, rowptr, colidx, Vval, W, T, wsh);
 }
 
 template <typename TW, int R>
@@ -130,14 +141,13 @@ __global__ void __launch_bounds__(256) k_spmm_wv_lp(int n, const int* __restrict
 // ---------------------------------------------------------------------------
 // With dv != nullptr the kernel also forms dv . Hv (one deterministic grid
 // reduction into *dout; PCG's p . Hp), first moving *pro_src to *pro_dst.
-__global__ void __launch_bounds__(256) k_sddmm_f64(int n, int m, const int* __restrict__ eptr,
-                                                   const int* __restrict__ ep, const int* __restrict__ eq,
-                                                   const double* __restrict__ ecoef,
-                                                   const double* __restrict__ W, const double* __restrict__ T,
-                                                   double* __restrict__ Hv, const double* __restrict__ dv,
-                                                   double* dpart, unsigned int* ticket, double* dout,
-                                                   double* pro_dst, const double* pro_src) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+__device__ __forceinline__ void sddmm_f64_body(int lb, int nb, int n, int m, const int* __restrict__ eptr,
+                                               const int* __restrict__ ep, const int* __restrict__ eq,
+                                               const double* __restrict__ ecoef, const double* __restrict__ W,
+                                               const double* __restrict__ T, double* __restrict__ Hv,
+                                               const double* __restrict__ dv, double* dpart, unsigned int* ticket,
+                                               double* dout, double* pro_dst, const double* pro_src) {
+  const int i = (lb * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   double acc = 0.0;
   if (i < m) {
     for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
@@ -153,11 +163,59 @@ __global__ void __launch_bounds__(256) k_sddmm_f64(int n, int m, const int* __re
   if (dv) {
     const double c = (i < m && lane == 0) ? dv[i] * acc : 0.0;
     double tot;
-    if (lb_reduce(c, dpart, ticket, &tot)) {
+    if (lb_reduce(c, dpart, ticket, &tot, lb, nb)) {
       if (pro_dst) *pro_dst = *pro_src;
       *dout = tot;
     }
   }
+}
+__global__ void __launch_bounds__(256) k_sddmm_f64(int n, int m, const int* __restrict__ eptr,
+                                                   const int* __restrict__ ep, const int* __restrict__ eq,
+                                                   const double* __restrict__ ecoef,
+                                                   const double* __restrict__ W, const double* __restrict__ T,
+                                                   double* __restrict__ Hv, const double* __restrict__ dv,
+                                                   double* dpart, unsigned int* ticket, double* dout,
+                                                   double* pro_dst, const double* pro_src) {
+  sddmm_f64_body(blockIdx.x, gridDim.x, n, m, eptr, ep, eq, ecoef, W, T, Hv, dv, dpart, ticket, dout, pro_dst,
+                 pro_src);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms (one launch for every problem of a batch; see batch.cu)
+// ---------------------------------------------------------------------------
+constexpr int BATCH_SPMM_R = 4;
+__global__ void kb_assemble(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active) return;
+  const int lb = blockIdx.x - off[i];
+  assemble_body(lb * blockDim.x + threadIdx.x, D.nnzV, D.sptr, D.scon, D.scoef, D.pp, nullptr, D.Vval);
+}
+__global__ void __launch_bounds__(256) kb_spmm(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  extern __shared__ double wsh[];
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active) return;
+  spmm_f64_body<BATCH_SPMM_R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W, D.T, wsh);
+}
+__global__ void __launch_bounds__(256) kb_sddmm(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active) return;
+  sddmm_f64_body(blockIdx.x - off[i], off[i + 1] - off[i], D.n, D.m, D.eptr, D.ep, D.eq, D.ecoef, D.W, D.T, D.pq,
+                 D.pp, D.part, D.ticket, D.scal + S_PQ, D.scal + S_RZ, D.scal + S_RZN);
+}
+int batch_blocks_assemble(int nnzV) { return (int)cdiv(nnzV, 256); }
+int batch_blocks_spmm(int n) { return (int)cdiv(n, BATCH_SPMM_R); }
+int batch_blocks_sddmm(int m) { return (int)cdiv((size_t)m * 32, 256); }
+void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm, const int* off_spmm,
+                         const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax) {
+  const size_t smem = (size_t)BATCH_SPMM_R * nmax * sizeof(double);
+  allow_max_smem((const void*)kb_spmm);
+  count_launch(3);
+  kb_assemble<<<nb_asm, 256, 0, st>>>(desc, off_asm, N);
+  kb_spmm<<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N);
+  kb_sddmm<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
 }
 
 template <typename TW>
@@ -197,7 +255,7 @@ __global__ void __launch_bounds__(256) k_sddmm_lp(int n, int m, const int* __res
   if (dv) {
     const double c = (i < m && lane == 0) ? dv[i] * hv : 0.0;
     double tot;
-    if (lb_reduce(c, dpart, ticket, &tot)) {
+    if (lb_reduce(c, dpart, ticket, &tot, blockIdx.x, gridDim.x)) {
       if (pro_dst) *pro_dst = *pro_src;
       *dout = tot;
     }

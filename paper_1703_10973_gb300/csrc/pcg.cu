@@ -18,7 +18,6 @@ namespace sdpgb {
 
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
-enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6, S_IT = 7, S_MAXIT = 8, S_BRK = 9, S_GO = 10 };
 
 // A breakdown (p.q or r.z not positive and finite: rounding has made the
 // preconditioned operator indefinite in some direction) leaves x and r at the
@@ -26,26 +25,32 @@ enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6
 // solve then continues from the true residual.
 
 // p = z + beta p  with beta = rz_new / rz
-__global__ void k_pcg_p(int m, double* __restrict__ p, const double* __restrict__ z, double* scal) {
+__device__ __forceinline__ void pcg_p_body(int lb, int nb, int m, double* __restrict__ p,
+                                           const double* __restrict__ z, double* scal) {
+  if (scal[S_GO] == 0.0) return;   // the loop has stopped: r may be exactly zero
   const double rzn = scal[S_RZN], rz = scal[S_RZ];
   if (!(rzn > 0.0 && isfinite(rzn) && rz > 0.0)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_BRK] = 1.0;
+    if (lb == 0 && threadIdx.x == 0) scal[S_BRK] = 1.0;
     return;
   }
   const double beta = rzn / rz;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) p[i] = fma(beta, p[i], z[i]);
+  for (int i = lb * blockDim.x + threadIdx.x; i < m; i += nb * blockDim.x) p[i] = fma(beta, p[i], z[i]);
+}
+__global__ void k_pcg_p(int m, double* __restrict__ p, const double* __restrict__ z, double* scal) {
+  pcg_p_body(blockIdx.x, gridDim.x, m, p, z, scal);
 }
 
 // x += a p;  r -= a q  (a = rz / pq), ||r||^2, iteration count and the loop
 // condition, in one kernel (the last block to finish reduces and decides).
-__global__ void k_pcg_xr_check(int m, double* __restrict__ x, double* __restrict__ r,
-                               const double* __restrict__ p, const double* __restrict__ q, double* scal,
-                               double* part, unsigned int* ticket, cudaGraphConditionalHandle cond, int use_cond) {
+// Returns true in the deciding thread when the loop must go on.
+__device__ __forceinline__ bool pcg_xr_body(int lb, int nb, int m, double* __restrict__ x, double* __restrict__ r,
+                                            const double* __restrict__ p, const double* __restrict__ q,
+                                            double* scal, double* part, unsigned int* ticket, bool* decided) {
   const double pq = scal[S_PQ], rz = scal[S_RZ];
   const bool ok = pq > 0.0 && rz > 0.0 && isfinite(pq) && isfinite(rz);
   const double a = ok ? rz / pq : 0.0;
   double rr = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+  for (int i = lb * blockDim.x + threadIdx.x; i < m; i += nb * blockDim.x) {
     double ri = r[i];
     if (ok) {
       x[i] = fma(a, p[i], x[i]);
@@ -55,15 +60,65 @@ __global__ void k_pcg_xr_check(int m, double* __restrict__ x, double* __restrict
     rr = fma(ri, ri, rr);
   }
   double tot;
-  if (lb_reduce(rr, part, ticket, &tot)) {
+  *decided = false;
+  if (lb_reduce(rr, part, ticket, &tot, lb, nb)) {
     scal[S_RR] = tot;
     const double it = scal[S_IT] + 1.0;
     scal[S_IT] = it;
     if (!ok) scal[S_BRK] = 1.0;
     const bool go = ok && (tot > scal[S_TOL2]) && (it < scal[S_MAXIT]) && isfinite(tot) && scal[S_BRK] == 0.0;
     scal[S_GO] = go ? 1.0 : 0.0;
-    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+    *decided = true;
+    return go;
   }
+  return false;
+}
+__global__ void k_pcg_xr_check(int m, double* __restrict__ x, double* __restrict__ r,
+                               const double* __restrict__ p, const double* __restrict__ q, double* scal,
+                               double* part, unsigned int* ticket, cudaGraphConditionalHandle cond, int use_cond) {
+  bool decided = false;
+  const bool go = pcg_xr_body(blockIdx.x, gridDim.x, m, x, r, p, q, scal, part, ticket, &decided);
+  if (decided && use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
+// Batched forms: the problems whose loop stops leave the batch's active set;
+// the batch loop goes on while any problem is active.
+__global__ void kb_pcg_xr(BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  BDesc& D = desc[i];
+  if (!D.active) return;
+  bool decided = false;
+  const bool go = pcg_xr_body(blockIdx.x - off[i], off[i + 1] - off[i], D.m, D.px, D.pr, D.pp, D.pq, D.scal,
+                              D.part, D.ticket, &decided);
+  if (decided && !go) D.active = 0;
+}
+__global__ void kb_pcg_p(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active) return;
+  pcg_p_body(blockIdx.x - off[i], off[i + 1] - off[i], D.m, D.pp, D.pz, D.scal);
+}
+__global__ void kb_any_active(const BDesc* __restrict__ desc, int N, cudaGraphConditionalHandle cond) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+    if (desc[i].active) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
+}
+int batch_blocks_vec(int m) { return (int)std::min(cdiv(m, 256), 2048u); }
+void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb) {
+  count_launch();
+  kb_pcg_xr<<<nb, 256, 0, st>>>(desc, off, N);
+}
+void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb) {
+  count_launch();
+  kb_pcg_p<<<nb, 256, 0, st>>>(desc, off, N);
+}
+void batch_launch_any(cudaStream_t st, const BDesc* desc, int N, cudaGraphConditionalHandle cond) {
+  count_launch();
+  kb_any_active<<<1, 256, 0, st>>>(desc, N, cond);
 }
 
 __global__ void k_pcg_init(double* scal, double rtol, int maxit) {
@@ -72,6 +127,7 @@ __global__ void k_pcg_init(double* scal, double rtol, int maxit) {
   scal[S_IT] = 0.0;
   scal[S_MAXIT] = (double)maxit;
   scal[S_BRK] = 0.0;
+  scal[S_GO] = 1.0;
 }
 
 static sdp_status pcg_alloc(sdp_problem* h) {
@@ -169,51 +225,59 @@ static double read_scalar(sdp_problem* h, const double* dev) {
   return v;
 }
 
-// Plain PCG from x = 0 in precision prec; x receives the iterate.  *rel is the
-// recursive relative residual at exit.
-static sdp_status pcg_core(sdp_problem* h, const double* rhs, double* x, double rtol, int maxit, int prec,
-                           int* iters, double* rel, bool* brk) {
+// Start of one PCG run from x = 0 on rhs (precision prec): r = rhs, z = M r,
+// p = z, scalars initialised on the device.  *nr0sq = ||rhs||^2 (zero: nothing
+// to run).  The loop itself is run by the caller (pcg_run, or a batch).
+static sdp_status pcg_start(sdp_problem* h, const double* rhs, double rtol, int maxit, int prec, bool graph,
+                            double* nr0sq) {
   cudaStream_t st = h->stream;
   const int m = h->m;
   double* scal = h->scal;
-  const bool use_graph = h->prm.pcg_graph != 0;
-  if (use_graph) SDP_TRY(pcg_graph(h, prec));
+  if (graph) SDP_TRY(pcg_graph(h, prec));
   else SDP_TRY(ensure_lowprec_W(h, prec));
   SDP_CK(h, cudaMemcpyAsync(h->pr, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   SDP_CK(h, cudaMemsetAsync(h->px, 0, m * sizeof(double), st));
   dot(st, m, h->pr, h->pr, scal + S_NR0, h->part);
-  const double nr0sq = read_scalar(h, scal + S_NR0);
-  if (!std::isfinite(nr0sq)) {
+  *nr0sq = read_scalar(h, scal + S_NR0);
+  if (!std::isfinite(*nr0sq)) {
     h->last_error = "pcg: non-finite right-hand side";
     return SDP_ERR_NUMERIC;
   }
-  if (nr0sq == 0.0) {
-    SDP_CK(h, cudaMemsetAsync(x, 0, m * sizeof(double), st));
-    *iters = 0;
-    *rel = 0.0;
-    if (brk) *brk = false;
-    return SDP_OK;
-  }
+  if (*nr0sq == 0.0) return SDP_OK;
   SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec, scal + S_RZ));
   SDP_CK(h, cudaMemcpyAsync(h->pp, h->pz, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   count_launch();
   k_pcg_init<<<1, 1, 0, st>>>(scal, rtol, maxit);
-  double v[11];
-  if (use_graph) {
+  return SDP_OK;
+}
+
+// The loop on the handle's own stream: the device-side graph, or the host loop.
+static sdp_status pcg_run(sdp_problem* h, int prec, bool graph) {
+  cudaStream_t st = h->stream;
+  if (graph) {
     SDP_CK(h, cudaGraphLaunch(h->pcg_exec, st));
-    SDP_CK(h, cudaMemcpyAsync(v, scal, 11 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    SDP_CK(h, cudaStreamSynchronize(st));
-  } else {
-    // the same body, launched from the host one iteration at a time
-    do {
-      SDP_TRY(pcg_body(h, prec, cudaGraphConditionalHandle{}, false));
-      SDP_CK(h, cudaMemcpyAsync(v, scal, 11 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      SDP_CK(h, cudaStreamSynchronize(st));
-    } while (v[S_GO] != 0.0);
+    return SDP_OK;
   }
+  double go = 1.0;
+  while (go != 0.0) {
+    SDP_TRY(pcg_body(h, prec, cudaGraphConditionalHandle{}, false));
+    SDP_CK(h, cudaMemcpyAsync(&go, h->scal + S_GO, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SDP_CK(h, cudaStreamSynchronize(st));
+  }
+  return SDP_OK;
+}
+
+// End of a run: x = the iterate, iteration count, recursive relative residual.
+static sdp_status pcg_finish(sdp_problem* h, double* x, double nr0sq, bool graph, int* iters, double* rel,
+                             bool* brk) {
+  cudaStream_t st = h->stream;
+  const int m = h->m;
+  double v[11];
+  SDP_CK(h, cudaMemcpyAsync(v, h->scal, 11 * sizeof(double), cudaMemcpyDeviceToHost, st));
   SDP_CK(h, cudaMemcpyAsync(x, h->px, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  SDP_CK(h, cudaStreamSynchronize(st));
   const int its = (int)v[S_IT];
-  if (use_graph) g_launches.fetch_add((int64_t)its * h->pcg_body_launches);
+  if (graph) g_launches.fetch_add((int64_t)its * h->pcg_body_launches);
   const double rr = v[S_RR];
   *iters = its;
   *rel = std::sqrt(rr / nr0sq);
@@ -240,72 +304,123 @@ static sdp_status true_residual(sdp_problem* h, const double* r, const double* y
   return SDP_OK;
 }
 
+// Restarted PCG = iterative refinement on the true FP64 residual.  Each sweep
+// runs PCG from zero on the current residual to the inner tolerance; restarting
+// discards the Krylov recurrences that rounding in the Woodbury apply (about
+// kappa(Ht) eps, Section IV) and in a reduced-precision matvec corrupts, so
+// the true residual keeps falling where one long PCG run stagnates.  The sweep
+// logic lives in PcgSweeps so that a batch runs exactly the same rules.
+sdp_status pcg_sweeps_init(sdp_problem* h, PcgSweeps* S, const double* r, double* y, double rtol, int maxit,
+                           int prec) {
+  SDP_TRY(pcg_alloc(h));
+  if (!h->pc_valid) SDP_TRY(precond_build_impl(h));
+  cudaStream_t st = h->stream;
+  const int m = h->m;
+  *S = PcgSweeps{};
+  S->r = r;
+  S->y = y;
+  S->rtol = rtol;
+  S->maxit = maxit;
+  S->prec = prec;
+  S->sweeps = std::max(1, h->prm.refine_maxit);
+  S->inner_fp64 = std::max(h->prm.inner_rtol, rtol);
+  S->inner_lp = std::max(h->prm.inner_rtol_lp, rtol);
+  S->tr = 1.0;
+  S->result = SDP_ERR_MAXIT;
+  SDP_CK(h, cudaMemsetAsync(y, 0, m * sizeof(double), st));
+  SDP_CK(h, cudaMemcpyAsync(h->pbest, r, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return SDP_OK;
+}
+
+// Starts the next sweep; *run = false when the solve is over, or when this
+// sweep has nothing to iterate (it is then finished here).
+sdp_status pcg_sweep_begin(sdp_problem* h, PcgSweeps* S, bool graph, bool* run) {
+  *run = false;
+  if (S->finished || S->sweep >= S->sweeps) {
+    S->finished = true;
+    return SDP_OK;
+  }
+  S->budget = std::max(1, std::min(S->maxit - S->total, 500));
+  S->graph = graph;
+  SDP_TRY(pcg_start(h, h->pbest, S->prec == SDP_FP64 ? S->inner_fp64 : S->inner_lp, S->budget, S->prec, graph,
+                    &S->nr0sq));
+  if (S->nr0sq == 0.0) {
+    S->finished = true;       // zero residual: y is exact already
+    S->result = SDP_OK;
+    S->tr = 0.0;
+    return SDP_OK;
+  }
+  *run = true;
+  return SDP_OK;
+}
+
+// Ends the running sweep: adds the correction and decides what comes next.
+sdp_status pcg_sweep_end(sdp_problem* h, PcgSweeps* S) {
+  cudaStream_t st = h->stream;
+  const int m = h->m;
+  int it = 0;
+  double rr = 0.0;
+  bool brk = false;
+  sdp_status s = pcg_finish(h, h->pcorr, S->nr0sq, S->graph, &it, &rr, &brk);
+  S->sweep++;
+  S->total += it;
+  if (s != SDP_OK && s != SDP_ERR_MAXIT) return s;
+  if (brk && it <= 1 && s != SDP_OK && S->prec == SDP_FP64) {   // breakdown before any progress
+    S->finished = true;
+    return SDP_OK;
+  }
+  const double tr_prev = S->tr;
+  if (it > 0) axpby(st, m, 1.0, S->y, 1.0, h->pcorr, S->y);
+  SDP_TRY(true_residual(h, S->r, S->y, h->pbest, &S->tr));
+  if (!(S->tr < tr_prev)) {
+    // the sweep did not reduce the FP64 residual: drop its correction; a
+    // reduced-precision inner solve hands over to FP64, an FP64 one stops
+    if (it > 0) axpby(st, m, 1.0, S->y, -1.0, h->pcorr, S->y);
+    SDP_TRY(true_residual(h, S->r, S->y, h->pbest, &S->tr));
+    if (S->prec == SDP_FP64) {
+      S->finished = true;
+    } else {
+      S->prec = SDP_FP64;
+      h->pcg_prec_fallbacks++;
+    }
+    return SDP_OK;
+  }
+  if (!std::isfinite(S->tr)) {
+    h->last_error = "pcg: non-finite true residual";
+    return SDP_ERR_NUMERIC;
+  }
+  if (S->tr <= S->rtol) {
+    S->result = SDP_OK;
+    S->finished = true;
+  } else if (S->total >= S->maxit) {
+    S->finished = true;
+  }
+  return SDP_OK;
+}
+
 static sdp_status pcg_impl_(sdp_problem* h, const double* r, double* y, double rtol, int maxit, int prec,
-                            int* iters, double* relres);
+                            int* iters, double* relres) {
+  PcgSweeps S;
+  SDP_TRY(pcg_sweeps_init(h, &S, r, y, rtol, maxit, prec));
+  const bool graph = h->prm.pcg_graph != 0;
+  for (;;) {
+    bool run = false;
+    SDP_TRY(pcg_sweep_begin(h, &S, graph, &run));
+    if (!run) break;
+    SDP_TRY(pcg_run(h, S.prec, graph));
+    SDP_TRY(pcg_sweep_end(h, &S));
+  }
+  if (iters) *iters = S.total;
+  if (relres) *relres = S.tr;
+  return S.result;
+}
+
 sdp_status pcg_impl(sdp_problem* h, const double* r, double* y, double rtol, int maxit, int prec, int* iters,
                     double* relres) {
   ktimer_begin(h->stream, "pcg");
   sdp_status s = pcg_impl_(h, r, y, rtol, maxit, prec, iters, relres);
   ktimer_end(h->stream, "pcg", 0.0, 0.0);
   return s;
-}
-static sdp_status pcg_impl_(sdp_problem* h, const double* r, double* y, double rtol, int maxit, int prec,
-                            int* iters, double* relres) {
-  SDP_TRY(pcg_alloc(h));
-  if (!h->pc_valid) SDP_TRY(precond_build_impl(h));
-  cudaStream_t st = h->stream;
-  const int m = h->m;
-  // Restarted PCG = iterative refinement on the true FP64 residual.  Each sweep
-  // runs PCG from zero on the current residual to a loose tolerance; restarting
-  // discards the Krylov recurrences that rounding in the Woodbury apply (about
-  // kappa(Ht) eps, Section IV) and in a reduced-precision matvec corrupts, so
-  // the true residual keeps falling where one long PCG run stagnates.
-  SDP_CK(h, cudaMemsetAsync(y, 0, m * sizeof(double), st));
-  double* resid = h->pbest;
-  double* corr = h->pcorr;
-  SDP_CK(h, cudaMemcpyAsync(resid, r, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  double tr = 1.0;
-  int total = 0;
-  sdp_status result = SDP_ERR_MAXIT;
-  const int sweeps = std::max(1, h->prm.refine_maxit);
-  const double inner_fp64 = std::max(h->prm.inner_rtol, rtol);
-  const double inner_lp = std::max(h->prm.inner_rtol_lp, rtol);
-  for (int sweep = 0; sweep < sweeps; ++sweep) {
-    int it = 0;
-    double rr = 0.0;
-    const int budget = std::max(1, std::min(maxit - total, 500));
-    bool brk = false;
-    sdp_status s = pcg_core(h, resid, corr, prec == SDP_FP64 ? inner_fp64 : inner_lp, budget, prec, &it, &rr,
-                            &brk);
-    total += it;
-    if (s != SDP_OK && s != SDP_ERR_MAXIT) return s;
-    if (brk && it <= 1 && prec == SDP_FP64) break;   // breakdown before any progress
-    const double tr_prev = tr;
-    if (it > 0) axpby(st, m, 1.0, y, 1.0, corr, y);
-    SDP_TRY(true_residual(h, r, y, resid, &tr));
-    if (!(tr < tr_prev)) {
-      // the sweep did not reduce the FP64 residual: drop its correction; a
-      // reduced-precision inner solve hands over to FP64, an FP64 one stops
-      if (it > 0) axpby(st, m, 1.0, y, -1.0, corr, y);
-      SDP_TRY(true_residual(h, r, y, resid, &tr));
-      if (prec == SDP_FP64) break;
-      prec = SDP_FP64;
-      h->pcg_prec_fallbacks++;
-      continue;
-    }
-    if (!std::isfinite(tr)) {
-      h->last_error = "pcg: non-finite true residual";
-      return SDP_ERR_NUMERIC;
-    }
-    if (tr <= rtol) {
-      result = SDP_OK;
-      break;
-    }
-    if (total >= maxit) break;
-  }
-  if (iters) *iters = total;
-  if (relres) *relres = tr;
-  return result;
 }
 
 }  // namespace sdpgb

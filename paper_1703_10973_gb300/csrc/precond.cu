@@ -80,12 +80,13 @@ __global__ void k_csr_mm(int rows, const int* __restrict__ rowptr, const int* __
 
 // z_i = (ginv_i / tau^2) (r_i - (UU s)_i),  (UU s)_i = A_i . (ZS U^T); with
 // dout != nullptr also *dout = r . z (one deterministic grid reduction).
-__global__ void k_apply_tail(int m, int k, const int* __restrict__ eptr, const int* __restrict__ ep,
-                             const int* __restrict__ eq, const double* __restrict__ ecoef,
-                             const double* __restrict__ ZS, const double* __restrict__ U,
-                             const double* __restrict__ ginv, const double* __restrict__ r, double inv_tau2,
-                             double* __restrict__ z, double* dpart, unsigned int* ticket, double* dout) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void apply_tail_body(int lb, int nb, int m, int k, const int* __restrict__ eptr,
+                                                const int* __restrict__ ep, const int* __restrict__ eq,
+                                                const double* __restrict__ ecoef, const double* __restrict__ ZS,
+                                                const double* __restrict__ U, const double* __restrict__ ginv,
+                                                const double* __restrict__ r, double inv_tau2, double* __restrict__ z,
+                                                double* dpart, unsigned int* ticket, double* dout) {
+  const int i = lb * blockDim.x + threadIdx.x;
   double rz = 0.0;
   if (i < m) {
     double us = 0.0;
@@ -109,17 +110,25 @@ __global__ void k_apply_tail(int m, int k, const int* __restrict__ eptr, const i
   }
   if (dout) {
     double tot;
-    if (lb_reduce(rz, dpart, ticket, &tot)) *dout = tot;
+    if (lb_reduce(rz, dpart, ticket, &tot, lb, nb)) *dout = tot;
   }
+}
+__global__ void k_apply_tail(int m, int k, const int* __restrict__ eptr, const int* __restrict__ ep,
+                             const int* __restrict__ eq, const double* __restrict__ ecoef,
+                             const double* __restrict__ ZS, const double* __restrict__ U,
+                             const double* __restrict__ ginv, const double* __restrict__ r, double inv_tau2,
+                             double* __restrict__ z, double* dpart, unsigned int* ticket, double* dout) {
+  apply_tail_body(blockIdx.x, gridDim.x, m, k, eptr, ep, eq, ecoef, ZS, U, ginv, r, inv_tau2, z, dpart, ticket,
+                  dout);
 }
 
 // Hhat apply, first product: u[l n + a] = scale * sum_{s in row a} V_s U[col(s)][l]
 // with V = sum_i g_i^{-1} r_i A_i assembled on the fly; one warp per row a.
-__global__ void k_hat_u(int n, int k, const int* __restrict__ rowptr, const int* __restrict__ colidx,
-                        const int* __restrict__ sptr, const int* __restrict__ scon, const double* __restrict__ scoef,
-                        const double* __restrict__ ginv, const double* __restrict__ r, const double* __restrict__ U,
-                        double scale, double* __restrict__ u) {
-  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void hat_u_body(int a, int lane, int n, int k, const int* __restrict__ rowptr,
+                                           const int* __restrict__ colidx, const int* __restrict__ sptr,
+                                           const int* __restrict__ scon, const double* __restrict__ scoef,
+                                           const double* __restrict__ ginv, const double* __restrict__ r,
+                                           const double* __restrict__ U, double scale, double* __restrict__ u) {
   if (a >= n) return;
   double acc[8];
 #pragma unroll
@@ -143,6 +152,40 @@ __global__ void k_hat_u(int n, int k, const int* __restrict__ rowptr, const int*
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) u[(size_t)l * n + a] = scale * t;
   }
+}
+__global__ void k_hat_u(int n, int k, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                        const int* __restrict__ sptr, const int* __restrict__ scon, const double* __restrict__ scoef,
+                        const double* __restrict__ ginv, const double* __restrict__ r, const double* __restrict__ U,
+                        double scale, double* __restrict__ u) {
+  hat_u_body((blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, n, k, rowptr, colidx, sptr, scon,
+             scoef, ginv, r, U, scale, u);
+}
+
+// Batched forms of the Hhat apply ends (the core solve is in schur.cu)
+__global__ void kb_hat_u(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active) return;
+  const int lb = blockIdx.x - off[i];
+  hat_u_body((lb * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, D.n, D.k, D.rowptr, D.colidx, D.sptr, D.scon,
+             D.scoef, D.ginv, D.pr, D.U, D.zscale, D.uvec);
+}
+__global__ void kb_apply_tail(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active) return;
+  apply_tail_body(blockIdx.x - off[i], off[i + 1] - off[i], D.m, D.k, D.eptr, D.ep, D.eq, D.ecoef, D.Bn, D.U,
+                  D.ginv, D.pr, D.inv_tau2, D.pz, D.part, D.ticket, D.scal + S_RZN);
+}
+int batch_blocks_hat_u(int n) { return (int)cdiv((size_t)n * 32, 256); }
+int batch_blocks_tail(int m) { return (int)cdiv(m, 256); }
+void batch_launch_hat_u(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb) {
+  count_launch();
+  kb_hat_u<<<nb, 256, 0, st>>>(desc, off, N);
+}
+void batch_launch_tail(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb) {
+  count_launch();
+  kb_apply_tail<<<nb, 256, 0, st>>>(desc, off, N);
 }
 
 __global__ void k_scale_ginv(int m, const double* __restrict__ ginv, const double* __restrict__ r, double s,

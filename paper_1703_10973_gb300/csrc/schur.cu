@@ -241,9 +241,9 @@ __global__ void __launch_bounds__(256) k_hat_schur_rows(int k, int Rk, const int
 // ---------------------------------------------------------------------------
 // Device: apply pieces (u and the result in the k x n layout u[l n + c])
 // ---------------------------------------------------------------------------
-__global__ void k_hat_fwdP(int np, int n, int k, const int* __restrict__ pverts, const double* __restrict__ D,
-                           const double* __restrict__ u, double* __restrict__ yP) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fwdP_body(int a, int np, int n, int k, const int* __restrict__ pverts,
+                                          const double* __restrict__ D, const double* __restrict__ u,
+                                          double* __restrict__ yP) {
   if (a >= np) return;
   const double* La = D + (size_t)a * k * k;
   const int v = pverts[a];
@@ -255,6 +255,10 @@ __global__ void k_hat_fwdP(int np, int n, int k, const int* __restrict__ pverts,
     yP[(size_t)a * k + i] = x[i];
   }
 }
+__global__ void k_hat_fwdP(int np, int n, int k, const int* __restrict__ pverts, const double* __restrict__ D,
+                           const double* __restrict__ u, double* __restrict__ yP) {
+  fwdP_body(blockIdx.x * blockDim.x + threadIdx.x, np, n, k, pverts, D, u, yP);
+}
 
 __device__ __forceinline__ double hs_warp_sum(double v) {
 #pragma unroll
@@ -264,10 +268,11 @@ __device__ __forceinline__ double hs_warp_sum(double v) {
 
 // tR[r k + l2] = u[l2 n + rverts[r]] - sum over blocks (a, r) of (F^T y_a)[l2];
 // one warp per r, lanes over the blocks
-__global__ void k_hat_fwdR(int nr, int n, int k, const int* __restrict__ rverts, const int* __restrict__ btptr,
-                           const int* __restrict__ btslot, const int* __restrict__ bp, const double* __restrict__ F,
-                           const double* __restrict__ yP, const double* __restrict__ u, double* __restrict__ tR) {
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void fwdR_body(int r, int lane, int nr, int n, int k, const int* __restrict__ rverts,
+                                          const int* __restrict__ btptr, const int* __restrict__ btslot,
+                                          const int* __restrict__ bp, const double* __restrict__ F,
+                                          const double* __restrict__ yP, const double* __restrict__ u,
+                                          double* __restrict__ tR) {
   if (r >= nr) return;
   double acc[KMAX];
 #pragma unroll
@@ -290,13 +295,37 @@ __global__ void k_hat_fwdR(int nr, int n, int k, const int* __restrict__ rverts,
     if (lane == 0) tR[(size_t)r * k + c] = u[(size_t)c * n + rverts[r]] - s;
   }
 }
+__global__ void k_hat_fwdR(int nr, int n, int k, const int* __restrict__ rverts, const int* __restrict__ btptr,
+                           const int* __restrict__ btslot, const int* __restrict__ bp, const double* __restrict__ F,
+                           const double* __restrict__ yP, const double* __restrict__ u, double* __restrict__ tR) {
+  fwdR_body((blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, nr, n, k, rverts, btptr, btslot, bp, F,
+            yP, u, tR);
+}
+
+// y = A x for a triangular A (lower: columns 0..r of row r; upper: r..n-1), one
+// warp per row (the two dense solves with the Schur factor: L_C^{-1} and its
+// transpose, each stored row-major)
+__device__ __forceinline__ void tri_gemv_body(int r, int lane, int n, bool lower, const double* __restrict__ A,
+                                              const double* __restrict__ x, double* __restrict__ y) {
+  if (r >= n) return;
+  const int c0 = lower ? 0 : r, c1 = lower ? r + 1 : n;
+  const double* ar = A + (size_t)r * n;
+  double s = 0.0;
+  for (int c = c0 + lane; c < c1; c += 32) s = fma(ar[c], x[c], s);
+  s = hs_warp_sum(s);
+  if (lane == 0) y[r] = s;
+}
+__global__ void k_tri_gemv(int n, int lower, const double* __restrict__ A, const double* __restrict__ x,
+                           double* __restrict__ y) {
+  tri_gemv_body((blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, n, lower != 0, A, x, y);
+}
 
 // x_a = L_a^{-T}(y_a - F_a x_R); out[pverts[a] k + l] = scale x_a[l]; one warp per a
-__global__ void k_hat_bwdP(int np, int n, int k, const int* __restrict__ pverts, const int* __restrict__ bptr,
-                           const int* __restrict__ bcol, const double* __restrict__ F, const double* __restrict__ D,
-                           const double* __restrict__ yP, const double* __restrict__ xR, double scale,
-                           double* __restrict__ out) {
-  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void bwdP_body(int a, int lane, int np, int k, const int* __restrict__ pverts,
+                                          const int* __restrict__ bptr, const int* __restrict__ bcol,
+                                          const double* __restrict__ F, const double* __restrict__ D,
+                                          const double* __restrict__ yP, const double* __restrict__ xR,
+                                          double scale, double* __restrict__ out) {
   if (a >= np) return;
   double acc[KMAX];
 #pragma unroll
@@ -324,13 +353,81 @@ __global__ void k_hat_bwdP(int np, int n, int k, const int* __restrict__ pverts,
     out[(size_t)v * k + i] = scale * z[i];
   }
 }
+__global__ void k_hat_bwdP(int np, int n, int k, const int* __restrict__ pverts, const int* __restrict__ bptr,
+                           const int* __restrict__ bcol, const double* __restrict__ F, const double* __restrict__ D,
+                           const double* __restrict__ yP, const double* __restrict__ xR, double scale,
+                           double* __restrict__ out) {
+  (void)n;
+  bwdP_body((blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, np, k, pverts, bptr, bcol, F, D, yP, xR,
+            scale, out);
+}
 
-__global__ void k_hat_outR(int nr, int k, const int* __restrict__ rverts, const double* __restrict__ xR,
-                           double scale, double* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void outR_body(int t, int nr, int k, const int* __restrict__ rverts,
+                                          const double* __restrict__ xR, double scale, double* __restrict__ out) {
   if (t >= nr * k) return;
   const int r = t / k, l = t % k;
   out[(size_t)rverts[r] * k + l] = scale * xR[t];
+}
+__global__ void k_hat_outR(int nr, int k, const int* __restrict__ rverts, const double* __restrict__ xR,
+                           double scale, double* __restrict__ out) {
+  outR_body(blockIdx.x * blockDim.x + threadIdx.x, nr, k, rverts, xR, scale, out);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms of the core solve (one launch each for every problem of a batch)
+// ---------------------------------------------------------------------------
+#define HS_BATCH_PROLOGUE                                  \
+  const int inst = batch_find(off, N, blockIdx.x);         \
+  const BDesc& Dd = desc[inst];                            \
+  if (!Dd.active) return;                                  \
+  const int lb = blockIdx.x - off[inst];
+
+__global__ void kb_fwdP(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  HS_BATCH_PROLOGUE
+  fwdP_body(lb * blockDim.x + threadIdx.x, Dd.np, Dd.n, Dd.k, Dd.pverts, Dd.D, Dd.uvec, Dd.yP);
+}
+__global__ void kb_fwdR(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  HS_BATCH_PROLOGUE
+  fwdR_body((lb * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, Dd.nr, Dd.n, Dd.k, Dd.rverts, Dd.btptr,
+            Dd.btslot, Dd.bp, Dd.F, Dd.yP, Dd.uvec, Dd.v1);
+}
+__global__ void kb_gemv_lower(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  HS_BATCH_PROLOGUE
+  tri_gemv_body((lb * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, Dd.Rk, true, Dd.Cinv, Dd.v1, Dd.v2);
+}
+__global__ void kb_gemv_upper(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  HS_BATCH_PROLOGUE
+  tri_gemv_body((lb * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, Dd.Rk, false, Dd.CinvT, Dd.v2, Dd.v1);
+}
+__global__ void kb_outR(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  HS_BATCH_PROLOGUE
+  outR_body(lb * blockDim.x + threadIdx.x, Dd.nr, Dd.k, Dd.rverts, Dd.v1, Dd.zscale, Dd.Bn);
+}
+__global__ void kb_bwdP(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  HS_BATCH_PROLOGUE
+  bwdP_body((lb * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, Dd.np, Dd.k, Dd.pverts, Dd.bptr, Dd.bcol, Dd.F,
+            Dd.D, Dd.yP, Dd.v1, Dd.zscale, Dd.Bn);
+}
+int batch_blocks_fwdP(int np) { return (int)cdiv(np, 128); }
+int batch_blocks_warp_rows(int rows) { return (int)cdiv((size_t)rows * 32, 256); }
+int batch_blocks_outR(int Rk) { return (int)cdiv(Rk, 128); }
+void batch_launch_core_solve(cudaStream_t st, const BDesc* desc, int N, const int* off_fwdP, int nb_fwdP,
+                             const int* off_fwdR, int nb_fwdR, const int* off_gemv, int nb_gemv,
+                             const int* off_outR, int nb_outR, const int* off_bwdP, int nb_bwdP) {
+  count_launch(2);
+  kb_fwdP<<<nb_fwdP, 128, 0, st>>>(desc, off_fwdP, N);
+  kb_fwdR<<<nb_fwdR, 256, 0, st>>>(desc, off_fwdR, N);
+  if (nb_gemv > 0) {
+    count_launch(2);
+    kb_gemv_lower<<<nb_gemv, 256, 0, st>>>(desc, off_gemv, N);
+    kb_gemv_upper<<<nb_gemv, 256, 0, st>>>(desc, off_gemv, N);
+  }
+  if (nb_outR > 0) {
+    count_launch();
+    kb_outR<<<nb_outR, 128, 0, st>>>(desc, off_outR, N);
+  }
+  count_launch();
+  kb_bwdP<<<nb_bwdP, 256, 0, st>>>(desc, off_bwdP, N);
 }
 
 // ---------------------------------------------------------------------------
@@ -344,6 +441,7 @@ sdp_status schur_alloc(sdp_problem* h, int k) {
   SDP_TRY(h->allocT(&h->hs_yP, std::max<size_t>(np * k, 1)));
   SDP_TRY(h->allocT(&h->hs_C, std::max<size_t>(Rk * Rk, 1)));
   SDP_TRY(h->allocT(&h->hs_Cinv, std::max<size_t>(Rk * Rk, 1)));
+  SDP_TRY(h->allocT(&h->hs_CinvT, std::max<size_t>(Rk * Rk, 1)));
   SDP_TRY(h->allocT(&h->hs_v1, std::max<size_t>(Rk, 1)));
   SDP_TRY(h->allocT(&h->hs_v2, std::max<size_t>(Rk, 1)));
   SDP_TRY(h->allocT(&h->hs_v3, std::max<size_t>(Rk, 1)));
@@ -395,6 +493,7 @@ sdp_status schur_build(sdp_problem* h, int k, double tau) {
     fill(st, h->hs_Cinv, (size_t)Rk * Rk, 0.0);
     add_diag(st, Rk, h->hs_Cinv, Rk, 1.0);
     trsm_left_lower_ex(st, false, Rk, Rk, h->hs_C, Rk, h->hs_Cinv, Rk, h->work, true);
+    transpose(st, Rk, Rk, h->hs_Cinv, Rk, h->hs_CinvT, Rk);
   }
   int inf2[2] = {0, 0};
   SDP_CK(h, cudaMemcpyAsync(inf2, h->info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -418,9 +517,10 @@ sdp_status schur_apply(sdp_problem* h, const double* u, double* out, double scal
     count_launch();
     k_hat_fwdR<<<cdiv((size_t)nr * 32, 256), 256, 0, st>>>(nr, n, k, h->hs_rverts, h->hs_btptr, h->hs_btslot,
                                                             h->hs_bp, h->hs_F, h->hs_yP, u, h->hs_v1);
-    // y_R = L_C^{-1} t_R and x_R = L_C^{-T} y_R
-    trmv_lower_ex(st, false, Rk, h->hs_Cinv, Rk, h->hs_v1, h->hs_v2, h->trpart, 1.0, nullptr, 0.0);
-    trmv_lower_ex(st, true, Rk, h->hs_Cinv, Rk, h->hs_v2, h->hs_v1, h->trpart, 1.0, nullptr, 0.0);
+    // y_R = L_C^{-1} t_R and x_R = L_C^{-T} y_R (both inverses stored row-major)
+    count_launch(2);
+    k_tri_gemv<<<cdiv((size_t)Rk * 32, 256), 256, 0, st>>>(Rk, 1, h->hs_Cinv, h->hs_v1, h->hs_v2);
+    k_tri_gemv<<<cdiv((size_t)Rk * 32, 256), 256, 0, st>>>(Rk, 0, h->hs_CinvT, h->hs_v2, h->hs_v1);
     count_launch();
     k_hat_outR<<<cdiv(Rk, 128), 128, 0, st>>>(nr, k, h->hs_rverts, h->hs_v1, scale, out);
     if (np > 0) {
