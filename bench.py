@@ -5,9 +5,12 @@ matrix-completion workload (p, q uniform in [50, 400], r uniform in {1..4},
 m = min(pq/2, ceil(3 r (p+q) ln(p+q))) uniform observations, seeds 4000..4015).
 One step solves all 16 SDPs, each from the interior-point start point to
 relative gap, primal and dual infeasibility <= 1e-6 with every Newton system
-solved by PCG to a 1e-8 true relative residual, on 4 CUDA streams (one host
-thread per stream, one resident problem per instance).  The problem data stay
-in HBM across steps; each solve resets its iterate on the device.
+solved by PCG to a 1e-8 true relative residual.  By default the 16 problems are
+advanced in lockstep (sdp_batch_solve): their dense phases on one stream and
+host thread each, and every PCG iteration of all 16 Newton systems as one
+sequence of batched launches under a CUDA graph.  --batched-launch 0 solves
+them as independent problems on --streams streams.  The problem data stay in
+HBM across steps; each solve resets its iterate on the device.
 
 `--workload C2` runs the single n = 1000, m = 8000, rank-2 instance instead; its
 nuclear-norm optimum has rank about 38, outside the low-rank regime the
@@ -518,8 +521,9 @@ def main():
                     help="kernel class for the roofline object; auto = the one with the most device time")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batched-launch", action="store_true",
-                    help="solve the batch in lockstep with one launch per PCG step for all problems")
+    ap.add_argument("--batched-launch", type=int, default=1, choices=[0, 1],
+                    help="1: solve the batch in lockstep with one launch per PCG step for all problems; "
+                         "0: independent problems on --streams streams")
     ap.add_argument("--pcg-graph", type=int, default=1, choices=[0, 1],
                     help="0: host-driven PCG loop (same kernels; for profilers without conditional-graph support)")
     args = ap.parse_args()
