@@ -37,6 +37,7 @@ import os
 import queue
 import statistics
 import subprocess
+import tempfile
 import sys
 import threading
 import time
@@ -92,7 +93,8 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.environ.get("SDP_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                     f"sdp_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -252,6 +254,7 @@ def run(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     batch = None
+    stage_ms = {}          # batched mode: wall ms per lockstep stage of the last solve
     if args.batched_launch:
         from paper_1703_10973_gb300 import SDPBatch
         bstream = torch.cuda.Stream()
@@ -271,6 +274,7 @@ def run(args):
             res_b = batch.solve(allow_maxit=True)
             torch.cuda.synchronize()
             ms = (time.perf_counter() - t0b) * 1e3
+            stage_ms.update({k: round(v * 1e3, 1) for k, v in batch.stage_seconds().items()})
             return [ms] * len(probs), res_b
         if start_event is not None:
             for st in streams:
@@ -326,6 +330,7 @@ def run(args):
             lat_all += lat
             res_last = res
     launches = probs[0].launch_count() - l0
+    stage_timed = dict(stage_ms)
     total_ms = sum(step_ms)
     if dist is not None:
         total_ms = max_over_ranks(total_ms, dist, "cuda")
@@ -439,7 +444,7 @@ def run(args):
                            "pcg_iters_per_solve_mean": float(np.mean(pcg_iters)),
                            "max_relgap": max(r["relgap"] for r in res_last)},
                 "latency_ms": {"p50": p50, "p99": p99},
-                "roofline": roof, "breakdown_ms_per_step": breakdown, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "stage_ms_per_step": stage_timed or None, "breakdown_ms_per_step": breakdown, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk.summary(),
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)

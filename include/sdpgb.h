@@ -230,8 +230,7 @@ int64_t sdp_device_bytes(const sdp_problem* h);
 int64_t sdp_launch_count(const sdp_problem* h);
 
 /*
- * Batched solves (SURVEY pattern "batched": many uneven problems advanced
- * together).  sdp_batch_create groups count set-up problems (each keeps its own
+ * Batched solves (many uneven problems advanced together).  sdp_batch_create groups count set-up problems (each keeps its own
  * stream, data and state; all must use SDP_FP64 and SDP_PRECOND_HAT, 1 <= k <= 8).
  * sdp_batch_solve runs their interior-point iterations in lockstep: the dense
  * per-problem phases on each problem's stream (one host thread per problem),
@@ -249,6 +248,12 @@ sdp_status sdp_batch_create(sdp_problem* const* problems, int count, void* cuda_
 sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results);
 const char* sdp_batch_last_error(const sdp_batch* b);
 void sdp_batch_destroy(sdp_batch* b);
+/* Host wall-clock seconds the last sdp_batch_solve spent in each stage, summed
+ * over its iterations: out[0] residuals + NT scaling + preconditioner (all
+ * problems), out[1] predictor PCG (batched), out[2] predictor step lengths and
+ * corrector right-hand side, out[3] corrector PCG (batched), out[4] step
+ * lengths and the checked update.  out: 5 doubles.  SDP_ERR_ARG for NULL. */
+sdp_status sdp_batch_stage_seconds(const sdp_batch* b, double* out);
 
 /*
  * sdp_hessian_matvec_static -- handle-free, allocation-free variant of

@@ -107,6 +107,7 @@ SIGNATURES = {
     "sdp_batch_solve": (C.c_int, [_P, C.POINTER(sdp_result)]),
     "sdp_batch_last_error": (C.c_char_p, [_P]),
     "sdp_batch_destroy": (None, [_P]),
+    "sdp_batch_stage_seconds": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "sdp_destroy": (None, [_P]),
     "sdp_status_str": (C.c_char_p, [C.c_int]),
     "sdp_last_error": (C.c_char_p, [_P]),

@@ -271,6 +271,14 @@ class SDPBatch:
                                  f"{self.lib.sdp_batch_last_error(self.b).decode()}")
         return [{f: getattr(r, f) for f, _ in L.sdp_result._fields_} for r in res]
 
+    STAGES = ("nt_precond", "pcg_pred", "step_pred", "pcg_corr", "step_update")
+
+    def stage_seconds(self):
+        """Wall seconds of the last solve per stage (sdp_batch_stage_seconds)."""
+        out = (C.c_double * 5)()
+        self.lib.sdp_batch_stage_seconds(self.b, out)
+        return dict(zip(self.STAGES, list(out)))
+
     def close(self):
         if getattr(self, "b", None):
             self.lib.sdp_batch_destroy(self.b)

@@ -47,6 +47,7 @@ struct sdp_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t body_launches = 0;
+  double stage_s[5] = {};             // wall seconds per stage of the last solve
   std::string last_error;
 };
 
@@ -263,6 +264,13 @@ extern "C" sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results) {
   std::vector<double> rr(N, 0.0);
   int ipm_maxit = 0;
   for (auto* h : b->hs) ipm_maxit = std::max(ipm_maxit, h->prm.ipm_maxit);
+  for (double& x : b->stage_s) x = 0.0;
+  auto tick = std::chrono::steady_clock::now();
+  auto lap = [&](int stage) {
+    const auto now = std::chrono::steady_clock::now();
+    b->stage_s[stage] += std::chrono::duration<double>(now - tick).count();
+    tick = now;
+  };
   for (int it = 0; it <= ipm_maxit; ++it) {
     std::vector<int> act;
     for (int i = 0; i < N; ++i)
@@ -274,6 +282,7 @@ extern "C" sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results) {
       st[i] = ipm_phase_a(b->hs[i], &s[i], &d);
       conv[i] = d;
     });
+    lap(0);
     std::vector<int> solve;
     for (int i : act) {
       if (st[i] != SDP_OK) continue;
@@ -283,21 +292,25 @@ extern "C" sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results) {
     }
     if (solve.empty()) continue;
     SDP_TRY(batch_newton(b, solve, its, rr, st));
+    lap(1);
     std::vector<int> nxt;
     for (int i : solve) if (st[i] == SDP_OK) nxt.push_back(i);
     parallel_for(nxt, [&](int i) {
       pcg_total[i] += its[i];
       st[i] = ipm_phase_b(b->hs[i], &s[i], its[i], rr[i]);
     });
+    lap(2);
     std::vector<int> nxt2;
     for (int i : nxt) if (st[i] == SDP_OK) nxt2.push_back(i);
     SDP_TRY(batch_newton(b, nxt2, its, rr, st));
+    lap(3);
     std::vector<int> nxt3;
     for (int i : nxt2) if (st[i] == SDP_OK) nxt3.push_back(i);
     parallel_for(nxt3, [&](int i) {
       pcg_total[i] += its[i];
       st[i] = ipm_phase_c(b->hs[i], &s[i], its[i], rr[i]);
     });
+    lap(4);
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   sdp_status worst = SDP_OK;
@@ -323,6 +336,12 @@ extern "C" sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results) {
 }
 
 extern "C" const char* sdp_batch_last_error(const sdp_batch* b) { return b ? b->last_error.c_str() : ""; }
+
+extern "C" sdp_status sdp_batch_stage_seconds(const sdp_batch* b, double* out) {
+  if (!b || !out) return SDP_ERR_ARG;
+  for (int i = 0; i < 5; ++i) out[i] = b->stage_s[i];
+  return SDP_OK;
+}
 
 extern "C" void sdp_batch_destroy(sdp_batch* b) {
   if (!b) return;

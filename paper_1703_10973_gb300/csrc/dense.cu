@@ -22,12 +22,19 @@ static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) 
 template <typename T, int BM, int BN, bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A,
                                               int lda, const T* __restrict__ B, int ldb, T beta,
-                                              T* __restrict__ C, int ldc, int lower_only,
+                                              T* __restrict__ C, int ldc, int flags,
                                               long long sA, long long sB, long long sC) {
   constexpr int BK = 16;
   constexpr int TM = BM / 16, TN = BN / 16;
   const int bm = blockIdx.y * BM, bn = blockIdx.x * BN;
-  if (lower_only && bn > bm + BM - 1) return;
+  if ((flags & GEMM_LOWER_C) && bn > bm + BM - 1) return;
+  // k range that can hold nonzero products when op(A) or op(B) is triangular
+  // (the skipped entries are stored zeros, so the boundary chunk needs no mask)
+  int kbeg = 0, kend = K;
+  if (flags & GEMM_A_UPPER) kbeg = max(kbeg, bm);
+  if (flags & GEMM_B_LOWER) kbeg = max(kbeg, bn);
+  if (flags & GEMM_A_LOWER) kend = min(kend, bm + BM);
+  if (flags & GEMM_B_UPPER) kend = min(kend, bn + BN);
   A += (long long)blockIdx.z * sA;
   B += (long long)blockIdx.z * sB;
   C += (long long)blockIdx.z * sC;
@@ -40,7 +47,7 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, T alpha, cons
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 
-  for (int k0 = 0; k0 < K; k0 += BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
     for (int t = threadIdx.x; t < BM * BK; t += 256) {
       int r, c;
       if (!TA) { r = t / BK; c = t % BK; } else { c = t / BM; r = t % BM; }
@@ -89,22 +96,40 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, T alpha, cons
 
 template <typename T, int BM, int BN>
 static void gemm_launch(cudaStream_t st, bool tA, bool tB, int M, int N, int K, T alpha, const T* A,
-                        int lda, const T* B, int ldb, T beta, T* C, int ldc, int lower_only,
+                        int lda, const T* B, int ldb, T beta, T* C, int ldc, int flags,
                         int batch, long long sA, long long sB, long long sC) {
   dim3 grid(cdiv(N, BN), cdiv(M, BM), batch);
   count_launch();
   if (!tA && !tB)
-    k_gemm<T, BM, BN, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, sA, sB, sC);
+    k_gemm<T, BM, BN, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, sA, sB, sC);
   else if (!tA && tB)
-    k_gemm<T, BM, BN, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, sA, sB, sC);
+    k_gemm<T, BM, BN, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, sA, sB, sC);
   else if (tA && !tB)
-    k_gemm<T, BM, BN, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, sA, sB, sC);
+    k_gemm<T, BM, BN, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, sA, sB, sC);
   else
-    k_gemm<T, BM, BN, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, sA, sB, sC);
+    k_gemm<T, BM, BN, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, sA, sB, sC);
+}
+
+// Multiply-adds a gemm call performs on entries that are not structural zeros:
+// the k range of every tile it runs, times the tile's rows and columns inside C.
+double gemm_useful_fma(int M, int N, int K, int flags, int tile) {
+  double f = 0.0;
+  for (int bm = 0; bm < M; bm += tile)
+    for (int bn = 0; bn < N; bn += tile) {
+      if ((flags & GEMM_LOWER_C) && bn > bm + tile - 1) continue;
+      int kbeg = 0, kend = K;
+      if (flags & GEMM_A_UPPER) kbeg = std::max(kbeg, bm);
+      if (flags & GEMM_B_LOWER) kbeg = std::max(kbeg, bn);
+      if (flags & GEMM_A_LOWER) kend = std::min(kend, bm + tile);
+      if (flags & GEMM_B_UPPER) kend = std::min(kend, bn + tile);
+      if (kend > kbeg)
+        f += (double)std::min(tile, M - bm) * std::min(tile, N - bn) * (kend - kbeg);
+    }
+  return f;
 }
 
 void gemm(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
-          int lda, const double* B, int ldb, double beta, double* C, int ldc, int lower_only,
+          int lda, const double* B, int ldb, double beta, double* C, int ldc, int flags,
           int batch, long long sA, long long sB, long long sC) {
   if (M <= 0 || N <= 0) return;
   if (K <= 0) {  // C = beta C
@@ -112,19 +137,20 @@ void gemm(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, 
       for (int b = 0; b < batch; ++b) copy2d(st, M, N, nullptr, 0, C + b * sC, ldc);
     } else {
       gemm_launch<double, 32, 32>(st, false, false, M, N, 1, 0.0, C, ldc, C, ldc, beta, C, ldc,
-                                  lower_only, batch, sC, sC, sC);
+                                  flags & GEMM_LOWER_C, batch, sC, sC, sC);
     }
     return;
   }
   const long long tiles64 = (long long)cdiv(M, 64) * cdiv(N, 64) * batch;
   const bool timed = ktimer_on("gemm_f64");
   if (timed) ktimer_begin(st, "gemm_f64");
-  if (tiles64 >= 2 * 152)
-    gemm_launch<double, 64, 64>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, batch, sA, sB, sC);
+  const int tile = (tiles64 >= 2 * 152) ? 64 : 32;
+  if (tile == 64)
+    gemm_launch<double, 64, 64>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, batch, sA, sB, sC);
   else
-    gemm_launch<double, 32, 32>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, batch, sA, sB, sC);
+    gemm_launch<double, 32, 32>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, batch, sA, sB, sC);
   if (timed) {
-    const double f = 2.0 * M * N * (double)K * batch * (lower_only ? 0.5 : 1.0);
+    const double f = 2.0 * gemm_useful_fma(M, N, K, flags, tile) * batch;
     const double by = 8.0 * ((double)M * K + (double)K * N + 2.0 * M * N) * batch;
     ktimer_end(st, "gemm_f64", f, by);
   }

@@ -9,11 +9,13 @@
 //  3. Eigenvectors of T by inverse iteration with a pivoted tridiagonal LU (one
 //     thread per eigenvalue, interleaved workspace so that the per-thread
 //     sequential sweeps load coalesced).
-//  4. Re-orthogonalisation of the eigenvector block by one Cholesky-QR pass
-//     (Gram matrix GEMM, Cholesky, triangular solve), which repairs the loss of
-//     orthogonality of inverse iteration inside eigenvalue clusters.
+//  4. Re-orthogonalisation of the eigenvector block by up to two Cholesky-QR
+//     passes (Gram matrix GEMM, Cholesky, triangular solve), which repair the
+//     loss of orthogonality of inverse iteration inside eigenvalue clusters; a
+//     pass whose Gram matrix is already the identity to 1e-12 stops there.
 //  5. Back-transformation by the stored reflectors (one warp per eigenvector,
 //     no inter-CTA communication).
+#include <cstring>
 #include "internal.cuh"
 
 #include <cooperative_groups.h>
@@ -893,15 +895,45 @@ static void eigenvectors(cudaStream_t st, int n, EigWork* w, int nblocks, const 
   }
 }
 
+// max over the lower triangle of |G_ij - delta_ij| (non-negative doubles order
+// like their bit patterns, so an integer atomicMax takes the maximum)
+constexpr double ORTH_TOL = 1e-12;
+__global__ void k_gram_err(int n, const double* __restrict__ G, int ldg, unsigned long long* err) {
+  double m = 0.0;
+  const size_t total = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (j > i) continue;
+    double v = fabs(G[(size_t)i * ldg + j] - (i == j ? 1.0 : 0.0));
+    if (!(v == v)) v = INFINITY;   // NaN counts as not orthogonal
+    m = fmax(m, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(err, (unsigned long long)__double_as_longlong(m));
+}
+
 sdp_status eig_full(cudaStream_t st, int n, double* A, double* wout, double* E, EigWork* w) {
   SDP_TRY(sytrd(st, n, A, w));
   const int nb = split_blocks(st, n, w);
   eigenvalues_all(st, n, w, nb, wout);
   eigenvectors(st, n, w, nb, wout, 0, n, E);
-  // two Cholesky-QR passes on the rows of E (the second removes the residual
-  // non-orthogonality left by the first inside tight clusters of one block)
+  // Up to two Cholesky-QR passes on the rows of E.  Inverse iteration leaves
+  // vectors of well separated eigenvalues orthogonal to working accuracy; only
+  // tight clusters inside one block lose orthogonality.  Each pass first forms
+  // the Gram matrix and stops when max |E E^T - I| is already at rounding level,
+  // so the factorisation and the triangular solve run only when needed.
   for (int pass = 0; pass < 2; ++pass) {
-    gemm(st, false, true, n, n, n, 1.0, E, n, E, n, 0.0, w->G, n, 1);
+    gemm(st, false, true, n, n, n, 1.0, E, n, E, n, 0.0, w->G, n, GEMM_LOWER_C);
+    unsigned long long* err = reinterpret_cast<unsigned long long*>(w->part);
+    SDP_CK_ST(cudaMemsetAsync(err, 0, sizeof(unsigned long long), st));
+    count_launch();
+    k_gram_err<<<std::min<unsigned>(cdiv((size_t)n * n, 256), 1024), 256, 0, st>>>(n, w->G, n, err);
+    unsigned long long bits = 0;
+    SDP_CK_ST(cudaMemcpyAsync(&bits, err, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    SDP_CK_ST(cudaStreamSynchronize(st));
+    double e;
+    std::memcpy(&e, &bits, sizeof(e));
+    if (e <= ORTH_TOL) break;
     potrf(st, n, w->G, n, w->info, w->aux);
     trsm_left_lower(st, false, n, n, w->G, n, E, n, w->aux);
   }

@@ -164,12 +164,19 @@ struct DBuf {
 // ---------------------------------------------------------------------------
 // Dense FP64 linear algebra (dense.cu).  Row-major storage; ld = row stride.
 // ---------------------------------------------------------------------------
-// C[M x N] = alpha * op(A) * op(B) + beta * C.  op(A) is M x K.  When
-// lower_only != 0 tiles strictly above the diagonal of C are skipped.
-// Batched over `batch` with element strides sA, sB, sC.
+// C[M x N] = alpha * op(A) * op(B) + beta * C.  op(A) is M x K.
+// flags: GEMM_LOWER_C skips tiles strictly above the diagonal of C (a symmetric
+// product; symmetrize_lower completes it).  GEMM_A_LOWER / GEMM_A_UPPER /
+// GEMM_B_LOWER / GEMM_B_UPPER declare op(A) or op(B) triangular with its other
+// triangle STORED as zeros, and restrict each tile's k range to the band that
+// can be nonzero.  Batched over `batch` with element strides sA, sB, sC.
+enum GemmFlags : int {
+  GEMM_LOWER_C = 1, GEMM_A_LOWER = 2, GEMM_A_UPPER = 4, GEMM_B_LOWER = 8, GEMM_B_UPPER = 16
+};
 void gemm(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha,
           const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
-          int lower_only = 0, int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0);
+          int flags = 0, int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0);
+double gemm_useful_fma(int M, int N, int K, int flags, int tile);
 void gemm_f32(cudaStream_t st, bool tA, bool tB, int M, int N, int K, float alpha,
               const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc);
 

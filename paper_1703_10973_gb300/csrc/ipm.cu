@@ -174,9 +174,9 @@ static sdp_status newton_post(sdp_problem* h) {
   scatter_V_dense(h, h->Vval, -1.0, h->dS);
   // dX = Rc - W dS W
   gemm(st, false, false, n, n, n, 1.0, h->W, n, h->dS, n, 0.0, h->M1, n);
-  gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->M2, n);
-  axpby(st, nn, 1.0, h->Rc, -1.0, h->M2, h->dX);
-  symmetrize_avg(st, n, h->dX, n);
+  gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->M2, n, GEMM_LOWER_C);
+  axpby(st, nn, 1.0, h->Rc, -1.0, h->M2, h->dX);   // upper triangle replaced next
+  symmetrize_lower(st, n, h->dX, n);
   return SDP_OK;
 }
 
@@ -291,18 +291,21 @@ static sdp_status nt_scaling(sdp_problem* h) {
   cudaStream_t st = h->stream;
   const int n = h->n;
   const size_t nn = (size_t)n * n;
-  gemm(st, false, false, n, n, n, 1.0, h->S, n, h->L, n, 0.0, h->M1, n);   // S L
-  gemm(st, true, false, n, n, n, 1.0, h->L, n, h->M1, n, 0.0, h->M2, n);   // M = L^T S L
-  symmetrize_avg(st, n, h->M2, n);
+  // L is lower triangular with stored zeros: S L needs k >= j, L^T (S L) needs
+  // k >= i, and only the lower triangle of the symmetric results is formed.
+  gemm(st, false, false, n, n, n, 1.0, h->S, n, h->L, n, 0.0, h->M1, n, GEMM_B_LOWER);   // S L
+  gemm(st, true, false, n, n, n, 1.0, h->L, n, h->M1, n, 0.0, h->M2, n,
+       GEMM_A_UPPER | GEMM_LOWER_C);                                                       // M = L^T S L
+  symmetrize_lower(st, n, h->M2, n);
   copy2d(st, n, n, h->M2, n, h->M3, n);                                      // keep M
   SDP_TRY(eig_full(st, n, h->M2, h->lam, h->E, &h->eig));
-  gemm(st, false, true, n, n, n, 1.0, h->L, n, h->E, n, 0.0, h->Gt, n);    // Gt = L Q, Q = E^T
+  gemm(st, false, true, n, n, n, 1.0, h->L, n, h->E, n, 0.0, h->Gt, n, GEMM_A_LOWER);   // Gt = L Q, Q = E^T
   scale_cols(st, n, n, h->Gt, n, h->lam, -0.5, h->M1, n);
-  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->W, n);
-  symmetrize_avg(st, n, h->W, n);
+  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->W, n, GEMM_LOWER_C);
+  symmetrize_lower(st, n, h->W, n);
   scale_cols(st, n, n, h->Gt, n, h->lam, -1.0, h->M1, n);
-  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->Sinv, n);
-  symmetrize_avg(st, n, h->Sinv, n);
+  gemm(st, false, true, n, n, n, 1.0, h->M1, n, h->Gt, n, 0.0, h->Sinv, n, GEMM_LOWER_C);
+  symmetrize_lower(st, n, h->Sinv, n);
   // check W S W = X on NT_PROBES fixed pseudo-random vectors Z: W (S (W Z)) - X Z
   {
     const int pr = NT_PROBES;
@@ -443,8 +446,8 @@ sdp_status ipm_phase_a(sdp_problem* h, IpmStepState* s, bool* done) {
   // once a full dual step has made the iterate dual feasible: Rd = 0 exactly)
   if (v[1] != 0.0) {
     gemm(st, false, false, n, n, n, 1.0, h->W, n, h->Rd, n, 0.0, h->M1, n);
-    gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->M3, n);
-    symmetrize_avg(st, n, h->M3, n);
+    gemm(st, false, false, n, n, n, 1.0, h->M1, n, h->W, n, 0.0, h->M3, n, GEMM_LOWER_C);
+    symmetrize_lower(st, n, h->M3, n);
     op_A_dense(h, h->M3, h->Rp, 1.0, h->Rp, 1.0);   // Rp <- Rp + A(W Rd W)
   }
 
