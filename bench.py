@@ -274,7 +274,8 @@ def run(args):
             res_b = batch.solve(allow_maxit=True)
             torch.cuda.synchronize()
             ms = (time.perf_counter() - t0b) * 1e3
-            stage_ms.update({k: round(v * 1e3, 1) for k, v in batch.stage_seconds().items()})
+            stage_ms.update({k: (round(v * 1e3, 1) if k not in ("graph_launches", "batched_iters") else int(v))
+                             for k, v in batch.stage_seconds().items()})
             return [ms] * len(probs), res_b
         if start_event is not None:
             for st in streams:

@@ -76,7 +76,8 @@ typedef struct {
   int pcg_graph;       /* 1 = the PCG loop runs on the device as a CUDA graph with */
                        /* a conditional while node (default); 0 = host-driven     */
                        /* loop launching the same kernels (for profilers that do  */
-                       /* not support conditional graph nodes)                    */
+                       /* not support conditional graph nodes); a batch follows   */
+                       /* the setting of its first problem                        */
   double inner_rtol_lp; /* PCG tolerance of one sweep whose matvec runs in FP32 or */
                         /* BF16 (the FP64 true residual refines it); 1e-4         */
 } sdp_params;
@@ -231,7 +232,8 @@ int64_t sdp_launch_count(const sdp_problem* h);
 
 /*
  * Batched solves (many uneven problems advanced together).  sdp_batch_create groups count set-up problems (each keeps its own
- * stream, data and state; all must use SDP_FP64 and SDP_PRECOND_HAT, 1 <= k <= 8).
+ * stream, data and state; all must use SDP_PRECOND_HAT with 1 <= k <= 8, and
+ * the SDP_FP64 or the SDP_FP32 (split) matvec; SDP_ERR_UNSUPPORTED otherwise).
  * sdp_batch_solve runs their interior-point iterations in lockstep: the dense
  * per-problem phases on each problem's stream (one host thread per problem),
  * and every PCG iteration of all their Newton systems as one sequence of
@@ -252,7 +254,10 @@ void sdp_batch_destroy(sdp_batch* b);
  * over its iterations: out[0] residuals + NT scaling + preconditioner (all
  * problems), out[1] predictor PCG (batched), out[2] predictor step lengths and
  * corrector right-hand side, out[3] corrector PCG (batched), out[4] step
- * lengths and the checked update.  out: 5 doubles.  SDP_ERR_ARG for NULL. */
+ * lengths and the checked update; out[5] the part of out[1] + out[3] spent in
+ * the batched graph launches, out[6] the number of those launches (PCG sweeps
+ * of the batch), out[7] the batched PCG iterations they ran (per launch, the
+ * most any problem ran).  out: 8 doubles.  SDP_ERR_ARG for NULL. */
 sdp_status sdp_batch_stage_seconds(const sdp_batch* b, double* out);
 
 /*

@@ -271,11 +271,13 @@ class SDPBatch:
                                  f"{self.lib.sdp_batch_last_error(self.b).decode()}")
         return [{f: getattr(r, f) for f, _ in L.sdp_result._fields_} for r in res]
 
-    STAGES = ("nt_precond", "pcg_pred", "step_pred", "pcg_corr", "step_update")
+    STAGES = ("nt_precond", "pcg_pred", "step_pred", "pcg_corr", "step_update", "pcg_graph",
+              "graph_launches", "batched_iters")
 
     def stage_seconds(self):
-        """Wall seconds of the last solve per stage (sdp_batch_stage_seconds)."""
-        out = (C.c_double * 5)()
+        """Wall seconds of the last solve per stage, then graph seconds, graph launches and
+        batched PCG iterations (sdp_batch_stage_seconds)."""
+        out = (C.c_double * 8)()
         self.lib.sdp_batch_stage_seconds(self.b, out)
         return dict(zip(self.STAGES, list(out)))
 

@@ -18,7 +18,9 @@
 //
 // The restarted outer loop (refinement on the FP64 true residual) is the
 // single-problem PcgSweeps state machine, stepped for all problems together.
-// Supported: FP64 matvec and the Hhat preconditioner (the defaults).
+// Supported: the Hhat preconditioner (the default) with the FP64 matvec or the
+// FP32 split matvec; a problem whose FP32 sweep stalls hands over to FP64 on
+// its own, so one batched iteration can mix both forms.
 #include "internal.cuh"
 
 #include <algorithm>
@@ -31,7 +33,8 @@ namespace sdpgb {
 
 static inline int cdivi(int a, int b) { return (a + b - 1) / b; }
 
-enum { BK_ASM, BK_SPMM, BK_SDDMM, BK_VEC, BK_HATU, BK_TAIL, BK_FWDP, BK_FWDR, BK_GEMV, BK_OUTR, BK_BWDP, BK_COUNT };
+enum { BK_ASM, BK_SPMM, BK_SDDMM, BK_VEC, BK_HATU, BK_TAIL, BK_FWDP, BK_FWDR, BK_GEMV, BK_OUTR, BK_BWDP,
+       BK_SPLG, BK_SPLR, BK_SPLQ, BK_SPMM_LP, BK_COUNT };
 
 }  // namespace sdpgb
 
@@ -44,17 +47,24 @@ struct sdp_batch {
   std::vector<int> off;               // host copy
   int total[sdpgb::BK_COUNT] = {};
   int nmax = 0;
+  bool any_lp = false;                // some problem runs FP32 sweeps: the graph holds the FP32 matvec
+  bool host_loop = false;             // pcg_graph == 0: the host launches every iteration (profilers)
+  int* dflag = nullptr;               // host loop: "some problem active" after each iteration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t body_launches = 0;
-  double stage_s[5] = {};             // wall seconds per stage of the last solve
+  double stage_s[8] = {};             // wall seconds per stage of the last solve, then
+                                      // graph seconds, graph launches, batched iterations
   std::string last_error;
 };
 
 namespace sdpgb {
 
 static bool batch_supported(sdp_problem* h, std::string* why) {
-  if (h->prm.prec != SDP_FP64) { *why = "batched solves run the FP64 matvec (params.prec = SDP_FP64)"; return false; }
+  if (h->prm.prec != SDP_FP64 && h->prm.prec != SDP_FP32) {
+    *why = "batched solves run the FP64 or the FP32 split matvec (params.prec = SDP_FP64 or SDP_FP32)";
+    return false;
+  }
   if (h->prm.precond != SDP_PRECOND_HAT) { *why = "batched solves use the Hhat preconditioner"; return false; }
   const int k = std::min(h->k, std::max(h->n - 1, 0));
   if (k < 1 || k > 8) { *why = "batched solves need 1 <= k <= 8"; return false; }
@@ -73,15 +83,18 @@ static void batch_offsets(sdp_batch* b) {
                                batch_blocks_vec(h->m),         batch_blocks_hat_u(h->n), batch_blocks_tail(h->m),
                                batch_blocks_fwdP(h->hs_np),    batch_blocks_warp_rows(h->hs_nr),
                                batch_blocks_warp_rows(Rk),     batch_blocks_outR(Rk),
-                               batch_blocks_warp_rows(h->hs_np)};
+                               batch_blocks_warp_rows(h->hs_np),
+                               batch_blocks_split_G(h->n),     batch_blocks_split_R(h->n),
+                               batch_blocks_split_Q(h->n, k),  batch_blocks_spmm_lp(h->n)};
     for (int kd = 0; kd < BK_COUNT; ++kd)
       b->off[(size_t)kd * (N + 1) + i + 1] = b->off[(size_t)kd * (N + 1) + i] + cnt[kd];
     b->nmax = std::max(b->nmax, h->n);
+    if (h->prm.prec == SDP_FP32) b->any_lp = true;
   }
   for (int kd = 0; kd < BK_COUNT; ++kd) b->total[kd] = b->off[(size_t)kd * (N + 1) + N];
 }
 
-static BDesc make_desc(sdp_problem* h, int active) {
+static BDesc make_desc(sdp_problem* h, int active, int prec) {
   BDesc D{};
   D.n = h->n; D.m = h->m; D.k = h->kpc; D.np = h->hs_np; D.nr = h->hs_nr; D.Rk = h->hs_nr * h->kpc;
   D.nnzV = h->nnzV;
@@ -98,16 +111,24 @@ static BDesc make_desc(sdp_problem* h, int active) {
   D.yP = h->hs_yP; D.v1 = h->hs_v1; D.v2 = h->hs_v2; D.uvec = h->uvec; D.Bn = h->Bn;
   D.px = h->px; D.pr = h->pr; D.pp = h->pp; D.pq = h->pq; D.pz = h->pz;
   D.scal = h->scal; D.part = h->pcg_part; D.ticket = h->pcg_ticket;
+  D.lp = (prec == SDP_FP32) ? 1 : 0;
+  D.ks = (D.lp && h->W32_key >= 0) ? h->kpc : 0;
+  D.W32 = h->W32; D.T32 = h->T32; D.mvR = h->mv_R; D.mvPart = h->mv_part;
+  D.Etop = h->Etop; D.wtop = h->wtop; D.mvG = h->mv_G; D.mvQ = h->mv_Q;
   return D;
 }
 
 // One PCG iteration of every active problem (the body of the batched loop).
-static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle cond) {
+static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle cond, int* flag) {
   const int N = (int)b->hs.size();
   const int* o = b->doff;
   auto off = [&](int kd) { return o + (size_t)kd * (N + 1); };
   batch_launch_matvec(st, b->ddesc, off(BK_ASM), off(BK_SPMM), off(BK_SDDMM), N, b->total[BK_ASM],
                       b->total[BK_SPMM], b->total[BK_SDDMM], b->nmax);
+  if (b->any_lp)   // same SDDMM partition (and reduction groups) as the FP64 form
+    batch_launch_matvec_lp(st, b->ddesc, off(BK_SPLG), off(BK_SPLR), off(BK_SPLQ), off(BK_SPMM_LP), off(BK_SDDMM),
+                           N, b->total[BK_SPLG], b->total[BK_SPLR], b->total[BK_SPLQ], b->total[BK_SPMM_LP],
+                           b->total[BK_SDDMM], b->nmax);
   batch_launch_xr(st, b->ddesc, off(BK_VEC), N, b->total[BK_VEC]);
   batch_launch_hat_u(st, b->ddesc, off(BK_HATU), N, b->total[BK_HATU]);
   batch_launch_core_solve(st, b->ddesc, N, off(BK_FWDP), b->total[BK_FWDP], off(BK_FWDR), b->total[BK_FWDR],
@@ -115,11 +136,11 @@ static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle
                           b->total[BK_BWDP]);
   batch_launch_tail(st, b->ddesc, off(BK_TAIL), N, b->total[BK_TAIL]);
   batch_launch_p(st, b->ddesc, off(BK_VEC), N, b->total[BK_VEC]);
-  batch_launch_any(st, b->ddesc, N, cond);
+  batch_launch_any(st, b->ddesc, N, cond, flag);
 }
 
 static sdp_status batch_prepare(sdp_batch* b) {
-  if (b->exec) return SDP_OK;
+  if (b->exec || b->host_loop) return SDP_OK;
   const int N = (int)b->hs.size();
   batch_offsets(b);
   if (cudaMalloc(&b->ddesc, sizeof(BDesc) * N) != cudaSuccess ||
@@ -129,6 +150,15 @@ static sdp_status batch_prepare(sdp_batch* b) {
     return SDP_ERR_OOM;
   }
   cudaMemcpy(b->doff, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice);
+  if (b->hs[0]->prm.pcg_graph == 0) {
+    if (cudaMalloc(&b->dflag, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      b->last_error = "sdp_batch: device allocation failed";
+      return SDP_ERR_OOM;
+    }
+    b->host_loop = true;
+    return SDP_OK;
+  }
   cudaGraph_t g = nullptr;
   cudaGraphConditionalHandle cond;
   cudaGraphNodeParams np = {};
@@ -150,7 +180,7 @@ static sdp_status batch_prepare(sdp_batch* b) {
   ktimer_pause(true);
   cudaError_t e = cudaStreamBeginCaptureToGraph(b->capture, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                 cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) batch_body(b, b->capture, cond);
+  if (e == cudaSuccess) batch_body(b, b->capture, cond, nullptr);
   cudaGraph_t out = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(b->capture, &out);
   ktimer_pause(false);
@@ -175,7 +205,7 @@ static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::v
   std::vector<char> live(N, 0);
   for (int i : idx) {
     sdp_problem* h = b->hs[i];
-    st[i] = pcg_sweeps_init(h, &S[i], h->rhs, h->dy, h->prm.pcg_rtol, h->prm.pcg_maxit, SDP_FP64);
+    st[i] = pcg_sweeps_init(h, &S[i], h->rhs, h->dy, h->prm.pcg_rtol, h->prm.pcg_maxit, h->prm.prec);
     live[i] = (st[i] == SDP_OK);
   }
   SDP_TRY(batch_prepare(b));
@@ -191,16 +221,31 @@ static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::v
       else live[i] = 0;
     }
     if (running.empty()) break;
-    for (int i = 0; i < N; ++i) hd[i] = make_desc(b->hs[i], 0);
+    for (int i = 0; i < N; ++i) hd[i] = make_desc(b->hs[i], 0, S[i].prec);
     for (int i : running) {
       cudaStreamSynchronize(b->hs[i]->stream);
       hd[i].active = 1;
     }
-    if (cudaMemcpyAsync(b->ddesc, hd.data(), sizeof(BDesc) * N, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-        cudaGraphLaunch(b->exec, b->stream) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    const auto g0 = std::chrono::steady_clock::now();
+    if (cudaMemcpyAsync(b->ddesc, hd.data(), sizeof(BDesc) * N, cudaMemcpyHostToDevice, b->stream) != cudaSuccess) {
+      b->last_error = std::string("sdp_batch: descriptor upload failed: ") + cudaGetErrorString(cudaGetLastError());
+      return SDP_ERR_CUDA;
+    }
+    if (b->host_loop) {
+      for (int flag = 1; flag;) {
+        batch_body(b, b->stream, cudaGraphConditionalHandle{}, b->dflag);
+        if (cudaMemcpyAsync(&flag, b->dflag, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+            cudaStreamSynchronize(b->stream) != cudaSuccess) {
+          b->last_error = std::string("sdp_batch: batched PCG failed: ") + cudaGetErrorString(cudaGetLastError());
+          return SDP_ERR_CUDA;
+        }
+      }
+    } else if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess) {
       b->last_error = std::string("sdp_batch: batched PCG failed: ") + cudaGetErrorString(cudaGetLastError());
       return SDP_ERR_CUDA;
     }
+    b->stage_s[5] += std::chrono::duration<double>(std::chrono::steady_clock::now() - g0).count();
+    b->stage_s[6] += 1.0;
     int max_it = 0;
     for (int i : running) {
       const int before = S[i].total;
@@ -208,7 +253,8 @@ static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::v
       max_it = std::max(max_it, S[i].total - before);
       if (st[i] != SDP_OK) live[i] = 0;
     }
-    g_launches.fetch_add((int64_t)max_it * b->body_launches);
+    if (!b->host_loop) g_launches.fetch_add((int64_t)max_it * b->body_launches);
+    b->stage_s[7] += max_it;
   }
   for (int i : idx) {
     its[i] = S[i].total;
@@ -339,7 +385,7 @@ extern "C" const char* sdp_batch_last_error(const sdp_batch* b) { return b ? b->
 
 extern "C" sdp_status sdp_batch_stage_seconds(const sdp_batch* b, double* out) {
   if (!b || !out) return SDP_ERR_ARG;
-  for (int i = 0; i < 5; ++i) out[i] = b->stage_s[i];
+  for (int i = 0; i < 8; ++i) out[i] = b->stage_s[i];
   return SDP_OK;
 }
 
@@ -351,5 +397,6 @@ extern "C" void sdp_batch_destroy(sdp_batch* b) {
   if (b->capture) cudaStreamDestroy(b->capture);
   if (b->ddesc) cudaFree(b->ddesc);
   if (b->doff) cudaFree(b->doff);
+  if (b->dflag) cudaFree(b->dflag);
   delete b;
 }

@@ -64,7 +64,7 @@ __device__ inline bool lb_reduce(double v, double* part, unsigned int* ticket, d
 enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6, S_IT = 7, S_MAXIT = 8,
        S_BRK = 9, S_GO = 10 };
 
-// One problem of a batched PCG launch (FP64 matvec, Hhat preconditioner): the
+// One problem of a batched PCG launch (FP64 or FP32 split matvec, Hhat preconditioner): the
 // device pointers and sizes the batched kernels read, refreshed by the host
 // before every batched solve.
 struct BDesc {
@@ -81,6 +81,12 @@ struct BDesc {
   double *px, *pr, *pp, *pq, *pz;
   double *scal, *part;
   unsigned int* ticket;
+  // FP32 split matvec (a problem in a reduced-precision sweep)
+  int lp, ks;                       // lp: this sweep runs the FP32 matvec; ks: split rank (0: none)
+  const float* W32;
+  float *T32, *mvR, *mvPart;
+  const double *Etop, *wtop;
+  double *mvG, *mvQ;
 };
 
 // Finds the problem that owns block b of a batched grid: off[0..N] are the
@@ -457,11 +463,19 @@ int batch_blocks_tail(int m);
 int batch_blocks_fwdP(int np);
 int batch_blocks_warp_rows(int rows);
 int batch_blocks_outR(int Rk);
+int batch_blocks_split_G(int n);
+int batch_blocks_split_R(int n);
+int batch_blocks_split_Q(int n, int k);
+int batch_blocks_spmm_lp(int n);
+void batch_launch_matvec_lp(cudaStream_t st, const BDesc* desc, const int* off_g, const int* off_r,
+                            const int* off_q, const int* off_spmm, const int* off_sddmm, int N, int nb_g, int nb_r,
+                            int nb_q, int nb_spmm, int nb_sddmm, int nmax);
 void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm, const int* off_spmm,
                          const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax);
 void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb);
 void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
-void batch_launch_any(cudaStream_t st, const BDesc* desc, int N, cudaGraphConditionalHandle cond);
+// flag != nullptr: write "some problem active" to *flag (host-driven loop) instead of the graph condition
+void batch_launch_any(cudaStream_t st, const BDesc* desc, int N, cudaGraphConditionalHandle cond, int* flag);
 void batch_launch_hat_u(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
 void batch_launch_tail(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
 void batch_launch_core_solve(cudaStream_t st, const BDesc* desc, int N, const int* off_fwdP, int nb_fwdP,

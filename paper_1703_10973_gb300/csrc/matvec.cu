@@ -72,6 +72,7 @@ void assemble_V(sdp_problem* h, const double* v, const double* scale, double* Vv
 // ---------------------------------------------------------------------------
 // K1: T = W V, R rows of W per CTA staged in shared memory
 // ---------------------------------------------------------------------------
+constexpr int SPMM_UNROLL = 8;
 template <int R>
 __device__ __forceinline__ void spmm_f64_body(int blk, int n, const int* __restrict__ rowptr,
                                               const int* __restrict__ colidx, const double* __restrict__ Vval,
@@ -87,7 +88,23 @@ __device__ __forceinline__ void spmm_f64_body(int blk, int n, const int* __restr
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) acc[rr] = 0.0;
     const int s1 = rowptr[l + 1];
-    for (int s = rowptr[l]; s < s1; ++s) {
+    int s = rowptr[l];
+    // eight entries of column l per step: their loads are independent, so each
+    // thread keeps eight L2 requests in flight instead of one
+    for (; s + SPMM_UNROLL <= s1; s += SPMM_UNROLL) {
+      int col[SPMM_UNROLL];
+      double val[SPMM_UNROLL];
+#pragma unroll
+      for (int u = 0; u < SPMM_UNROLL; ++u) {
+        col[u] = colidx[s + u];
+        val[u] = Vval[s + u];
+      }
+#pragma unroll
+      for (int u = 0; u < SPMM_UNROLL; ++u)
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) acc[rr] = fma(val[u], wsh[rr * n + col[u]], acc[rr]);
+    }
+    for (; s < s1; ++s) {
       const double val = Vval[s];
       const int col = colidx[s];
 #pragma unroll
@@ -108,12 +125,10 @@ __global__ void __launch_bounds__(256) k_spmm_wv_f64(int n, const int* __restric
 }
 
 template <typename TW, int R>
-__global__ void __launch_bounds__(256) k_spmm_wv_lp(int n, const int* __restrict__ rowptr,
-                                                    const int* __restrict__ colidx,
-                                                    const double* __restrict__ Vval,
-                                                    const TW* __restrict__ W, float* __restrict__ T) {
-  extern __shared__ float fsh[];  // R x n
-  const int r0 = blockIdx.x * R;
+__device__ __forceinline__ void spmm_lp_body(int blk, int n, const int* __restrict__ rowptr,
+                                             const int* __restrict__ colidx, const double* __restrict__ Vval,
+                                             const TW* __restrict__ W, float* __restrict__ T, float* fsh) {
+  const int r0 = blk * R;
   for (int t = threadIdx.x; t < R * n; t += blockDim.x) {
     const int rr = t / n, c = t % n;
     fsh[t] = (r0 + rr < n) ? tof<TW>(W[(size_t)(r0 + rr) * n + c]) : 0.f;
@@ -124,7 +139,21 @@ __global__ void __launch_bounds__(256) k_spmm_wv_lp(int n, const int* __restrict
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) acc[rr] = 0.f;
     const int s1 = rowptr[l + 1];
-    for (int s = rowptr[l]; s < s1; ++s) {
+    int s = rowptr[l];
+    for (; s + SPMM_UNROLL <= s1; s += SPMM_UNROLL) {
+      int col[SPMM_UNROLL];
+      float val[SPMM_UNROLL];
+#pragma unroll
+      for (int u = 0; u < SPMM_UNROLL; ++u) {
+        col[u] = colidx[s + u];
+        val[u] = (float)Vval[s + u];
+      }
+#pragma unroll
+      for (int u = 0; u < SPMM_UNROLL; ++u)
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) acc[rr] = fmaf(val[u], fsh[rr * n + col[u]], acc[rr]);
+    }
+    for (; s < s1; ++s) {
       const float val = (float)Vval[s];
       const int col = colidx[s];
 #pragma unroll
@@ -134,6 +163,14 @@ __global__ void __launch_bounds__(256) k_spmm_wv_lp(int n, const int* __restrict
     for (int rr = 0; rr < R; ++rr)
       if (r0 + rr < n) T[(size_t)(r0 + rr) * n + l] = acc[rr];
   }
+}
+template <typename TW, int R>
+__global__ void __launch_bounds__(256) k_spmm_wv_lp(int n, const int* __restrict__ rowptr,
+                                                    const int* __restrict__ colidx,
+                                                    const double* __restrict__ Vval,
+                                                    const TW* __restrict__ W, float* __restrict__ T) {
+  extern __shared__ float fsh[];  // R x n
+  spmm_lp_body<TW, R>(blockIdx.x, n, rowptr, colidx, Vval, W, T, fsh);
 }
 
 // ---------------------------------------------------------------------------
@@ -154,7 +191,16 @@ __device__ __forceinline__ void sddmm_f64_body(int lb, int nb, int n, int m, con
       const double* wp = W + (size_t)ep[e] * n;
       const double* tq = T + (size_t)eq[e] * n;
       double s = 0.0;
-      for (int l = lane; l < n; l += 32) s = fma(wp[l], tq[l], s);
+      int l = lane;
+      for (; l + 96 < n; l += 128) {   // four loads of each row in flight per lane
+        const double w0 = wp[l], w1 = wp[l + 32], w2 = wp[l + 64], w3 = wp[l + 96];
+        const double t0 = tq[l], t1 = tq[l + 32], t2 = tq[l + 64], t3 = tq[l + 96];
+        s = fma(w0, t0, s);
+        s = fma(w1, t1, s);
+        s = fma(w2, t2, s);
+        s = fma(w3, t3, s);
+      }
+      for (; l < n; l += 32) s = fma(wp[l], tq[l], s);
       acc = fma(ecoef[e], s, acc);
     }
     acc = wsum_d(acc);
@@ -195,13 +241,13 @@ __global__ void __launch_bounds__(256) kb_spmm(const BDesc* __restrict__ desc, c
   extern __shared__ double wsh[];
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
-  if (!D.active) return;
+  if (!D.active || D.lp) return;
   spmm_f64_body<BATCH_SPMM_R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W, D.T, wsh);
 }
 __global__ void __launch_bounds__(256) kb_sddmm(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
-  if (!D.active) return;
+  if (!D.active || D.lp) return;
   sddmm_f64_body(blockIdx.x - off[i], off[i + 1] - off[i], D.n, D.m, D.eptr, D.ep, D.eq, D.ecoef, D.W, D.T, D.pq,
                  D.pp, D.part, D.ticket, D.scal + S_PQ, D.scal + S_RZ, D.scal + S_RZN);
 }
@@ -219,15 +265,15 @@ void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm,
 }
 
 template <typename TW>
-__global__ void __launch_bounds__(256) k_sddmm_lp(int n, int m, const int* __restrict__ eptr,
-                                                  const int* __restrict__ ep, const int* __restrict__ eq,
-                                                  const double* __restrict__ ecoef, const TW* __restrict__ W,
-                                                  const float* __restrict__ T, double* __restrict__ Hv,
-                                                  const double* __restrict__ dv, double* dpart, unsigned int* ticket,
-                                                  double* dout, double* pro_dst, const double* pro_src, int k,
-                                                  const double* __restrict__ E, const float* __restrict__ R,
-                                                  const double* __restrict__ Q) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+__device__ __forceinline__ void sddmm_lp_body(int lb, int nb, int n, int m, const int* __restrict__ eptr,
+                                              const int* __restrict__ ep, const int* __restrict__ eq,
+                                              const double* __restrict__ ecoef, const TW* __restrict__ W,
+                                              const float* __restrict__ T, double* __restrict__ Hv,
+                                              const double* __restrict__ dv, double* dpart, unsigned int* ticket,
+                                              double* dout, double* pro_dst, const double* pro_src, int k,
+                                              const double* __restrict__ E, const float* __restrict__ R,
+                                              const double* __restrict__ Q) {
+  const int i = (lb * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   double hv = 0.0;
   if (i < m) {
     for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
@@ -235,7 +281,17 @@ __global__ void __launch_bounds__(256) k_sddmm_lp(int n, int m, const int* __res
       const TW* wp = W + (size_t)p * n;
       const float* tq = T + (size_t)q * n;
       float s = 0.f;
-      for (int l = lane; l < n; l += 32) s = fmaf(tof<TW>(wp[l]), tq[l], s);
+      int l = lane;
+      for (; l + 96 < n; l += 128) {
+        const float w0 = tof<TW>(wp[l]), w1 = tof<TW>(wp[l + 32]), w2 = tof<TW>(wp[l + 64]),
+                    w3 = tof<TW>(wp[l + 96]);
+        const float t0 = tq[l], t1 = tq[l + 32], t2 = tq[l + 64], t3 = tq[l + 96];
+        s = fmaf(w0, t0, s);
+        s = fmaf(w1, t1, s);
+        s = fmaf(w2, t2, s);
+        s = fmaf(w3, t3, s);
+      }
+      for (; l < n; l += 32) s = fmaf(tof<TW>(wp[l]), tq[l], s);
       double v = (double)wsum_f(s);
       if (k > 0 && lane == 0) {
         // low-rank terms of the split, in FP64
@@ -255,18 +311,31 @@ __global__ void __launch_bounds__(256) k_sddmm_lp(int n, int m, const int* __res
   if (dv) {
     const double c = (i < m && lane == 0) ? dv[i] * hv : 0.0;
     double tot;
-    if (lb_reduce(c, dpart, ticket, &tot, blockIdx.x, gridDim.x)) {
+    if (lb_reduce(c, dpart, ticket, &tot, lb, nb)) {
       if (pro_dst) *pro_dst = *pro_src;
       *dout = tot;
     }
   }
 }
+template <typename TW>
+__global__ void __launch_bounds__(256) k_sddmm_lp(int n, int m, const int* __restrict__ eptr,
+                                                  const int* __restrict__ ep, const int* __restrict__ eq,
+                                                  const double* __restrict__ ecoef, const TW* __restrict__ W,
+                                                  const float* __restrict__ T, double* __restrict__ Hv,
+                                                  const double* __restrict__ dv, double* dpart, unsigned int* ticket,
+                                                  double* dout, double* pro_dst, const double* pro_src, int k,
+                                                  const double* __restrict__ E, const float* __restrict__ R,
+                                                  const double* __restrict__ Q) {
+  sddmm_lp_body<TW>(blockIdx.x, gridDim.x, n, m, eptr, ep, eq, ecoef, W, T, Hv, dv, dpart, ticket, dout, pro_dst,
+                    pro_src, k, E, R, Q);
+}
 
 // Split: G^T[c][l] = (E V)[l][c] = sum_{s in row c} V[c][s] E[l][s] (V symmetric);
 // one warp per row c.
-__global__ void k_split_G(int n, int k, const int* __restrict__ rowptr, const int* __restrict__ colidx,
-                          const double* __restrict__ Vval, const double* __restrict__ E, double* __restrict__ Gt) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void split_G_body(int lb, int n, int k, const int* __restrict__ rowptr,
+                                             const int* __restrict__ colidx, const double* __restrict__ Vval,
+                                             const double* __restrict__ E, double* __restrict__ Gt) {
+  const int c = (lb * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (c >= n) return;
   double acc[8];
 #pragma unroll
@@ -285,15 +354,19 @@ __global__ void k_split_G(int n, int k, const int* __restrict__ rowptr, const in
     if (lane == 0) Gt[(size_t)c * k + l] = t;
   }
 }
+__global__ void k_split_G(int n, int k, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                          const double* __restrict__ Vval, const double* __restrict__ E, double* __restrict__ Gt) {
+  split_G_body(blockIdx.x, n, k, rowptr, colidx, Vval, E, Gt);
+}
 
 // Split: partial sums of (G W_s)[l][q] over a chunk of rows c (FP32; grid.y = chunk)
 constexpr int SPLIT_CHUNKS = 16;
 template <typename TW>
-__global__ void k_split_R_part(int n, int k, const double* __restrict__ Gt, const TW* __restrict__ Ws,
-                               float* __restrict__ part) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void split_R_part_body(int bx, int by, int n, int k, const double* __restrict__ Gt,
+                                                  const TW* __restrict__ Ws, float* __restrict__ part) {
+  const int q = bx * blockDim.x + threadIdx.x;
   const int rows = (n + SPLIT_CHUNKS - 1) / SPLIT_CHUNKS;
-  const int c0 = blockIdx.y * rows, c1 = min(n, c0 + rows);
+  const int c0 = by * rows, c1 = min(n, c0 + rows);
   if (q >= n) return;
   float acc[8];
 #pragma unroll
@@ -306,14 +379,20 @@ __global__ void k_split_R_part(int n, int k, const double* __restrict__ Gt, cons
   }
 #pragma unroll
   for (int l = 0; l < 8; ++l)
-    if (l < k) part[((size_t)blockIdx.y * k + l) * n + q] = acc[l];
+    if (l < k) part[((size_t)by * k + l) * n + q] = acc[l];
+}
+template <typename TW>
+__global__ void k_split_R_part(int n, int k, const double* __restrict__ Gt, const TW* __restrict__ Ws,
+                               float* __restrict__ part) {
+  split_R_part_body<TW>(blockIdx.x, blockIdx.y, n, k, Gt, Ws, part);
 }
 // R[l][q] = lambda_l sum_chunks part;  Q[l][l2] = lambda_l lambda_l2 sum_c G[l][c] E[l2][c]
 // (the Q block is formed by the first k * k warps of the grid)
-__global__ void k_split_R_Q(int n, int k, const float* __restrict__ part, const double* __restrict__ lam,
-                            const double* __restrict__ Gt, const double* __restrict__ E, float* __restrict__ R,
-                            double* __restrict__ Q) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void split_R_Q_body(int lb, int n, int k, const float* __restrict__ part,
+                                               const double* __restrict__ lam, const double* __restrict__ Gt,
+                                               const double* __restrict__ E, float* __restrict__ R,
+                                               double* __restrict__ Q) {
+  const int t = lb * blockDim.x + threadIdx.x;
   if (t < n * k) {
     const int l = t / n, q = t % n;
     float s = 0.f;
@@ -329,6 +408,11 @@ __global__ void k_split_R_Q(int n, int k, const float* __restrict__ part, const 
     if (lane == 0) Q[l * k + l2] = lam[l] * lam[l2] * s;
   }
 }
+__global__ void k_split_R_Q(int n, int k, const float* __restrict__ part, const double* __restrict__ lam,
+                            const double* __restrict__ Gt, const double* __restrict__ E, float* __restrict__ R,
+                            double* __restrict__ Q) {
+  split_R_Q_body(blockIdx.x, n, k, part, lam, Gt, E, R, Q);
+}
 
 // W_s = W - E^T diag(lam) E into Ws (n x n FP64)
 __global__ void k_split_Ws(int n, int k, const double* __restrict__ W, const double* __restrict__ E,
@@ -339,6 +423,63 @@ __global__ void k_split_Ws(int n, int k, const double* __restrict__ W, const dou
   double v = W[t];
   for (int l = 0; l < k; ++l) v = fma(-lam[l] * E[(size_t)l * n + a], E[(size_t)l * n + b], v);
   Ws[t] = v;
+}
+
+// Batched FP32 forms: the same bodies over the same per-problem partitions as
+// the single-problem launches (problems in an FP64 sweep return at once).
+constexpr int BATCH_SPMM_LP_R = 8;
+__global__ void __launch_bounds__(256) kb_split_G(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active || !D.lp || D.ks == 0) return;
+  split_G_body(blockIdx.x - off[i], D.n, D.ks, D.rowptr, D.colidx, D.Vval, D.Etop, D.mvG);
+}
+__global__ void __launch_bounds__(128) kb_split_R_part(const BDesc* __restrict__ desc, const int* __restrict__ off,
+                                                       int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active || !D.lp || D.ks == 0) return;
+  const int lb = blockIdx.x - off[i], gx = (D.n + 127) / 128;
+  split_R_part_body<float>(lb % gx, lb / gx, D.n, D.ks, D.mvG, D.W32, D.mvPart);
+}
+__global__ void __launch_bounds__(256) kb_split_R_Q(const BDesc* __restrict__ desc, const int* __restrict__ off,
+                                                    int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active || !D.lp || D.ks == 0) return;
+  split_R_Q_body(blockIdx.x - off[i], D.n, D.ks, D.mvPart, D.wtop, D.mvG, D.Etop, D.mvR, D.mvQ);
+}
+__global__ void __launch_bounds__(256) kb_spmm_lp(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  extern __shared__ float fsh[];
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active || !D.lp) return;
+  spmm_lp_body<float, BATCH_SPMM_LP_R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W32, D.T32, fsh);
+}
+__global__ void __launch_bounds__(256) kb_sddmm_lp(const BDesc* __restrict__ desc, const int* __restrict__ off,
+                                                   int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active || !D.lp) return;
+  sddmm_lp_body<float>(blockIdx.x - off[i], off[i + 1] - off[i], D.n, D.m, D.eptr, D.ep, D.eq, D.ecoef, D.W32,
+                       D.T32, D.pq, D.pp, D.part, D.ticket, D.scal + S_PQ, D.scal + S_RZ, D.scal + S_RZN, D.ks,
+                       D.Etop, D.mvR, D.mvQ);
+}
+int batch_blocks_split_G(int n) { return (int)cdiv((size_t)n * 32, 256); }
+int batch_blocks_split_R(int n) { return (int)cdiv(n, 128) * SPLIT_CHUNKS; }
+int batch_blocks_split_Q(int n, int k) { return (int)cdiv(std::max((size_t)n * k, (size_t)k * k * 32), 256); }
+int batch_blocks_spmm_lp(int n) { return (int)cdiv(n, BATCH_SPMM_LP_R); }
+void batch_launch_matvec_lp(cudaStream_t st, const BDesc* desc, const int* off_g, const int* off_r,
+                            const int* off_q, const int* off_spmm, const int* off_sddmm, int N, int nb_g, int nb_r,
+                            int nb_q, int nb_spmm, int nb_sddmm, int nmax) {
+  const size_t smem = (size_t)BATCH_SPMM_LP_R * nmax * sizeof(float);
+  allow_max_smem((const void*)kb_spmm_lp);
+  count_launch(5);
+  kb_split_G<<<nb_g, 256, 0, st>>>(desc, off_g, N);
+  kb_split_R_part<<<nb_r, 128, 0, st>>>(desc, off_r, N);
+  kb_split_R_Q<<<nb_q, 256, 0, st>>>(desc, off_q, N);
+  kb_spmm_lp<<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N);
+  kb_sddmm_lp<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
 }
 
 // Reduced-precision copy of W, or of W_s when a preconditioner with top

@@ -107,6 +107,16 @@ __global__ void kb_any_active(const BDesc* __restrict__ desc, int N, cudaGraphCo
   __syncthreads();
   if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
+// Host-driven form (no graph): the flag is read back after every iteration.
+__global__ void kb_any_active_flag(const BDesc* __restrict__ desc, int N, int* flag) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+    if (desc[i].active) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = any;
+}
 int batch_blocks_vec(int m) { return (int)std::min(cdiv(m, 256), 2048u); }
 void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb) {
   count_launch();
@@ -116,9 +126,10 @@ void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, i
   count_launch();
   kb_pcg_p<<<nb, 256, 0, st>>>(desc, off, N);
 }
-void batch_launch_any(cudaStream_t st, const BDesc* desc, int N, cudaGraphConditionalHandle cond) {
+void batch_launch_any(cudaStream_t st, const BDesc* desc, int N, cudaGraphConditionalHandle cond, int* flag) {
   count_launch();
-  kb_any_active<<<1, 256, 0, st>>>(desc, N, cond);
+  if (flag) kb_any_active_flag<<<1, 256, 0, st>>>(desc, N, flag);
+  else kb_any_active<<<1, 256, 0, st>>>(desc, N, cond);
 }
 
 __global__ void k_pcg_init(double* scal, double rtol, int maxit) {

@@ -25,19 +25,24 @@ def _instances():
     return [si.mc_instance(s["p"], s["q"], s["r"], s["m"], s["seed"]) for s in specs]
 
 
-def test_batch_equals_alone():
-    from paper_1703_10973_gb300 import SDPBatch, SDPProblem
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_equals_alone(prec):
+    from paper_1703_10973_gb300 import SDPBatch, SDPProblem, default_params
+    params = default_params(prec=prec)
     insts = _instances()
     alone = []
     for d in insts:
-        with SDPProblem.from_data(d) as p:
+        with SDPProblem.from_data(d, params=params) as p:
             r = p.solve()
             alone.append((r, p.get_solution()))
     streams = [torch.cuda.Stream() for _ in insts]
-    probs = [SDPProblem.from_data(d, stream=s.cuda_stream) for d, s in zip(insts, streams)]
+    probs = [SDPProblem.from_data(d, params=params, stream=s.cuda_stream) for d, s in zip(insts, streams)]
     with SDPBatch(probs) as b:
         res = b.solve()
         sols = [p.get_solution() for p in probs]
+        stages = b.stage_seconds()
+    assert set(stages) == set(SDPBatch.STAGES) and all(v >= 0.0 for v in stages.values())
+    assert stages["pcg_pred"] > 0.0 and stages["nt_precond"] > 0.0
     for p in probs:
         p.close()
     for (ra, sa), rb, sb in zip(alone, res, sols):
@@ -52,9 +57,25 @@ def test_batch_rejects_unsupported_precision():
     from paper_1703_10973_gb300 import SDPBatch, SDPProblem, default_params
     from paper_1703_10973_gb300._lib import SDPError
     d = _instances()[0]
-    with SDPProblem.from_data(d, params=default_params(prec="fp32")) as p:
+    with SDPProblem.from_data(d, params=default_params(prec="bf16")) as p:
         with pytest.raises(SDPError):
             SDPBatch([p])
+
+
+def test_batch_mixed_precisions_match_oracle():
+    """FP32 and FP64 problems in one batch; each reaches the oracle's optimum."""
+    from oracle import sdp_oracle as o
+    from paper_1703_10973_gb300 import SDPBatch, SDPProblem, default_params
+    insts = _instances()[1:4]
+    precs = ["fp32", "fp64", "fp32"]
+    probs = [SDPProblem.from_data(d, params=default_params(prec=pr)) for d, pr in zip(insts, precs)]
+    with SDPBatch(probs) as b:
+        res = b.solve()
+    for d, p, r in zip(insts, probs, res):
+        P = o.Problem.from_data(d)
+        ref = o.ipm_solve(P)
+        assert r["converged"] and abs(r["obj_p"] - ref.obj_p) <= 1e-6 * abs(ref.obj_p)
+        p.close()
 
 
 def test_batch_matches_oracle():
@@ -72,3 +93,24 @@ def test_batch_matches_oracle():
         cert = o.kkt_certificate(P, X, y, S)
         assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6
         p.close()
+
+
+def test_batch_host_loop_equals_graph():
+    """pcg_graph = 0 drives the same batched kernels from the host: identical iterates."""
+    from paper_1703_10973_gb300 import SDPBatch, SDPProblem, default_params
+    insts = _instances()[:3]
+    out = []
+    for g in (1, 0):
+        params = default_params(pcg_graph=g)
+        probs = [SDPProblem.from_data(d, params=params) for d in insts]
+        with SDPBatch(probs) as b:
+            res = b.solve()
+            out.append((res, [p.get_solution() for p in probs]))
+        for p in probs:
+            p.close()
+    (r1, s1), (r0, s0) = out
+    for a, c in zip(r1, r0):
+        assert a["iters"] == c["iters"] and a["pcg_iters_total"] == c["pcg_iters_total"] and a["obj_p"] == c["obj_p"]
+    for a, c in zip(s1, s0):
+        for xa, xc in zip(a, c):
+            assert np.array_equal(xa, xc)
