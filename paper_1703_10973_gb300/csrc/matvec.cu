@@ -36,11 +36,6 @@ __device__ __forceinline__ double wsum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ float wsum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // ---------------------------------------------------------------------------
 // K0: V values from v (gather form, no atomics)
@@ -176,38 +171,60 @@ __global__ void __launch_bounds__(256) k_spmm_wv_lp(int n, const int* __restrict
 // ---------------------------------------------------------------------------
 // K2: per-constraint gather of W[p,:] . T[q,:]
 // ---------------------------------------------------------------------------
+// A warp serves SDDMM_G constraints, SDDMM_L = 32 / SDDMM_G lanes each: the
+// cross-lane sums then cost log2(SDDMM_L) shuffle-adds per SDDMM_G constraints
+// instead of five per constraint, which matters on a GPU whose FP64 pipe is
+// the bound; the group's lanes read a row segment of SDDMM_L consecutive
+// doubles, and the SDDMM_G groups of a warp read SDDMM_G rows at once.
 // With dv != nullptr the kernel also forms dv . Hv (one deterministic grid
 // reduction into *dout; PCG's p . Hp), first moving *pro_src to *pro_dst.
+constexpr int SDDMM_G = 4;
+constexpr int SDDMM_L = 32 / SDDMM_G;
+constexpr int SDDMM_PER_BLOCK = (256 / 32) * SDDMM_G;   // constraints per 256-thread block
+__device__ __forceinline__ double gsum_d(double v) {
+#pragma unroll
+  for (int o = SDDMM_L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float gsum_f(float v) {
+#pragma unroll
+  for (int o = SDDMM_L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 __device__ __forceinline__ void sddmm_f64_body(int lb, int nb, int n, int m, const int* __restrict__ eptr,
                                                const int* __restrict__ ep, const int* __restrict__ eq,
                                                const double* __restrict__ ecoef, const double* __restrict__ W,
                                                const double* __restrict__ T, double* __restrict__ Hv,
                                                const double* __restrict__ dv, double* dpart, unsigned int* ticket,
                                                double* dout, double* pro_dst, const double* pro_src) {
-  const int i = (lb * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  const int warp = (lb * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  const int gl = lane % SDDMM_L;
+  const int i = warp * SDDMM_G + lane / SDDMM_L;
+  const int e0 = (i < m) ? eptr[i] : 0, cnt = (i < m) ? eptr[i + 1] - e0 : 0;
+  const int maxcnt = __reduce_max_sync(0xffffffffu, cnt);
   double acc = 0.0;
-  if (i < m) {
-    for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
-      const double* wp = W + (size_t)ep[e] * n;
-      const double* tq = T + (size_t)eq[e] * n;
-      double s = 0.0;
-      int l = lane;
-      for (; l + 96 < n; l += 128) {   // four loads of each row in flight per lane
-        const double w0 = wp[l], w1 = wp[l + 32], w2 = wp[l + 64], w3 = wp[l + 96];
-        const double t0 = tq[l], t1 = tq[l + 32], t2 = tq[l + 64], t3 = tq[l + 96];
+  for (int t = 0; t < maxcnt; ++t) {
+    double s = 0.0;
+    if (t < cnt) {
+      const double* wp = W + (size_t)ep[e0 + t] * n;
+      const double* tq = T + (size_t)eq[e0 + t] * n;
+      int l = gl;
+      for (; l + 3 * SDDMM_L < n; l += 4 * SDDMM_L) {   // four loads of each row in flight per lane
+        const double w0 = wp[l], w1 = wp[l + SDDMM_L], w2 = wp[l + 2 * SDDMM_L], w3 = wp[l + 3 * SDDMM_L];
+        const double t0 = tq[l], t1 = tq[l + SDDMM_L], t2 = tq[l + 2 * SDDMM_L], t3 = tq[l + 3 * SDDMM_L];
         s = fma(w0, t0, s);
         s = fma(w1, t1, s);
         s = fma(w2, t2, s);
         s = fma(w3, t3, s);
       }
-      for (; l < n; l += 32) s = fma(wp[l], tq[l], s);
-      acc = fma(ecoef[e], s, acc);
+      for (; l < n; l += SDDMM_L) s = fma(wp[l], tq[l], s);
     }
-    acc = wsum_d(acc);
-    if (lane == 0) Hv[i] = acc;
+    s = gsum_d(s);   // every lane of the group holds the dot
+    if (t < cnt) acc = fma(ecoef[e0 + t], s, acc);
   }
+  if (i < m && gl == 0) Hv[i] = acc;
   if (dv) {
-    const double c = (i < m && lane == 0) ? dv[i] * acc : 0.0;
+    const double c = (i < m && gl == 0) ? dv[i] * acc : 0.0;
     double tot;
     if (lb_reduce(c, dpart, ticket, &tot, lb, nb)) {
       if (pro_dst) *pro_dst = *pro_src;
@@ -253,7 +270,7 @@ __global__ void __launch_bounds__(256) kb_sddmm(const BDesc* __restrict__ desc, 
 }
 int batch_blocks_assemble(int nnzV) { return (int)cdiv(nnzV, 256); }
 int batch_blocks_spmm(int n) { return (int)cdiv(n, BATCH_SPMM_R); }
-int batch_blocks_sddmm(int m) { return (int)cdiv((size_t)m * 32, 256); }
+int batch_blocks_sddmm(int m) { return (int)cdiv(m, SDDMM_PER_BLOCK); }
 void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm, const int* off_spmm,
                          const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax) {
   const size_t smem = (size_t)BATCH_SPMM_R * nmax * sizeof(double);
@@ -273,43 +290,52 @@ __device__ __forceinline__ void sddmm_lp_body(int lb, int nb, int n, int m, cons
                                               double* dout, double* pro_dst, const double* pro_src, int k,
                                               const double* __restrict__ E, const float* __restrict__ R,
                                               const double* __restrict__ Q) {
-  const int i = (lb * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  const int warp = (lb * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  const int gl = lane % SDDMM_L;
+  const int i = warp * SDDMM_G + lane / SDDMM_L;
+  const int e0 = (i < m) ? eptr[i] : 0, cnt = (i < m) ? eptr[i + 1] - e0 : 0;
+  const int maxcnt = __reduce_max_sync(0xffffffffu, cnt);
   double hv = 0.0;
-  if (i < m) {
-    for (int e = eptr[i]; e < eptr[i + 1]; ++e) {
-      const int p = ep[e], q = eq[e];
+  for (int t = 0; t < maxcnt; ++t) {
+    const bool on = t < cnt;
+    const int p = on ? ep[e0 + t] : 0, q = on ? eq[e0 + t] : 0;
+    float s = 0.f;
+    if (on) {
       const TW* wp = W + (size_t)p * n;
       const float* tq = T + (size_t)q * n;
-      float s = 0.f;
-      int l = lane;
-      for (; l + 96 < n; l += 128) {
-        const float w0 = tof<TW>(wp[l]), w1 = tof<TW>(wp[l + 32]), w2 = tof<TW>(wp[l + 64]),
-                    w3 = tof<TW>(wp[l + 96]);
-        const float t0 = tq[l], t1 = tq[l + 32], t2 = tq[l + 64], t3 = tq[l + 96];
+      int l = gl;
+      for (; l + 3 * SDDMM_L < n; l += 4 * SDDMM_L) {
+        const float w0 = tof<TW>(wp[l]), w1 = tof<TW>(wp[l + SDDMM_L]), w2 = tof<TW>(wp[l + 2 * SDDMM_L]),
+                    w3 = tof<TW>(wp[l + 3 * SDDMM_L]);
+        const float t0 = tq[l], t1 = tq[l + SDDMM_L], t2 = tq[l + 2 * SDDMM_L], t3 = tq[l + 3 * SDDMM_L];
         s = fmaf(w0, t0, s);
         s = fmaf(w1, t1, s);
         s = fmaf(w2, t2, s);
         s = fmaf(w3, t3, s);
       }
-      for (; l < n; l += 32) s = fmaf(tof<TW>(wp[l]), tq[l], s);
-      double v = (double)wsum_f(s);
-      if (k > 0 && lane == 0) {
-        // low-rank terms of the split, in FP64
-        for (int l = 0; l < k; ++l) {
-          const double epl = E[(size_t)l * n + p], eql = E[(size_t)l * n + q];
-          v = fma(epl, (double)R[(size_t)l * n + q], v);
-          v = fma(eql, (double)R[(size_t)l * n + p], v);
-          double t = 0.0;
-          for (int l2 = 0; l2 < k; ++l2) t = fma(Q[l * k + l2], E[(size_t)l2 * n + q], t);
-          v = fma(epl, t, v);
-        }
-      }
-      hv = fma(ecoef[e], v, hv);
+      for (; l < n; l += SDDMM_L) s = fmaf(tof<TW>(wp[l]), tq[l], s);
     }
-    if (lane == 0) Hv[i] = hv;
+    double v = (double)gsum_f(s);
+    if (k > 0) {
+      // low-rank terms of the split, in FP64, lane l of the group taking term l
+      // (k <= SDDMM_L):  E[l][p] R[l][q] + E[l][q] R[l][p] + E[l][p] (Q E)[l][q]
+      double tl = 0.0;
+      if (on && gl < k) {
+        const int l = gl;
+        const double epl = E[(size_t)l * n + p], eql = E[(size_t)l * n + q];
+        double qe = 0.0;
+        for (int l2 = 0; l2 < k; ++l2) qe = fma(Q[l * k + l2], E[(size_t)l2 * n + q], qe);
+        tl = epl * (double)R[(size_t)l * n + q];
+        tl = fma(eql, (double)R[(size_t)l * n + p], tl);
+        tl = fma(epl, qe, tl);
+      }
+      v += gsum_d(tl);
+    }
+    if (on) hv = fma(ecoef[e0 + t], v, hv);
   }
+  if (i < m && gl == 0) Hv[i] = hv;
   if (dv) {
-    const double c = (i < m && lane == 0) ? dv[i] * hv : 0.0;
+    const double c = (i < m && gl == 0) ? dv[i] * hv : 0.0;
     double tot;
     if (lb_reduce(c, dpart, ticket, &tot, lb, nb)) {
       if (pro_dst) *pro_dst = *pro_src;
@@ -371,6 +397,7 @@ __device__ __forceinline__ void split_R_part_body(int bx, int by, int n, int k, 
   float acc[8];
 #pragma unroll
   for (int l = 0; l < 8; ++l) acc[l] = 0.f;
+#pragma unroll 4
   for (int c = c0; c < c1; ++c) {
     const float w = tof<TW>(Ws[(size_t)c * n + q]);
 #pragma unroll
@@ -571,7 +598,7 @@ sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec, do
       default: launch_spmm_f64<1>(h, h->Vval); break;
     }
     count_launch();
-    k_sddmm_f64<<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(n, h->m, h->eptr, h->ep, h->eq, h->ecoef,
+    k_sddmm_f64<<<cdiv(h->m, SDDMM_PER_BLOCK), 256, 0, h->stream>>>(n, h->m, h->eptr, h->ep, h->eq, h->ecoef,
                                                                      h->W, h->T, Hv, dv, h->pcg_part,
                                                                      h->pcg_ticket, dot_out, pro_dst, pro_src);
   } else if (prec == SDP_FP32 || prec == SDP_BF16) {
@@ -601,7 +628,7 @@ sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec, do
       default: launch_spmm_lp<float, 1>(h, h->Vval, h->W32); break;
     }
     count_launch();
-    k_sddmm_lp<float><<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(
+    k_sddmm_lp<float><<<cdiv(h->m, SDDMM_PER_BLOCK), 256, 0, h->stream>>>(
         n, h->m, h->eptr, h->ep, h->eq, h->ecoef, h->W32, h->T32, Hv, dv, h->pcg_part, h->pcg_ticket, dot_out,
         pro_dst, pro_src, h->W32_key >= 0 ? h->kpc : 0, h->Etop, h->mv_R, h->mv_Q);
   } else if (prec == SDP_BF16) {
@@ -612,7 +639,7 @@ sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec, do
       default: launch_spmm_lp<__nv_bfloat16, 1>(h, h->Vval, h->W16); break;
     }
     count_launch();
-    k_sddmm_lp<__nv_bfloat16><<<cdiv((size_t)h->m * 32, 256), 256, 0, h->stream>>>(
+    k_sddmm_lp<__nv_bfloat16><<<cdiv(h->m, SDDMM_PER_BLOCK), 256, 0, h->stream>>>(
         n, h->m, h->eptr, h->ep, h->eq, h->ecoef, h->W16, h->T32, Hv, dv, h->pcg_part, h->pcg_ticket, dot_out,
         pro_dst, pro_src, h->W16_key >= 0 ? h->kpc : 0, h->Etop, h->mv_R, h->mv_Q);
   } else if (prec != SDP_FP64) {
