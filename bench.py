@@ -258,7 +258,7 @@ def run(args):
     if args.batched_launch:
         from paper_1703_10973_gb300 import SDPBatch
         bstream = torch.cuda.Stream()
-        batch = SDPBatch(probs, stream=bstream.cuda_stream)
+        batch = SDPBatch(probs, stream=bstream.cuda_stream, groups=args.batch_groups)
 
     def run_batch(start_event=None):
         """Solve every instance once; stream s handles instances s, s+S, ...  Returns per-solve ms."""
@@ -405,7 +405,7 @@ def run(args):
                 from paper_1703_10973_gb300 import SDPBatch
                 ps = [SDPProblem.from_data(insts[i], params=params, stream=streams[i].cuda_stream)
                       for i in range(len(insts))]
-                with SDPBatch(ps, stream=bstream.cuda_stream) as b2:
+                with SDPBatch(ps, stream=bstream.cuda_stream, groups=args.batch_groups) as b2:
                     b2.solve(allow_maxit=True)
                 for i, p2 in enumerate(ps):
                     X, y = outs[i]
@@ -440,6 +440,7 @@ def run(args):
                 "data": "synthetic",
                 "config": {"workload": desc, "instances": len(insts), "streams": nstreams, "prec": args.prec, "pcg_loop": "graph" if args.pcg_graph else "host",
                            "batched_launch": bool(args.batched_launch),
+                           "batch_groups": args.batch_groups if args.batched_launch else None,
                            "parallelism": f"replicas{ws}", "l2_flush": True, "converged": converged,
                            "ipm_iters_mean": float(np.mean(ipm_iters)),
                            "pcg_iters_per_solve_mean": float(np.mean(pcg_iters)),
@@ -527,6 +528,8 @@ def main():
                     help="kernel class for the roofline object; auto = the one with the most device time")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-groups", type=int, default=0,
+                    help="lockstep groups solved concurrently (batched mode; 0 = pairs)")
     ap.add_argument("--batched-launch", type=int, default=1, choices=[0, 1],
                     help="1: solve the batch in lockstep with one launch per PCG step for all problems; "
                          "0: independent problems on --streams streams")

@@ -250,6 +250,14 @@ sdp_status sdp_batch_create(sdp_problem* const* problems, int count, void* cuda_
 sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results);
 const char* sdp_batch_last_error(const sdp_batch* b);
 void sdp_batch_destroy(sdp_batch* b);
+/* Lockstep groups of a batch (default 0 = pairs: ceil(count / 2) groups).
+ * sdp_batch_solve deals the problems, largest first, round-robin into the
+ * groups and solves every group as its own lockstep batch on its own stream
+ * and host thread, so that one group's dense phases overlap another group's
+ * batched PCG.  1 = all problems in one lockstep.  Results do not depend on
+ * the grouping (each problem's iterates are the same as alone).
+ * SDP_ERR_ARG for a NULL batch or groups < 0. */
+sdp_status sdp_batch_set_groups(sdp_batch* b, int groups);
 /* Host wall-clock seconds the last sdp_batch_solve spent in each stage, summed
  * over its iterations: out[0] residuals + NT scaling + preconditioner (all
  * problems), out[1] predictor PCG (batched), out[2] predictor step lengths and
@@ -257,7 +265,8 @@ void sdp_batch_destroy(sdp_batch* b);
  * lengths and the checked update; out[5] the part of out[1] + out[3] spent in
  * the batched graph launches, out[6] the number of those launches (PCG sweeps
  * of the batch), out[7] the batched PCG iterations they ran (per launch, the
- * most any problem ran).  out: 8 doubles.  SDP_ERR_ARG for NULL. */
+ * most any problem ran).  With groups, out[0..5] are the slowest group's and
+ * out[6..7] the sum over groups.  out: 8 doubles.  SDP_ERR_ARG for NULL. */
 sdp_status sdp_batch_stage_seconds(const sdp_batch* b, double* out);
 
 /*

@@ -108,6 +108,7 @@ SIGNATURES = {
     "sdp_batch_last_error": (C.c_char_p, [_P]),
     "sdp_batch_destroy": (None, [_P]),
     "sdp_batch_stage_seconds": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "sdp_batch_set_groups": (C.c_int, [_P, C.c_int]),
     "sdp_destroy": (None, [_P]),
     "sdp_status_str": (C.c_char_p, [C.c_int]),
     "sdp_last_error": (C.c_char_p, [_P]),

@@ -250,7 +250,7 @@ def hessian_matvec_static(n, m, Ak, Ai, Aj, Av, W, v, out=None, stream=None):
 class SDPBatch:
     """sdp_batch_*: solve several SDPProblem objects in lockstep with batched PCG launches."""
 
-    def __init__(self, problems, stream=None):
+    def __init__(self, problems, stream=None, groups=0):
         self.lib = L.load()
         self.problems = list(problems)
         arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
@@ -261,6 +261,9 @@ class SDPBatch:
         if st != L.SDP_OK:
             raise L.SDPError(st, f"sdp_batch_create: {self.lib.sdp_status_str(st).decode()}")
         self.b = b
+        st = self.lib.sdp_batch_set_groups(self.b, int(groups))
+        if st != L.SDP_OK:
+            raise L.SDPError(st, f"sdp_batch_set_groups: {self.lib.sdp_status_str(st).decode()}")
 
     def solve(self, allow_maxit=False):
         res = (L.sdp_result * len(self.problems))()

@@ -55,6 +55,10 @@ struct sdp_batch {
   int64_t body_launches = 0;
   double stage_s[8] = {};             // wall seconds per stage of the last solve, then
                                       // graph seconds, graph launches, batched iterations
+  int groups = 0;                     // lockstep groups solved concurrently (0: pairs)
+  std::vector<sdp_batch*> child;      // one batch per group when groups > 1
+  std::vector<std::vector<int>> members;   // problems of each group
+  std::vector<cudaStream_t> child_streams;
   std::string last_error;
 };
 
@@ -264,6 +268,30 @@ static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::v
   return SDP_OK;
 }
 
+sdp_status self_batch_newton(sdp_problem* h, int* its, double* rr, bool* used) {
+  *used = false;
+  std::string why;
+  if (h->prm.pcg_graph == 0 || !batch_supported(h, &why)) return SDP_OK;
+  if (!h->self_batch) {
+    sdp_problem* one[1] = {h};
+    if (sdp_batch_create(one, 1, h->stream, &h->self_batch) != SDP_OK) return SDP_OK;   // old path
+  }
+  *used = true;
+  std::vector<int> idx{0}, it(1, 0);
+  std::vector<double> r(1, 0.0);
+  std::vector<sdp_status> st(1, SDP_OK);
+  ktimer_begin(h->stream, "pcg");
+  const sdp_status s = batch_newton(h->self_batch, idx, it, r, st);
+  ktimer_end(h->stream, "pcg", 0.0, 0.0);
+  if (s != SDP_OK) {
+    h->last_error = h->self_batch->last_error;
+    return s;
+  }
+  *its = it[0];
+  *rr = r[0];
+  return st[0];
+}
+
 // Runs fn(i) for every listed problem on its own host thread.
 template <typename F>
 static void parallel_for(const std::vector<int>& idx, F fn) {
@@ -299,8 +327,80 @@ extern "C" sdp_status sdp_batch_create(sdp_problem* const* hs, int count, void* 
   return SDP_OK;
 }
 
+static sdp_status batch_solve_lockstep(sdp_batch* b, sdp_result* results);
+
+// Groups: problems sorted by order, largest first, dealt round-robin, so that
+// the groups carry similar work; each group is a lockstep batch of its own on
+// its own stream and host thread.  One group's dense phases then overlap
+// another group's batched PCG instead of all problems alternating together
+// between latency-bound phases and the throughput-bound PCG.
+static sdp_status batch_make_groups(sdp_batch* b, int G) {
+  const int N = (int)b->hs.size();
+  std::vector<int> order(N);
+  for (int i = 0; i < N; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->hs[x]->n > b->hs[y]->n; });
+  b->members.assign(G, {});
+  for (int t = 0; t < N; ++t) b->members[t % G].push_back(order[t]);
+  for (int g = 0; g < G; ++g) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      b->last_error = "sdp_batch: stream creation failed";
+      return SDP_ERR_CUDA;
+    }
+    b->child_streams.push_back(s);
+    std::vector<sdp_problem*> hs;
+    for (int i : b->members[g]) hs.push_back(b->hs[i]);
+    sdp_batch* c = nullptr;
+    const sdp_status st = sdp_batch_create(hs.data(), (int)hs.size(), s, &c);
+    if (st != SDP_OK) {
+      b->last_error = "sdp_batch: group creation failed";
+      return st;
+    }
+    c->groups = 1;
+    b->child.push_back(c);
+  }
+  return SDP_OK;
+}
+
 extern "C" sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results) {
   if (!b) return SDP_ERR_ARG;
+  const int N = (int)b->hs.size();
+  const int G = std::min(N, b->groups > 0 ? b->groups : (N + 1) / 2);
+  if (G <= 1) return batch_solve_lockstep(b, results);
+  if ((int)b->child.size() != G) {
+    for (sdp_batch* c : b->child) sdp_batch_destroy(c);
+    for (cudaStream_t s : b->child_streams) cudaStreamDestroy(s);
+    b->child.clear();
+    b->child_streams.clear();
+    SDP_TRY(batch_make_groups(b, G));
+  }
+  std::vector<std::vector<sdp_result>> res(G);
+  std::vector<sdp_status> st(G, SDP_OK);
+  std::vector<std::thread> th;
+  for (int g = 0; g < G; ++g) {
+    res[g].resize(b->members[g].size());
+    th.emplace_back([&, g] { st[g] = sdp_batch_solve(b->child[g], res[g].data()); });
+  }
+  for (auto& t : th) t.join();
+  for (double& x : b->stage_s) x = 0.0;
+  sdp_status worst = SDP_OK;
+  for (int g = 0; g < G; ++g) {
+    for (size_t t = 0; t < b->members[g].size(); ++t)
+      if (results) results[b->members[g][t]] = res[g][t];
+    for (int k = 0; k < 8; ++k)   // seconds: the slowest group; counts: all groups
+      b->stage_s[k] = (k < 6) ? std::max(b->stage_s[k], b->child[g]->stage_s[k]) : b->stage_s[k] + b->child[g]->stage_s[k];
+    if (st[g] == SDP_ERR_MAXIT && worst == SDP_OK) {
+      worst = SDP_ERR_MAXIT;
+    } else if (st[g] != SDP_OK && st[g] != SDP_ERR_MAXIT && (worst == SDP_OK || worst == SDP_ERR_MAXIT)) {
+      worst = st[g];   // the first hard error wins over an iteration limit
+      b->last_error = b->child[g]->last_error;
+    }
+  }
+  return worst;
+}
+
+static sdp_status batch_solve_lockstep(sdp_batch* b, sdp_result* results) {
   const int N = (int)b->hs.size();
   const auto t0 = std::chrono::steady_clock::now();
   std::vector<IpmStepState> s(N);
@@ -383,6 +483,12 @@ extern "C" sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results) {
 
 extern "C" const char* sdp_batch_last_error(const sdp_batch* b) { return b ? b->last_error.c_str() : ""; }
 
+extern "C" sdp_status sdp_batch_set_groups(sdp_batch* b, int groups) {
+  if (!b || groups < 0) return SDP_ERR_ARG;
+  b->groups = groups;
+  return SDP_OK;
+}
+
 extern "C" sdp_status sdp_batch_stage_seconds(const sdp_batch* b, double* out) {
   if (!b || !out) return SDP_ERR_ARG;
   for (int i = 0; i < 8; ++i) out[i] = b->stage_s[i];
@@ -398,5 +504,7 @@ extern "C" void sdp_batch_destroy(sdp_batch* b) {
   if (b->ddesc) cudaFree(b->ddesc);
   if (b->doff) cudaFree(b->doff);
   if (b->dflag) cudaFree(b->dflag);
+  for (sdp_batch* c : b->child) sdp_batch_destroy(c);
+  for (cudaStream_t s : b->child_streams) cudaStreamDestroy(s);
   delete b;
 }

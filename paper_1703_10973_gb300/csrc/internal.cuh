@@ -410,6 +410,7 @@ struct sdp_problem {
   cudaGraphExec_t pcg_exec = nullptr;
   int64_t pcg_key = -1;
   int64_t pcg_body_launches = 0;
+  sdp_batch* self_batch = nullptr;   // one-problem batch driving this handle's Newton solves
 
   // ---- PCG vectors ----
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr, *px = nullptr,
@@ -503,4 +504,10 @@ sdp_status ipm_phase_a(sdp_problem* h, IpmStepState* s, bool* done);
 sdp_status ipm_phase_b(sdp_problem* h, IpmStepState* s, int pcg_its, double pcg_rr);
 sdp_status ipm_phase_c(sdp_problem* h, IpmStepState* s, int pcg_its, double pcg_rr);
 sdp_status ipm_step_impl(sdp_problem* h, sdp_ipm_info* info);
+// The Newton system H dy = h->rhs of one problem through its one-problem batch
+// (batch.cu): the batched PCG graph is captured once per handle, where the
+// single-problem graph is captured again for every new preconditioner.
+// *used = false (nothing done) when the configuration is not batchable or the
+// PCG loop is host-driven (pcg_graph = 0).
+sdp_status self_batch_newton(sdp_problem* h, int* its, double* rr, bool* used);
 }  // namespace sdpgb

@@ -522,7 +522,10 @@ sdp_status ipm_phase_c(sdp_problem* h, IpmStepState* s, int its, double rr) {
 }
 
 static sdp_status newton_solve(sdp_problem* h, int* its, double* rr) {
-  sdp_status s = pcg_impl(h, h->rhs, h->dy, h->prm.pcg_rtol, h->prm.pcg_maxit, h->prm.prec, its, rr);
+  bool used = false;
+  sdp_status s = self_batch_newton(h, its, rr, &used);
+  if (used) return s;
+  s = pcg_impl(h, h->rhs, h->dy, h->prm.pcg_rtol, h->prm.pcg_maxit, h->prm.prec, its, rr);
   return (s == SDP_OK || s == SDP_ERR_MAXIT) ? SDP_OK : s;
 }
 

@@ -276,9 +276,9 @@ void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm,
   const size_t smem = (size_t)BATCH_SPMM_R * nmax * sizeof(double);
   allow_max_smem((const void*)kb_spmm);
   count_launch(3);
-  kb_assemble<<<nb_asm, 256, 0, st>>>(desc, off_asm, N);
-  kb_spmm<<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N);
-  kb_sddmm<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
+  if (nb_asm > 0) kb_assemble<<<nb_asm, 256, 0, st>>>(desc, off_asm, N);
+  if (nb_spmm > 0) kb_spmm<<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N);
+  if (nb_sddmm > 0) kb_sddmm<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
 }
 
 template <typename TW>
@@ -502,11 +502,11 @@ void batch_launch_matvec_lp(cudaStream_t st, const BDesc* desc, const int* off_g
   const size_t smem = (size_t)BATCH_SPMM_LP_R * nmax * sizeof(float);
   allow_max_smem((const void*)kb_spmm_lp);
   count_launch(5);
-  kb_split_G<<<nb_g, 256, 0, st>>>(desc, off_g, N);
-  kb_split_R_part<<<nb_r, 128, 0, st>>>(desc, off_r, N);
-  kb_split_R_Q<<<nb_q, 256, 0, st>>>(desc, off_q, N);
-  kb_spmm_lp<<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N);
-  kb_sddmm_lp<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
+  if (nb_g > 0) kb_split_G<<<nb_g, 256, 0, st>>>(desc, off_g, N);
+  if (nb_r > 0) kb_split_R_part<<<nb_r, 128, 0, st>>>(desc, off_r, N);
+  if (nb_q > 0) kb_split_R_Q<<<nb_q, 256, 0, st>>>(desc, off_q, N);
+  if (nb_spmm > 0) kb_spmm_lp<<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N);
+  if (nb_sddmm > 0) kb_sddmm_lp<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
 }
 
 // Reduced-precision copy of W, or of W_s when a preconditioner with top

@@ -120,11 +120,11 @@ __global__ void kb_any_active_flag(const BDesc* __restrict__ desc, int N, int* f
 int batch_blocks_vec(int m) { return (int)std::min(cdiv(m, 256), 2048u); }
 void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb) {
   count_launch();
-  kb_pcg_xr<<<nb, 256, 0, st>>>(desc, off, N);
+  if (nb > 0) kb_pcg_xr<<<nb, 256, 0, st>>>(desc, off, N);
 }
 void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb) {
   count_launch();
-  kb_pcg_p<<<nb, 256, 0, st>>>(desc, off, N);
+  if (nb > 0) kb_pcg_p<<<nb, 256, 0, st>>>(desc, off, N);
 }
 void batch_launch_any(cudaStream_t st, const BDesc* desc, int N, cudaGraphConditionalHandle cond, int* flag) {
   count_launch();

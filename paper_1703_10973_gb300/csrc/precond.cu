@@ -181,11 +181,11 @@ int batch_blocks_hat_u(int n) { return (int)cdiv((size_t)n * 32, 256); }
 int batch_blocks_tail(int m) { return (int)cdiv(m, 256); }
 void batch_launch_hat_u(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb) {
   count_launch();
-  kb_hat_u<<<nb, 256, 0, st>>>(desc, off, N);
+  if (nb > 0) kb_hat_u<<<nb, 256, 0, st>>>(desc, off, N);
 }
 void batch_launch_tail(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb) {
   count_launch();
-  kb_apply_tail<<<nb, 256, 0, st>>>(desc, off, N);
+  if (nb > 0) kb_apply_tail<<<nb, 256, 0, st>>>(desc, off, N);
 }
 
 __global__ void k_scale_ginv(int m, const double* __restrict__ ginv, const double* __restrict__ r, double s,

@@ -414,9 +414,16 @@ int batch_blocks_outR(int Rk) { return (int)cdiv(Rk, 128); }
 void batch_launch_core_solve(cudaStream_t st, const BDesc* desc, int N, const int* off_fwdP, int nb_fwdP,
                              const int* off_fwdR, int nb_fwdR, const int* off_gemv, int nb_gemv,
                              const int* off_outR, int nb_outR, const int* off_bwdP, int nb_bwdP) {
-  count_launch(2);
-  kb_fwdP<<<nb_fwdP, 128, 0, st>>>(desc, off_fwdP, N);
-  kb_fwdR<<<nb_fwdR, 256, 0, st>>>(desc, off_fwdR, N);
+  // a batch with no rows of a kind (e.g. no vertex outside the independent
+  // set) launches nothing for it: a grid of zero blocks is not a launch
+  if (nb_fwdP > 0) {
+    count_launch();
+    kb_fwdP<<<nb_fwdP, 128, 0, st>>>(desc, off_fwdP, N);
+  }
+  if (nb_fwdR > 0) {
+    count_launch();
+    kb_fwdR<<<nb_fwdR, 256, 0, st>>>(desc, off_fwdR, N);
+  }
   if (nb_gemv > 0) {
     count_launch(2);
     kb_gemv_lower<<<nb_gemv, 256, 0, st>>>(desc, off_gemv, N);
@@ -426,8 +433,10 @@ void batch_launch_core_solve(cudaStream_t st, const BDesc* desc, int N, const in
     count_launch();
     kb_outR<<<nb_outR, 128, 0, st>>>(desc, off_outR, N);
   }
-  count_launch();
-  kb_bwdP<<<nb_bwdP, 256, 0, st>>>(desc, off_bwdP, N);
+  if (nb_bwdP > 0) {
+    count_launch();
+    kb_bwdP<<<nb_bwdP, 256, 0, st>>>(desc, off_bwdP, N);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -83,6 +83,7 @@ extern "C" void sdp_destroy(sdp_problem* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
   }
+  if (h->self_batch) sdp_batch_destroy(h->self_batch);
   if (h->pcg_exec) cudaGraphExecDestroy(h->pcg_exec);
   if (h->pcg_graph) cudaGraphDestroy(h->pcg_graph);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);

@@ -27,17 +27,26 @@ def _instances():
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_batch_equals_alone(prec):
+    """Batched kernels under the batch graph, and a solve on its own (which runs
+    its Newton systems through a one-problem batch), both equal the
+    single-problem kernels driven from the host (pcg_graph = 0) bit for bit."""
     from paper_1703_10973_gb300 import SDPBatch, SDPProblem, default_params
     params = default_params(prec=prec)
     insts = _instances()
     alone = []
     for d in insts:
-        with SDPProblem.from_data(d, params=params) as p:
+        with SDPProblem.from_data(d, params=default_params(prec=prec, pcg_graph=0)) as p:
             r = p.solve()
             alone.append((r, p.get_solution()))
+        with SDPProblem.from_data(d, params=params) as p:
+            r1 = p.solve()
+            s1 = p.get_solution()
+        assert r1["iters"] == r["iters"] and r1["pcg_iters_total"] == r["pcg_iters_total"]
+        for xa, xb in zip(alone[-1][1], s1):
+            assert np.array_equal(xa, xb)
     streams = [torch.cuda.Stream() for _ in insts]
     probs = [SDPProblem.from_data(d, params=params, stream=s.cuda_stream) for d, s in zip(insts, streams)]
-    with SDPBatch(probs) as b:
+    with SDPBatch(probs, groups=1) as b:
         res = b.solve()
         sols = [p.get_solution() for p in probs]
         stages = b.stage_seconds()
@@ -112,5 +121,29 @@ def test_batch_host_loop_equals_graph():
     for a, c in zip(r1, r0):
         assert a["iters"] == c["iters"] and a["pcg_iters_total"] == c["pcg_iters_total"] and a["obj_p"] == c["obj_p"]
     for a, c in zip(s1, s0):
+        for xa, xc in zip(a, c):
+            assert np.array_equal(xa, xc)
+
+
+@pytest.mark.parametrize("groups", [0, 2, 5])
+def test_batch_groups_equal_one_lockstep(groups):
+    """Concurrent lockstep groups (0 = pairs) give every problem the same iterates."""
+    from paper_1703_10973_gb300 import SDPBatch, SDPProblem
+    insts = _instances()
+    out = []
+    for g in (1, groups):
+        streams = [torch.cuda.Stream() for _ in insts]
+        probs = [SDPProblem.from_data(d, stream=s.cuda_stream) for d, s in zip(insts, streams)]
+        with SDPBatch(probs, groups=g) as b:
+            res = b.solve()
+            out.append((res, [p.get_solution() for p in probs], b.stage_seconds()))
+        for p in probs:
+            p.close()
+    (r1, s1, _), (rg, sg, stg) = out
+    assert stg["graph_launches"] >= 1
+    for a, c in zip(r1, rg):
+        assert a["converged"] and c["converged"]
+        assert a["iters"] == c["iters"] and a["pcg_iters_total"] == c["pcg_iters_total"] and a["obj_p"] == c["obj_p"]
+    for a, c in zip(s1, sg):
         for xa, xc in zip(a, c):
             assert np.array_equal(xa, xc)
