@@ -262,6 +262,23 @@ def split_W(W, k, z_kind="chol"):
     return Split(tau=float(tau), lam=lam, V=V, U=U, W0=W0, Z=Z)
 
 
+def rank_estimate(W, kmax, eta):
+    """Adaptive rank of the implementation notes of Section V:
+    k~ = max{ i in {0, ..., kmax} : lambda_i(W) >= eta * lambda_{i+1}(W) },
+    eigenvalues of W in decreasing order (lambda_1 the largest).
+
+    Reading: lambda_0 = +inf, so i = 0 always qualifies and k~ >= 0; i is capped
+    at n - 1 so that lambda_{i+1} exists.  Prop. Weig gives lambda_k / lambda_{k+1}
+    in Theta(1/mu) for k = rank X*, so k~ tends to rank X* as mu -> 0.
+    """
+    lam = np.sort(np.linalg.eigvalsh(W))[::-1]
+    best = 0
+    for i in range(1, min(int(kmax), lam.size - 1) + 1):
+        if lam[i - 1] >= eta * lam[i]:
+            best = i
+    return best
+
+
 def UU_matvec(P: Problem, U, Z, X):
     """eq. (Umv a): (UU vec X)_i = A_i . (Z X U^T) for X in R^{n x k}."""
     return op_A(P, Z @ X @ U.T)

@@ -431,3 +431,65 @@ def test_max_step_is_boundary():
     a = o.max_step(X, dX)
     assert np.linalg.eigvalsh(X + 0.999 * a * dX)[0] > 0
     assert np.linalg.eigvalsh(X + 1.001 * a * dX)[0] < 0
+
+
+# ---------------------------------------------------------------------------
+# Adaptive rank k~ (Section V, implementation notes; Prop. Weig)
+# ---------------------------------------------------------------------------
+def _with_spectrum(lam_desc, seed=21):
+    n = len(lam_desc)
+    Q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((n, n)))
+    return (Q * np.asarray(lam_desc, dtype=float)) @ Q.T
+
+
+def test_rank_estimate_rule_on_known_spectra():
+    # the largest index with a ratio of at least eta wins, not the first or the biggest ratio
+    W = _with_spectrum([100.0, 90.0, 1.0, 0.9, 0.8, 0.7])
+    assert o.rank_estimate(W, kmax=4, eta=10.0) == 2
+    W = _with_spectrum([1000.0, 100.0, 10.0, 1.0, 0.5])
+    assert o.rank_estimate(W, kmax=4, eta=5.0) == 3
+    assert o.rank_estimate(W, kmax=2, eta=5.0) == 2       # kmax caps the index
+    assert o.rank_estimate(W, kmax=0, eta=5.0) == 0
+    # a flat spectrum has no gap: k~ = 0 (lambda_0 = +inf is the only qualifying index)
+    assert o.rank_estimate(3.0 * np.eye(6), kmax=5, eta=2.0) == 0
+    # kmax beyond n - 1 is harmless
+    W = _with_spectrum([8.0, 1.0, 1.0])
+    assert o.rank_estimate(W, kmax=10, eta=4.0) == 1
+
+
+def test_rank_estimate_equality_counts():
+    # lambda_i = eta * lambda_{i+1} exactly qualifies (>=); eigenvalues exact in binary
+    W = np.diag([16.0, 4.0, 1.0, 1.0])
+    assert o.rank_estimate(W, kmax=3, eta=4.0) == 2
+    assert o.rank_estimate(W, kmax=3, eta=4.5) == 0
+
+
+@pytest.mark.parametrize("spec,r", [(dict(p=20, q=20, r=1, m=200, seed=1), 1),
+                                    (dict(p=20, q=20, r=2, m=300, seed=13), 2)])
+def test_rank_estimate_finds_rank_at_the_optimum(spec, r):
+    """Prop. Weig: at the optimum of an exactly recovered completion, W has r eigenvalues
+    of order one and the rest of order mu, so k~ = r = rank X* (and the planted rank)."""
+    d = si.mc_instance(**spec)
+    P = o.Problem.from_data(d)
+    res = o.ipm_solve(P)
+    assert res.converged
+    assert _rel(o.mc_recovered(P, res.X), d.meta["M"]) <= 1e-5
+    W = o.nt_scaling(res.X, res.S)
+    assert o.rank_estimate(W, kmax=5, eta=10.0) == r
+    # at the start point W is a multiple of I: no gap yet
+    X0, _, S0 = o.start_point(P)
+    assert o.rank_estimate(o.nt_scaling(X0, S0), kmax=5, eta=10.0) == 0
+
+
+def test_rank_estimate_tracks_rank_of_X_when_recovery_fails():
+    """Too few samples: the SDP optimum has rank above the planted r; k~ follows rank X*,
+    the quantity Prop. Weig is about, not the planted rank."""
+    d = si.mc_instance(16, 16, 3, 180, 12)
+    P = o.Problem.from_data(d)
+    res = o.ipm_solve(P)
+    assert res.converged
+    lx = np.sort(np.linalg.eigvalsh(res.X))[::-1]
+    rank_x = int(np.sum(lx >= 1e-3 * lx[0]))
+    assert rank_x > 3
+    W = o.nt_scaling(res.X, res.S)
+    assert o.rank_estimate(W, kmax=6, eta=10.0) == rank_x
