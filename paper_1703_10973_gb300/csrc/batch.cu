@@ -123,12 +123,28 @@ static BDesc make_desc(sdp_problem* h, int active, int prec) {
 }
 
 // One PCG iteration of every active problem (the body of the batched loop).
-static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle cond, int* flag) {
+// fp64 (host loop only): per problem, 1 when it runs an FP64-matvec sweep this
+// iteration; the batched FP64 matvec is then timed as class "matvec_b" with the
+// algorithmic work of those problems (T = W V: 2 nnzV n flops; one length-n dot
+// per stored entry: 2 nent n; bytes: W and T once each, the sparse data).
+static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle cond, int* flag,
+                       const std::vector<char>* fp64 = nullptr) {
   const int N = (int)b->hs.size();
   const int* o = b->doff;
   auto off = [&](int kd) { return o + (size_t)kd * (N + 1); };
+  double fl = 0.0, by = 0.0;
+  if (fp64) {
+    for (int i = 0; i < N; ++i) {
+      if (!(*fp64)[i]) continue;
+      const sdp_problem* h = b->hs[i];
+      fl += 2.0 * h->nnzV * (double)h->n + 2.0 * h->nent * (double)h->n;
+      by += 16.0 * h->n * (double)h->n + 12.0 * h->nnzV + 16.0 * h->m;
+    }
+    ktimer_begin(st, "matvec_b");
+  }
   batch_launch_matvec(st, b->ddesc, off(BK_ASM), off(BK_SPMM), off(BK_SDDMM), N, b->total[BK_ASM],
                       b->total[BK_SPMM], b->total[BK_SDDMM], b->nmax);
+  if (fp64) ktimer_end(st, "matvec_b", fl, by);
   if (b->any_lp)   // same SDDMM partition (and reduction groups) as the FP64 form
     batch_launch_matvec_lp(st, b->ddesc, off(BK_SPLG), off(BK_SPLR), off(BK_SPLQ), off(BK_SPMM_LP), off(BK_SDDMM),
                            N, b->total[BK_SPLG], b->total[BK_SPLR], b->total[BK_SPLQ], b->total[BK_SPMM_LP],
@@ -155,7 +171,7 @@ static sdp_status batch_prepare(sdp_batch* b) {
   }
   cudaMemcpy(b->doff, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice);
   if (b->hs[0]->prm.pcg_graph == 0) {
-    if (cudaMalloc(&b->dflag, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&b->dflag, sizeof(int) * (N + 1)) != cudaSuccess) {
       cudaGetLastError();
       b->last_error = "sdp_batch: device allocation failed";
       return SDP_ERR_OOM;
@@ -236,13 +252,21 @@ static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::v
       return SDP_ERR_CUDA;
     }
     if (b->host_loop) {
-      for (int flag = 1; flag;) {
-        batch_body(b, b->stream, cudaGraphConditionalHandle{}, b->dflag);
-        if (cudaMemcpyAsync(&flag, b->dflag, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+      // flags[0]: some problem active; flags[1 + i]: problem i active (read back
+      // after every iteration, so each timed matvec knows its problems)
+      std::vector<int> flags(N + 1, 0);
+      std::vector<char> fp64(N, 0);
+      for (int i : running) fp64[i] = (S[i].prec == SDP_FP64);
+      for (;;) {
+        batch_body(b, b->stream, cudaGraphConditionalHandle{}, b->dflag, &fp64);
+        if (cudaMemcpyAsync(flags.data(), b->dflag, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, b->stream) !=
+                cudaSuccess ||
             cudaStreamSynchronize(b->stream) != cudaSuccess) {
           b->last_error = std::string("sdp_batch: batched PCG failed: ") + cudaGetErrorString(cudaGetLastError());
           return SDP_ERR_CUDA;
         }
+        if (!flags[0]) break;
+        for (int i = 0; i < N; ++i) fp64[i] = fp64[i] && flags[1 + i];
       }
     } else if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess) {
       b->last_error = std::string("sdp_batch: batched PCG failed: ") + cudaGetErrorString(cudaGetLastError());

@@ -475,7 +475,8 @@ void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm,
                          const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax);
 void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb);
 void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
-// flag != nullptr: write "some problem active" to *flag (host-driven loop) instead of the graph condition
+// flag != nullptr (host-driven loop): flag[0] = some problem active, flag[1 + i] = problem i
+// active, instead of setting the graph condition
 void batch_launch_any(cudaStream_t st, const BDesc* desc, int N, cudaGraphConditionalHandle cond, int* flag);
 void batch_launch_hat_u(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
 void batch_launch_tail(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);

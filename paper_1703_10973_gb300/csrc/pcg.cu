@@ -107,15 +107,19 @@ __global__ void kb_any_active(const BDesc* __restrict__ desc, int N, cudaGraphCo
   __syncthreads();
   if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
-// Host-driven form (no graph): the flag is read back after every iteration.
+// Host-driven form (no graph): flag[0] = some problem active, flag[1 + i] =
+// problem i active, read back after every iteration.
 __global__ void kb_any_active_flag(const BDesc* __restrict__ desc, int N, int* flag) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x)
-    if (desc[i].active) any = 1;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int a = desc[i].active ? 1 : 0;
+    flag[1 + i] = a;
+    if (a) any = 1;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) *flag = any;
+  if (threadIdx.x == 0) flag[0] = any;
 }
 int batch_blocks_vec(int m) { return (int)std::min(cdiv(m, 256), 2048u); }
 void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb) {
