@@ -174,7 +174,10 @@ sdp_status sdp_pcg_solve(sdp_problem* h, const double* r_dev, double* y_dev, dou
  * Newton directions, each from H dy = Rp - A(Rc) + A(W Rd W) solved by PCG;
  * step to step_frac of the boundary; update.  info may be NULL.  Returns
  * SDP_OK also when the point already satisfies the stopping test
- * (info->converged = 1, nothing changed).
+ * (info->converged = 1, nothing changed).  With the graph loop (pcg_graph = 1)
+ * and a batchable configuration (SDP_PRECOND_HAT, 1 <= k <= 8, SDP_FP64 or
+ * SDP_FP32) the two Newton systems run through a one-problem batch of this
+ * handle (its PCG graph is captured once); the iterates are the same.
  */
 sdp_status sdp_ipm_step(sdp_problem* h, sdp_ipm_info* info);
 
