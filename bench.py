@@ -1,32 +1,40 @@
-"""Benchmark: SDP solves/s and per-solve latency at 1e-6 relative duality gap.
+"""Benchmark: SDP solves/s and p50/p99 latency at 1e-6 relative duality gap, the
+mixed-precision form against the plain FP64 PCG method on the same GB300.
 
 Default workload ("batched"): the first 16 instances of the batched
 matrix-completion workload (p, q uniform in [50, 400], r uniform in {1..4},
 m = min(pq/2, ceil(3 r (p+q) ln(p+q))) uniform observations, seeds 4000..4015).
 One step solves all 16 SDPs, each from the interior-point start point to
 relative gap, primal and dual infeasibility <= 1e-6 with every Newton system
-solved by PCG to a 1e-8 true relative residual.  By default the 16 problems are
-advanced in lockstep (sdp_batch_solve): their dense phases on one stream and
-host thread each, and every PCG iteration of all 16 Newton systems as one
-sequence of batched launches under a CUDA graph.  --batched-launch 0 solves
-them as independent problems on --streams streams.  The problem data stay in
-HBM across steps; each solve resets its iterate on the device.
+solved to a 1e-8 FP64 true relative residual.  The problems are advanced in
+lockstep (sdp_batch_solve): their dense phases on one stream and host thread
+each, every PCG iteration of all their Newton systems as one sequence of batched
+launches under a CUDA graph.  The problem data stay in HBM across steps; each
+solve resets its iterate on the device; a 256 MB write flushes L2 between steps.
 
-`--workload C2` runs the single n = 1000, m = 8000, rank-2 instance instead; its
-nuclear-norm optimum has rank about 38, outside the low-rank regime the
-preconditioner is built for, and PCG stalls before 1e-6 (the line reports it).
+Two arms run on the same instances (--arms, default "fp32,fp64"): the mixed form
+(FP32 split matvec and FP32 core inverse inside PCG, FP64 refinement and FP64
+everything else) and the plain FP64 form.  The first arm is the headline `value`;
+`arms` carries both, each with solves/s, per-problem p50/p99 latency (start of
+the batched solve to the end of the problem's last iteration), iteration counts
+and its error against the FP64 arm and the planted matrix.
 
-The printed line (rank 0) carries the contract keys plus: latency_ms (p50/p99
-per solve), roofline (dominant kernel class, timed with CUDA events over one
-instrumented step after the timed ones), cpu_baseline (the FP64 oracle on the
-host cores, bounded sample), e2e (host triplets -> sdp_setup -> solve ->
-solution copied back, through the public API), clocks (nvidia-smi samples taken
-during the timed region) and gpu_launches (library kernels in the timed region).
+Other workloads: C2 (n = 1000, m = 8000, rank 2; --k-max/--eta for the adaptive
+split rank), C3 (n = 4000, m = 60,000, rank 3), fig2 (p = q = 500, rank 4,
+m = 20,000: the paper's Fig. 2 instance), serving (the request stream).
+
+The printed line (rank 0) carries the contract keys plus: roofline (the batched
+FP64 matvec, timed with CUDA events in an instrumented host-driven step after the
+timed ones) and rooflines of the other kernel classes, cpu_baseline (measured
+full oracle solves of the workload's smallest instances on the host cores), e2e
+(host triplets -> sdp_setup -> solve -> solution copied back, through the public
+API, headline arm), clocks (nvidia-smi samples taken during the timed region) and
+gpu_launches (library kernels launched in the timed region).
 
 --impl reference times the FP64 oracle (explicit Hessian + Cholesky) on the host
-cores on a bounded sample of the same workload.  Under torchrun (--gpus N) each
-rank solves its own 16 instances (ranks take distinct blocks of the 256) with no
-collective on the data path; the step time is the maximum over ranks.
+cores.  Under torchrun (--gpus N) each rank solves its own 16 instances (ranks
+take distinct blocks of the 256) with no collective on the data path; the step
+time is the maximum over ranks.
 """
 from __future__ import annotations
 
@@ -48,8 +56,17 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-METRIC = "SDP solves/s at 1e-6 relative duality gap"
+METRIC = "SDP solves/s + p50/p99 latency at 1e-6 gap: served/mixed vs plain FP64 PCG"
 UNIT = "solves/s"
+DTYPES = {"fp64": "f64", "fp32": "f32+f64 (mixed)", "bf16": "bf16+f32+f64 (mixed)"}
+FORMS = {"fp64": "plain FP64 PCG",
+         "fp32": "mixed: FP32 split matvec + FP32 core inverse in PCG, FP64 refinement and IPM",
+         "bf16": "mixed: BF16 split W_s (FP32 accumulation) + FP32 core inverse in PCG, FP64 refinement and IPM"}
+
+# FP32 FMA peak derived the same way: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_PEAK_SOURCE = "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"
+FP32_CLASSES = ("matvec_lp_b",)
 
 # FP64 FMA throughput of this GB300, measured with a register-resident DFMA
 # loop (1216 CTAs x 256 threads, 8 independent chains per thread): 1.194 TFLOP/s.
@@ -161,8 +178,14 @@ def workload(name, count, rank=0, world=1):
     import sdp_inputs as si
     if name == "C2":
         d = si.config_instance("C2")
-        return [d], ("matrix-completion SDP n1=n2=500 (n=1000), rank 2, m=8000, seed 2; "
-                     "plain method, k=8 (optimum rank ~38)")
+        return [d], "matrix-completion SDP n1=n2=500 (n=1000), rank 2, m=8000, seed 2"
+    if name == "C3":
+        d = si.config_instance("C3")
+        return [d], "matrix-completion SDP n1=n2=2000 (n=4000), rank 3, m=60000, seed 3"
+    if name == "fig2":
+        d = si.mc_instance(500, 500, 4, 20000, 1702)
+        return [d], ("matrix-completion SDP p=q=500 (n=1000), rank 4, m=20000, seed 1702 "
+                     "(the instance shape of the paper's Fig. 2)")
     all_specs = si.batched_specs(256)
     idx = shard_indices(rank, world, count)
     specs = [all_specs[i] for i in idx]
@@ -175,61 +198,226 @@ def workload(name, count, rank=0, world=1):
     return inst, desc
 
 
-def cpu_oracle_rate(insts, iters_per_solve, budget_s=25.0):
-    """Oracle IPM iterations on the batch's instances (smallest first) for ~budget_s."""
+def oracle_sample(insts, budget_s=25.0):
+    """Measured oracle baseline: full FP64 oracle solves (explicit m x m Hessian and
+    Cholesky per Newton system) of the workload's smallest instances, smallest
+    first, until about budget_s of host time.  Returns (solves/s over the sampled
+    instances, description, per-instance records).  Nothing is extrapolated."""
     from oracle import sdp_oracle as o
-    done_t, done_i, used = 0.0, 0, []
+    done, used = 0.0, []
     for d in sorted(insts, key=lambda d: d.m):
         P = o.Problem.from_data(d)
         t0 = time.perf_counter()
-        o.ipm_solve(P, o.IPMParams(maxit=1))
+        r = o.ipm_solve(P)
         el = time.perf_counter() - t0
-        done_t += el
-        done_i += 1
-        used.append((d.n, d.m, el))
-        if done_t > budget_s:
+        done += el
+        used.append(dict(n=d.n, m=d.m, seconds=el, ipm_iters=len(r.log), converged=bool(r.converged)))
+        if done > budget_s:
             break
-    # scale: mean oracle seconds per IPM iteration over the sampled instances (weighted
-    # to the batch by m^3, the Cholesky cost) times iterations per solve
-    w_s = sum(el for _, _, el in used)
-    w_m = sum(m ** 3 for _, m, _ in used)
-    all_m = sum(d.m ** 3 for d in insts)
-    est_batch_iter = w_s * all_m / w_m
-    solve_s = est_batch_iter * iters_per_solve
-    sample = (f"one oracle IPM iteration (explicit m x m Hessian + Cholesky, NumPy/LAPACK FP64) on "
-              f"{done_i} of the {len(insts)} instances ({w_s:.1f} s), extrapolated to the batch by m^3 and "
-              f"to {iters_per_solve:.1f} IPM iterations per solve")
-    return len(insts) / solve_s, sample
+    rate = len(used) / done
+    sample = (f"full oracle solves (NumPy/LAPACK FP64, explicit m x m Hessian + Cholesky) of the {len(used)} "
+              f"smallest of the {len(insts)} workload instances (n {used[0]['n']}..{used[-1]['n']}, m "
+              f"{used[0]['m']}..{used[-1]['m']}), {done:.1f} s in total; solves/s of that sample, not of the "
+              f"whole workload (the largest instance, m = {max(d.m for d in insts)}, needs an "
+              f"{8 * max(d.m for d in insts) ** 2 / 1e9:.0f} GB Hessian)")
+    return rate, sample, used
 
 
 def run_reference(args):
+    """The oracle as the reference arm, timed on the machine's host cores: warm-up runs one
+    full oracle solve of the workload's smallest instance (its IPM iteration count);
+    each timed step is one oracle IPM iteration of that instance, and the value is
+    1 / (mean iteration time x iteration count), solves/s of that instance."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     insts, desc = workload(args.workload, args.batch)
-    times = []
     from oracle import sdp_oracle as o
     small = sorted(insts, key=lambda d: d.m)[0]
     P = o.Problem.from_data(small)
-    for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
+    t0 = time.perf_counter()
+    full = o.ipm_solve(P)
+    full_s = time.perf_counter() - t0
+    its = len(full.log)
+    for _ in range(max(0, args.warmup - 1)):
         o.ipm_solve(P, o.IPMParams(maxit=1))
-        if step >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    per_iter_small = statistics.median(times)
-    scale = sum(d.m ** 3 for d in insts) / small.m ** 3
-    iters = 20.0
-    value = len(insts) / (per_iter_small * scale * iters)
-    sample = (f"one oracle IPM iteration on the smallest instance (n={small.n}, m={small.m}) per step, "
-              f"scaled to the batch by m^3 and to {iters:.0f} IPM iterations per solve")
+    times = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        o.ipm_solve(P, o.IPMParams(maxit=1))
+        times.append(time.perf_counter() - t1)
+    per_iter = statistics.mean(times)
+    value = 1.0 / (per_iter * its)
+    sample = (f"oracle (NumPy/LAPACK FP64, explicit Hessian + Cholesky) on the workload's smallest instance "
+              f"(n={small.n}, m={small.m}): one IPM iteration per step ({per_iter:.2f} s) x {its} iterations of "
+              f"its measured full solve ({full_s:.1f} s, converged={bool(full.converged)})")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * len(insts) / value, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * per_iter, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": desc, "instances": len(insts), "l2_flush": False},
+            "config": {"workload": desc, "instances_timed": 1, "l2_flush": False, "same_config": False,
+                       "fits_in_driver_run": True, "oracle_full_solve_s": full_s, "oracle_ipm_iters": its},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _pct(xs, q):
+    srt = sorted(xs)
+    return srt[min(len(srt) - 1, max(0, int(math.ceil(q * len(srt))) - 1))]
+
+
+def _recovered(d, X):
+    """The p x q block Z of X for a matrix-completion instance (None otherwise)."""
+    p = d.meta.get("p") if isinstance(d.meta, dict) else None
+    return None if p is None else X[:p, p:]
+
+
+class Arm:
+    """One precision form of the workload: its problems resident on the device, a
+    lockstep batch over them, and the timings of its steps."""
+
+    def __init__(self, args, insts, prec, kk):
+        import torch
+        from paper_1703_10973_gb300 import SDPBatch, SDPProblem, default_params
+        self.prec = prec
+        self.args = args
+        self.insts = insts
+        extra = {"inner_rtol_lp": args.inner_lp} if args.inner_lp > 0 else {}
+        self.params = default_params(prec=prec, k=kk, pcg_maxit=args.pcg_maxit, pcg_graph=args.pcg_graph,
+                                     k_max=args.k_max, eta=args.eta, **extra)
+        n = len(insts) if args.batched_launch else min(args.streams, len(insts))
+        self.streams = [torch.cuda.Stream() for _ in range(n)]
+        self.probs = [SDPProblem.from_data(d, params=self.params, stream=self.streams[i % n].cuda_stream)
+                      for i, d in enumerate(insts)]
+        self.batch = None
+        self.bstream = torch.cuda.Stream()
+        if args.batched_launch:
+            self.batch = SDPBatch(self.probs, stream=self.bstream.cuda_stream, groups=args.batch_groups)
+        self.step_ms, self.lat_ms, self.res = [], [], None
+        self.stage_ms = {}
+
+    def solve_once(self, start_event=None):
+        """Solve every instance once from the start point; returns (per-solve ms, results)."""
+        import torch
+        if start_event is not None:
+            self.bstream.wait_event(start_event)
+            for st in self.streams:
+                st.wait_event(start_event)
+        if self.batch is not None:
+            torch.cuda.synchronize()
+            for p in self.probs:
+                p.reset()
+            res = self.batch.solve(allow_maxit=True)
+            torch.cuda.synchronize()
+            self.stage_ms = {k: (round(v * 1e3, 1) if k not in ("graph_launches", "batched_iters") else int(v))
+                             for k, v in self.batch.stage_seconds().items()}
+            # per problem: host wall time from the start of the batched solve to the
+            # end of that problem's last interior-point iteration
+            return [1e3 * r["seconds"] for r in res], res
+        lat = [None] * len(self.probs)
+        res = [None] * len(self.probs)
+        errs = []
+        nst = len(self.streams)
+
+        def worker(s):
+            try:
+                st = self.streams[s]
+                for i in range(s, len(self.probs), nst):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(st)
+                    self.probs[i].reset()
+                    res[i] = self.probs[i].solve(allow_maxit=True)
+                    b.record(st)
+                    b.synchronize()
+                    lat[i] = a.elapsed_time(b)
+            except Exception as e:  # surfaced after join
+                errs.append(e)
+
+        th = [threading.Thread(target=worker, args=(s,)) for s in range(nst)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        if errs:
+            raise errs[0]
+        return lat, res
+
+    def timed(self, flush, steps, dist):
+        import torch
+        for i in range(steps):
+            flush.fill_(float(i))          # evict L2 between steps (256 MB > 126 MB L2)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            lat, res = self.solve_once(t0)
+            for s in self.streams + [self.bstream]:   # join every stream into the default stream
+                torch.cuda.current_stream().wait_stream(s)
+            t1.record()
+            torch.cuda.synchronize()
+            self.step_ms.append(t0.elapsed_time(t1))
+            self.lat_ms += lat
+            self.res = res
+
+    def solutions(self):
+        return [p.get_solution()[0] for p in self.probs]
+
+    def close(self):
+        if self.batch is not None:
+            self.batch.close()
+        for p in self.probs:
+            p.close()
+
+
+def instrumented_step(args, insts, prec, kk, stream):
+    """One lockstep solve of the workload with CUDA events around every kernel class
+    and phase.  The batched PCG runs inside a graph whose kernels events cannot
+    bracket, so this step drives the same batched kernels from the host
+    (pcg_graph = 0), all problems in one lockstep group (nothing runs beside the
+    batched matvec)."""
+    import torch
+    from paper_1703_10973_gb300 import SDPBatch, SDPProblem, default_params
+    ip = default_params(prec=prec, k=kk, pcg_maxit=args.pcg_maxit, pcg_graph=0, k_max=args.k_max, eta=args.eta)
+    streams = [torch.cuda.Stream() for _ in insts]
+    probs = [SDPProblem.from_data(d, params=ip, stream=streams[i].cuda_stream) for i, d in enumerate(insts)]
+    ib = SDPBatch(probs, stream=stream.cuda_stream, groups=1)
+    torch.cuda.synchronize()
+    probs[0].timing_enable("*")
+    t0 = time.perf_counter()
+    ib.solve(allow_maxit=True)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1e3
+    rep = probs[0].timing_report()
+    probs[0].timing_enable(None)
+    ib.close()
+    for p in probs:
+        p.close()
+    return rep, wall
+
+
+def roofline_of(cls, rep, wall):
+    """Roofline object of kernel class `cls` from the instrumented step's records."""
+    kt = rep.get(cls)
+    if not kt or not kt[1]:
+        return None
+    ms, cnt, fl, by = kt
+    common = {"kernel": cls, "launches": cnt, "avg_us": 1e3 * ms / cnt, "busy_ms_per_step": ms,
+              "step_ms_instrumented": wall, "traffic": None}
+    if cls in FP32_CLASSES:
+        ach = fl / (ms * 1e-3) / 1e12
+        return dict(common, bound="alu", achieved=ach, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=ach / FP32_PEAK_TFLOPS, peak_source=FP32_PEAK_SOURCE,
+                    hbm_gbs=by / (ms * 1e-3) / 1e9)
+    if cls in ALU_CLASSES:
+        ach = fl / (ms * 1e-3) / 1e12
+        return dict(common, bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=ach / FP64_PEAK_TFLOPS, peak_source=FP64_PEAK_SOURCE)
+    peak = _peaks().get("hbm_gbs", 6776.3)
+    ach = by / (ms * 1e-3) / 1e9
+    return dict(common, bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak,
+                peak_source="measured copy bandwidth (MEASURED_PEAKS.json)")
 
 
 def run(args):
@@ -240,251 +428,175 @@ def run(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_1703_10973_gb300 import SDPProblem, _build, default_params, load
+    from paper_1703_10973_gb300 import SDPProblem, _build, load
     if not os.path.exists(_build.LIB):
         _build.build()
     load()
     insts, desc = workload(args.workload, args.batch, rank, ws)
-    kk = 8 if args.workload == "C2" else 0
-    params = default_params(prec=args.prec, k=kk, pcg_maxit=args.pcg_maxit, pcg_graph=args.pcg_graph)
-    nstreams = len(insts) if args.batched_launch else min(args.streams, len(insts))
-    streams = [torch.cuda.Stream() for _ in range(nstreams)]
-    probs = [SDPProblem.from_data(d, params=params, stream=streams[i % nstreams].cuda_stream)
-             for i, d in enumerate(insts)]
+    kk = args.k
+    precs = [x for x in args.arms.split(",") if x]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    arms = [Arm(args, insts, prec, kk) for prec in precs]
 
-    batch = None
-    stage_ms = {}          # batched mode: wall ms per lockstep stage of the last solve
-    if args.batched_launch:
-        from paper_1703_10973_gb300 import SDPBatch
-        bstream = torch.cuda.Stream()
-        batch = SDPBatch(probs, stream=bstream.cuda_stream, groups=args.batch_groups)
-
-    def run_batch(start_event=None):
-        """Solve every instance once; stream s handles instances s, s+S, ...  Returns per-solve ms."""
-        if batch is not None:   # lockstep: one launch per PCG step for all problems
-            if start_event is not None:
-                bstream.wait_event(start_event)
-                for st in streams:
-                    st.wait_event(start_event)
-            torch.cuda.synchronize()
-            for p in probs:
-                p.reset()
-            t0b = time.perf_counter()
-            res_b = batch.solve(allow_maxit=True)
-            torch.cuda.synchronize()
-            ms = (time.perf_counter() - t0b) * 1e3
-            stage_ms.update({k: (round(v * 1e3, 1) if k not in ("graph_launches", "batched_iters") else int(v))
-                             for k, v in batch.stage_seconds().items()})
-            return [ms] * len(probs), res_b
-        if start_event is not None:
-            for st in streams:
-                st.wait_event(start_event)
-        lat = [None] * len(probs)
-        res = [None] * len(probs)
-        errs = []
-
-        def worker(s):
-            try:
-                st = streams[s]
-                for i in range(s, len(probs), nstreams):
-                    a = torch.cuda.Event(enable_timing=True)
-                    b = torch.cuda.Event(enable_timing=True)
-                    a.record(st)
-                    probs[i].reset()
-                    res[i] = probs[i].solve(allow_maxit=True)
-                    b.record(st)
-                    b.synchronize()
-                    lat[i] = a.elapsed_time(b)
-            except Exception as e:  # surfaced after join
-                errs.append(e)
-
-        th = [threading.Thread(target=worker, args=(s,)) for s in range(nstreams)]
-        for t in th:
-            t.start()
-        for t in th:
-            t.join()
-        if errs:
-            raise errs[0]
-        return lat, res
-
-    for _ in range(args.warmup):
-        run_batch()
+    for arm in arms:
+        for _ in range(args.warmup):
+            arm.solve_once()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    l0 = probs[0].launch_count()
-    step_ms, lat_all, res_last = [], [], None
+    probe = arms[0].probs[0]
+    launches = {}
     with Clocks(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(float(i))          # evict L2 between steps (256 MB > 126 MB L2)
-            torch.cuda.synchronize()
-            t0 = torch.cuda.Event(enable_timing=True)
-            t1 = torch.cuda.Event(enable_timing=True)
-            t0.record()
-            lat, res = run_batch(t0)
-            for s in streams:              # join every stream into the default stream
-                torch.cuda.current_stream().wait_stream(s)
-            t1.record()
-            torch.cuda.synchronize()
-            step_ms.append(t0.elapsed_time(t1))
-            lat_all += lat
-            res_last = res
-    launches = probs[0].launch_count() - l0
-    stage_timed = dict(stage_ms)
-    total_ms = sum(step_ms)
+        for arm in arms:
+            l0 = probe.launch_count()
+            arm.timed(flush, args.steps, dist)
+            launches[arm.prec] = probe.launch_count() - l0
+    per_arm = {}
+    for arm in arms:
+        total_ms = sum(arm.step_ms)
+        if dist is not None:
+            total_ms = max_over_ranks(total_ms, dist, "cuda")
+        per_arm[arm.prec] = total_ms
     if dist is not None:
-        total_ms = max_over_ranks(total_ms, dist, "cuda")
         dist.barrier()
+    head = arms[0]
     solves = len(insts) * args.steps * ws
-    value = solves / (total_ms / 1e3)
-    converged = all(r["converged"] for r in res_last)
-    ipm_iters = [r["iters"] for r in res_last]
-    pcg_iters = [r["pcg_iters_total"] for r in res_last]
+    value = solves / (per_arm[head.prec] / 1e3)
 
-    # ---- one instrumented step: CUDA events around every kernel class and phase
-    roof, breakdown = None, None
+    # ---- each arm against the plain FP64 arm (same instances, same seed)
+    ref_arm = next((a for a in arms if a.prec == "fp64"), None)
+    ref_X = ref_arm.solutions() if ref_arm is not None else None
+    arm_lines = {}
+    for arm in arms:
+        Xs = arm.solutions()
+        res = arm.res
+        line = {"value": solves / (per_arm[arm.prec] / 1e3), "unit": UNIT,
+                "ms_per_step": per_arm[arm.prec] / args.steps,
+                "latency_ms": {"p50": _pct(arm.lat_ms, 0.50), "p99": _pct(arm.lat_ms, 0.99),
+                               "what": ("per problem: start of the batched solve -> end of its last IPM "
+                                        "iteration" if arm.batch is not None else
+                                        "per solve: CUDA events around the solve on its stream")},
+                "converged": all(r["converged"] for r in res),
+                "max_relgap": max(r["relgap"] for r in res),
+                "ipm_iters_mean": float(np.mean([r["iters"] for r in res])),
+                "pcg_iters_per_solve_mean": float(np.mean([r["pcg_iters_total"] for r in res])),
+                "gpu_launches": int(launches[arm.prec]),
+                "stage_ms_last_step": arm.stage_ms or None}
+        errs = []
+        for i, d in enumerate(insts):
+            Z = _recovered(d, Xs[i])
+            if Z is not None and "M" in d.meta:
+                M = d.meta["M"]
+                errs.append(float(np.linalg.norm(Z - M) / np.linalg.norm(M)))
+        if errs:
+            line["max_rel_err_vs_planted_M"] = max(errs)
+        if ref_arm is not None and arm is not ref_arm:
+            eo = [abs(a["obj_p"] - b["obj_p"]) / max(abs(b["obj_p"]), 1e-300) for a, b in zip(res, ref_arm.res)]
+            ez = []
+            for i, d in enumerate(insts):
+                Za, Zb = _recovered(d, Xs[i]), _recovered(d, ref_X[i])
+                if Za is None:
+                    Za, Zb = Xs[i], ref_X[i]
+                ez.append(float(np.linalg.norm(Za - Zb) / max(np.linalg.norm(Zb), 1e-300)))
+            line["max_rel_obj_err_vs_fp64"] = max(eo)
+            line["max_rel_Z_err_vs_fp64"] = max(ez)
+        arm_lines[arm.prec] = line
+
+    # ---- instrumented steps: kernel classes, phases and rooflines
+    roof, rooflines, breakdown = None, {}, {}
     if rank == 0 and args.timed_kernel:
-        if batch is not None:
-            # the batched PCG runs inside a graph, whose kernels events cannot
-            # bracket: the instrumented step drives the same batched kernels from
-            # the host (pcg_graph = 0), all problems in one lockstep group
-            from paper_1703_10973_gb300 import SDPBatch, default_params as _dp
-            iparams = _dp(prec=args.prec, k=kk, pcg_maxit=args.pcg_maxit, pcg_graph=0)
-            iprobs = [SDPProblem.from_data(d, params=iparams, stream=streams[i % nstreams].cuda_stream)
-                      for i, d in enumerate(insts)]
-            ib = SDPBatch(iprobs, stream=bstream.cuda_stream, groups=1)
-            torch.cuda.synchronize()
-            iprobs[0].timing_enable("*")
-            tk0 = time.perf_counter()
-            ib.solve(allow_maxit=True)
-            torch.cuda.synchronize()
-            step_wall = (time.perf_counter() - tk0) * 1e3
-            rep = iprobs[0].timing_report()
-            iprobs[0].timing_enable(None)
-            ib.close()
-            for p in iprobs:
-                p.close()
-        else:
-            probs[0].timing_enable("*")
-            tk0 = time.perf_counter()
-            run_batch()
-            torch.cuda.synchronize()
-            step_wall = (time.perf_counter() - tk0) * 1e3
-            rep = probs[0].timing_report()
-            probs[0].timing_enable(None)
-        breakdown = {k: round(v[0], 3) for k, v in sorted(rep.items(), key=lambda kv: -kv[1][0])}
-        if args.timed_kernel == "auto":
-            # the batched PCG matvec (SpMM + SDDMM of every active problem in one
-            # launch each) when the step ran batched: it is the hot path's kernel
-            # and, in the lockstep instrumented step, runs with nothing beside it;
-            # otherwise the kernel class with the most device time (phases excluded)
-            kcls = [k for k in rep if k not in PHASES and rep[k][2] > 0]
-            if args.prec == "fp64" and "matvec_b" in kcls and rep["matvec_b"][1] > 0:
-                args.timed_kernel = "matvec_b"
-            else:
-                args.timed_kernel = max(kcls, key=lambda k: rep[k][0]) if kcls else "sytrd"
-        kt = rep.get(args.timed_kernel)
-        if kt and kt[1]:
-            ms, cnt, fl, by = kt
-            avg = ms / cnt
-            if args.timed_kernel in ALU_CLASSES:
-                ach = fl / (ms * 1e-3) / 1e12
-                roof = {"kernel": args.timed_kernel, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                        "peak_source": FP64_PEAK_SOURCE, "launches": cnt, "avg_us": avg * 1e3,
-                        "busy_ms_per_step": ms, "step_ms_instrumented": step_wall}
-            else:
-                peak = _peaks().get("hbm_gbs", 6674.2)
-                ach = by / (ms * 1e-3) / 1e9
-                roof = {"kernel": args.timed_kernel, "bound": "hbm", "achieved": ach, "peak": peak,
-                        "unit": "GB/s", "frac": ach / peak, "traffic": None,
-                        "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
-                        "fp64_tflops": fl / (ms * 1e-3) / 1e12, "launches": cnt, "avg_us": avg * 1e3,
-                        "busy_ms_per_step": ms, "step_ms_instrumented": step_wall}
+        bs = torch.cuda.Stream()
+        for prec in dict.fromkeys(precs):
+            rep, wall = instrumented_step(args, insts, prec, kk, bs)
+            breakdown[prec] = {k: round(v[0], 3) for k, v in sorted(rep.items(), key=lambda kv: -kv[1][0])}
+            for cls in ("matvec_b", "matvec_lp_b", "gemm_f64", "potrf", "sytrd", "trsm"):
+                r = roofline_of(cls, rep, wall)
+                if r is not None:
+                    rooflines[f"{prec}:{cls}"] = r
+        want = args.timed_kernel if args.timed_kernel != "auto" else "matvec_b"
+        roof = rooflines.get(f"fp64:{want}") or next(iter(rooflines.values()), None)
 
-    # ---- end to end through the public API: host triplets in, solution out
+    # ---- end to end through the public API: host triplets in, solution out (headline arm)
     e2e = None
     if rank == 0 and args.e2e_steps > 0:
-        import ctypes as C
-        h2d = sum(d.Ci.nbytes + d.Cj.nbytes + d.Cv.nbytes + d.Ak.nbytes + d.Ai.nbytes + d.Aj.nbytes +
-                  d.Av.nbytes + d.b.nbytes for d in insts)
-        d2h = sum(8 * (d.n * d.n + d.m) for d in insts)
-        outs = [(np.empty((d.n, d.n)), np.empty(d.m)) for d in insts]
-        torch.cuda.synchronize()
-        te = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        e2e = run_e2e(args, insts, head)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, sample, used = oracle_sample(insts)
+        cpu = {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": sample,
+               "instances": used}
+
+    if rank == 0:
+        hl = arm_lines[head.prec]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": per_arm[head.prec] / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPES.get(head.prec, head.prec), "data": "synthetic",
+                "config": {"workload": desc, "instances": len(insts), "form": FORMS.get(head.prec, head.prec),
+                           "arms": precs, "pcg_loop": "graph" if args.pcg_graph else "host",
+                           "batched_launch": bool(args.batched_launch),
+                           "batch_groups": args.batch_groups if args.batched_launch else None,
+                           "parallelism": f"replicas{ws}", "l2_flush": True,
+                           "k_max": args.k_max, "eta": args.eta,
+                           "inner_rtol_lp": head.params.inner_rtol_lp},
+                "latency_ms": {"p50": hl["latency_ms"]["p50"], "p99": hl["latency_ms"]["p99"]},
+                "arms": arm_lines,
+                "roofline": roof, "rooflines": rooflines or None, "breakdown_ms_per_step": breakdown or None,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "gpu_launches": int(sum(launches.values()))}
+        print(json.dumps(line), flush=True)
+    for arm in arms:
+        arm.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, insts, head):
+    """The headline arm end to end through the public API: host triplets ->
+    sdp_setup -> batched (or per-stream) solve -> X and y copied back to the host."""
+    import ctypes as C
+    import torch
+    from paper_1703_10973_gb300 import SDPBatch, SDPProblem
+    h2d = sum(d.Ci.nbytes + d.Cj.nbytes + d.Cv.nbytes + d.Ak.nbytes + d.Ai.nbytes + d.Aj.nbytes +
+              d.Av.nbytes + d.b.nbytes for d in insts)
+    d2h = sum(8 * (d.n * d.n + d.m) for d in insts)
+    outs = [(np.empty((d.n, d.n)), np.empty(d.m)) for d in insts]
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ps = [SDPProblem.from_data(insts[i], params=head.params, stream=head.streams[i % len(head.streams)].cuda_stream)
+              for i in range(len(insts))]
+        if args.batched_launch:
+            with SDPBatch(ps, stream=head.bstream.cuda_stream, groups=args.batch_groups) as b2:
+                b2.solve(allow_maxit=True)
+        else:
             errs = []
 
-            def e2e_worker(s):
+            def w(s):
                 try:
-                    for i in range(s, len(insts), nstreams):
-                        p2 = SDPProblem.from_data(insts[i], params=params, stream=streams[s].cuda_stream)
-                        p2.solve(allow_maxit=True)
-                        X, y = outs[i]
-                        st = p2.lib.sdp_get_solution(p2.h, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data),
-                                                     None)
-                        assert st == 0
-                        p2.close()
+                    for i in range(s, len(ps), len(head.streams)):
+                        ps[i].solve(allow_maxit=True)
                 except Exception as e:
                     errs.append(e)
 
-            if args.batched_launch:   # set up all, solve in lockstep, copy every solution back
-                from paper_1703_10973_gb300 import SDPBatch
-                ps = [SDPProblem.from_data(insts[i], params=params, stream=streams[i].cuda_stream)
-                      for i in range(len(insts))]
-                with SDPBatch(ps, stream=bstream.cuda_stream, groups=args.batch_groups) as b2:
-                    b2.solve(allow_maxit=True)
-                for i, p2 in enumerate(ps):
-                    X, y = outs[i]
-                    st = p2.lib.sdp_get_solution(p2.h, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data), None)
-                    assert st == 0
-                    p2.close()
-                continue
-            th = [threading.Thread(target=e2e_worker, args=(s,)) for s in range(nstreams)]
+            th = [threading.Thread(target=w, args=(s,)) for s in range(len(head.streams))]
             for t in th:
                 t.start()
             for t in th:
                 t.join()
             if errs:
                 raise errs[0]
-        torch.cuda.synchronize()
-        el = time.perf_counter() - te
-        e2e = {"value": args.e2e_steps * len(insts) / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
-
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, sample = cpu_oracle_rate(insts, float(np.mean(ipm_iters)))
-        cpu = {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": sample}
-
-    if rank == 0:
-        srt = sorted(lat_all)
-        p50 = srt[len(srt) // 2]
-        p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else args.prec,
-                "data": "synthetic",
-                "config": {"workload": desc, "instances": len(insts), "streams": nstreams, "prec": args.prec, "pcg_loop": "graph" if args.pcg_graph else "host",
-                           "batched_launch": bool(args.batched_launch),
-                           "batch_groups": args.batch_groups if args.batched_launch else None,
-                           "parallelism": f"replicas{ws}", "l2_flush": True, "converged": converged,
-                           "ipm_iters_mean": float(np.mean(ipm_iters)),
-                           "pcg_iters_per_solve_mean": float(np.mean(pcg_iters)),
-                           "max_relgap": max(r["relgap"] for r in res_last)},
-                "latency_ms": {"p50": p50, "p99": p99},
-                "roofline": roof, "stage_ms_per_step": stage_timed or None, "breakdown_ms_per_step": breakdown, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clk.summary(),
-                "gpu_launches": int(launches)}
-        print(json.dumps(line), flush=True)
-    if batch is not None:
-        batch.close()
-    for p in probs:
-        p.close()
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+        for i, p2 in enumerate(ps):
+            X, y = outs[i]
+            st = p2.lib.sdp_get_solution(p2.h, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data), None)
+            assert st == 0
+            p2.close()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - te
+    return {"value": args.e2e_steps * len(insts) / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
 
 
 def run_serving(args):
@@ -544,17 +656,23 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "C2", "serving"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "C2", "C3", "fig2", "serving"])
+    ap.add_argument("--arms", default="fp32,fp64",
+                    help="precision forms timed on the same instances; the first is the headline value")
+    ap.add_argument("--k", type=int, default=0, help="split rank (0 = the instance's planted rank)")
+    ap.add_argument("--k-max", type=int, default=0, help="adaptive split rank: largest k~ (0 = fixed k)")
+    ap.add_argument("--eta", type=float, default=0.0, help="adaptive split rank: eigenvalue-gap ratio")
+    ap.add_argument("--inner-lp", type=float, default=0.0,
+                    help="PCG tolerance of one reduced-precision sweep (0 = the library default)")
     ap.add_argument("--requests", type=int, default=24, help="serving: requests per arrival rate")
     ap.add_argument("--serve-max-n", type=int, default=800, help="serving: largest SDP order admitted to the sample")
     ap.add_argument("--rates", default="0.25,0.5,1,1.5", help="serving: arrival rates as fractions of capacity")
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--streams", type=int, default=4)
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--pcg-maxit", type=int, default=2000)
     ap.add_argument("--timed-kernel", default="auto",
-                    help="kernel class for the roofline object; auto = the batched PCG matvec when the "
-                         "step ran batched, else the class with the most device time")
+                    help="kernel class of the roofline object (auto = matvec_b, the batched FP64 matvec); "
+                         "empty = no instrumented step")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-groups", type=int, default=0,

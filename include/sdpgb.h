@@ -20,9 +20,14 @@
  *    any status the handle may still be destroyed; sdp_last_error() gives text.
  *  - One handle is used by one host thread at a time.  All work is issued on the
  *    stream given to sdp_setup (NULL = the legacy default stream).
- *  - Precision argument `prec`: SDP_FP64 computes in double.  SDP_FP32 and
- *    SDP_BF16 store the operator data (W, Z, U, the core inverse) in float or
- *    bfloat16 and accumulate in float; vectors crossing the ABI stay double.
+ *  - Precision argument `prec`: SDP_FP64 computes in double.  With SDP_FP32 or
+ *    SDP_BF16 the Hessian matvec rounds the part W_s of the split W = W_l + W_s
+ *    (W_l = the top-k eigenpairs of the last preconditioner build, else W itself)
+ *    to float or bfloat16 and accumulates in float, adding the low-rank terms in
+ *    double; the Hhat preconditioner apply reads a float copy of its dense
+ *    Schur-factor inverse (both SDP_FP32 and SDP_BF16) and accumulates that
+ *    product in float.  The Algorithm 1 apply always runs in double.  Vectors
+ *    crossing the ABI stay double.
  */
 #ifndef SDPGB_H
 #define SDPGB_H
@@ -80,7 +85,21 @@ typedef struct {
                        /* the setting of its first problem                        */
   double inner_rtol_lp; /* PCG tolerance of one sweep whose matvec runs in FP32 or */
                         /* BF16 (the FP64 true residual refines it); 1e-4         */
+  long long wait_cycles; /* bound of every device-side spin wait (the grid barriers */
+                        /* of the cooperative tridiagonalisation, n > 1024), in SM */
+                        /* clock cycles; a wait that runs out makes the call return */
+                        /* SDP_ERR_TIMEOUT and leaves the handle usable; 0 = 4e9   */
+                        /* (about 2 s)                                             */
+  int k_max;            /* adaptive split rank (Section V implementation notes):   */
+                        /* with eta > 0 every preconditioner build uses            */
+                        /* k~ = max{i <= k_max : lambda_i(W) >= eta lambda_{i+1}(W)} */
+                        /* (eigenvalues decreasing, lambda_0 = +inf, k~ >= 1);     */
+                        /* 0 = k of sdp_setup.  At most SDP_K_MAX                  */
+  double eta;           /* eigenvalue-gap ratio of that rule; 0 = fixed rank k     */
 } sdp_params;
+
+/* Largest split rank (k of sdp_setup, params.k, params.k_max). */
+#define SDP_K_MAX 64
 
 typedef struct {
   int iter;                 /* IPM iteration index that produced this record      */
@@ -93,6 +112,7 @@ typedef struct {
   double pcg_relres_pred, pcg_relres_corr;   /* true FP64 residuals              */
   int converged;            /* 1 when the stopping test held at entry              */
   int nt_fallback;          /* 1 when W came from the Denman-Beavers iteration     */
+  int k_split;              /* split rank of this iteration's preconditioner        */
 } sdp_ipm_info;
 
 typedef struct {
@@ -114,7 +134,8 @@ void sdp_default_params(sdp_params* prm);
  * (A^T A)^{-1} = diag(1/||A_i||_F^2).  Assumption 2 is required in the form
  * "A^T A diagonal": SDP_ERR_UNSUPPORTED if two constraints have a nonzero inner
  * product.  Sets the start point X = S = xi I, y = 0.
- *   n >= 1, m >= 1, 1 <= k <= n.  C triplets: nnzC >= 0 (Ci, Cj, Cv may be
+ *   n >= 1, m >= 1, 1 <= k <= min(n, SDP_K_MAX); params k_max in [0, SDP_K_MAX],
+ *   eta >= 0 (SDP_ERR_ARG otherwise).  C triplets: nnzC >= 0 (Ci, Cj, Cv may be
  *   NULL when nnzC == 0).  A triplets: (Ak[t], Ai[t], Aj[t], Av[t]) adds Av[t]
  *   at (Ai,Aj) and (Aj,Ai) of A_{Ak[t]}.  b has m entries.  prm may be NULL
  *   (defaults).  cuda_stream is a cudaStream_t or NULL.  On success *out owns
@@ -175,8 +196,8 @@ sdp_status sdp_pcg_solve(sdp_problem* h, const double* r_dev, double* y_dev, dou
  * step to step_frac of the boundary; update.  info may be NULL.  Returns
  * SDP_OK also when the point already satisfies the stopping test
  * (info->converged = 1, nothing changed).  With the graph loop (pcg_graph = 1)
- * and a batchable configuration (SDP_PRECOND_HAT, 1 <= k <= 8, SDP_FP64 or
- * SDP_FP32) the two Newton systems run through a one-problem batch of this
+ * and a batchable configuration (SDP_PRECOND_HAT, 1 <= k <= 8, any prec) the
+ * two Newton systems run through a one-problem batch of this
  * handle (its PCG graph is captured once); the iterates are the same.
  */
 sdp_status sdp_ipm_step(sdp_problem* h, sdp_ipm_info* info);
@@ -196,6 +217,11 @@ sdp_status sdp_get_solution(sdp_problem* h, double* X_host, double* y_host, doub
 /* Replace the current iterate by host arrays X, S (n*n) and y (m); iter sets the counter. */
 sdp_status sdp_set_state(sdp_problem* h, const double* X_host, const double* y_host,
                          const double* S_host, int iter);
+
+/* Checkpoint: copy the current iterate to host arrays X, S (n*n) and y (m) and the
+ * IPM iteration counter to *iter (each may be NULL).  sdp_set_state of these values
+ * on a handle of the same problem resumes the solve with the same iterates. */
+sdp_status sdp_get_state(sdp_problem* h, double* X_host, double* y_host, double* S_host, int* iter);
 
 /* tau and the split rank used by the last sdp_precond_build. */
 sdp_status sdp_precond_info(sdp_problem* h, double* tau, int* k);
@@ -236,13 +262,15 @@ int64_t sdp_launch_count(const sdp_problem* h);
 /*
  * Batched solves (many uneven problems advanced together).  sdp_batch_create groups count set-up problems (each keeps its own
  * stream, data and state; all must use SDP_PRECOND_HAT with 1 <= k <= 8, and
- * the SDP_FP64 or the SDP_FP32 (split) matvec; SDP_ERR_UNSUPPORTED otherwise).
+ * the SDP_FP64, SDP_FP32 or SDP_BF16 (split) matvec; SDP_ERR_UNSUPPORTED otherwise).
  * sdp_batch_solve runs their interior-point iterations in lockstep: the dense
  * per-problem phases on each problem's stream (one host thread per problem),
  * and every PCG iteration of all their Newton systems as one sequence of
  * batched launches on cuda_stream, captured once as a CUDA graph that loops on
  * the device while any problem's PCG is running.  A problem's iterates are the
- * same in a batch as alone.  results: count entries (NULL allowed).  Returns
+ * same in a batch as alone.  results: count entries (NULL allowed); the
+ * seconds field of each is the host wall time from the start of the call to
+ * the end of that problem's last iteration.  Returns
  * SDP_OK when every problem converged, SDP_ERR_MAXIT when some hit an
  * iteration limit, else the first error (sdp_batch_last_error).  Problems
  * start from their current iterate (sdp_reset for the start point).  The batch
@@ -274,23 +302,31 @@ sdp_status sdp_batch_stage_seconds(const sdp_batch* b, double* out);
 
 /*
  * sdp_hessian_matvec_static -- handle-free, allocation-free variant of
- * sdp_hessian_matvec.  This call is an addition of this library for callers
- * that cannot allocate device memory; the paper has no counterpart.
+ * sdp_hessian_matvec.  The paper has no counterpart: this call exists for
+ * callers that cannot allocate device memory (code running inside a CUDA graph
+ * that is being captured, a host callback, or an embedding runtime that owns
+ * every device allocation itself), so it keeps no handle and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
  *
- * Computes Hv_dev[k] = A_k . (W V W), V = sum_j v_dev[j] A_j (eq. hesseqn2) in
- * FP64 from the constraint triplets (same convention as sdp_setup: (k, i, j, v)
- * sets (A_k)_ij = (A_k)_ji = v, duplicates add), all in device memory:
+ * Computes the same FP64 product as sdp_hessian_matvec, Hv_dev[k] = A_k . (W V W)
+ * with V = sum_j v_dev[j] A_j, directly from the constraint triplets (same
+ * convention as sdp_setup: (k, i, j, v) sets (A_k)_ij = (A_k)_ji = v,
+ * duplicates add), all in device memory:
  *   Ak_dev, Ai_dev, Aj_dev: int32[nnzA];  Av_dev: double[nnzA];
  *   W_dev: double[n*n], symmetric, row-major;  v_dev: double[m];
- *   Hv_dev: double[m], overwritten (cleared first).
+ *   Hv_dev: double[m], overwritten (cleared first).  Hv_dev must not overlap
+ *   v_dev or W_dev (SDP_ERR_ARG): it is cleared before they are read.
  * Scratch: two n x n FP64 matrices in a static __device__ array of this
- * library (SDP_STATIC_MAX_N^2 * 16 bytes = 4 MiB); nothing is allocated.
+ * library (SDP_STATIC_MAX_N^2 * 16 bytes = 4 MiB per device that loads it,
+ * held until the process exits); nothing is allocated.
  * n > SDP_STATIC_MAX_N returns SDP_ERR_ARG before any launch.  Triplets with
  * an index out of range are skipped by the kernels, counted, and make the call
  * return SDP_ERR_ARG.  The call synchronises cuda_stream once, to read that
  * count.  The first call on each device looks up the scratch address
  * (cudaGetSymbolAddress), which can load the module: make that first call
- * before capturing any stream.  Calls whose executions overlap (several
+ * before capturing any stream.  The products are accumulated with FP64
+ * atomic adds, so the last bits of a result can differ between runs (the
+ * handle matvec is deterministic).  Calls whose executions overlap (several
  * streams or host threads) share the scratch and race: serialise them.
  * Error text for this call: sdp_last_error(NULL), per host thread.
  */

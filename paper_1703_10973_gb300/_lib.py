@@ -15,6 +15,7 @@ SDP_OK, SDP_ERR_ARG, SDP_ERR_OOM, SDP_ERR_NOT_PD, SDP_ERR_MAXIT = 0, 1, 2, 3, 4
 SDP_ERR_UNSUPPORTED, SDP_ERR_NUMERIC, SDP_ERR_TIMEOUT, SDP_ERR_CUDA = 5, 6, 7, 8
 SDP_FP64, SDP_FP32, SDP_BF16 = 0, 1, 2
 SDP_STATIC_MAX_N = 512
+SDP_K_MAX = 64
 SDP_PRECOND_DIAG, SDP_PRECOND_WOODBURY, SDP_PRECOND_HAT = 0, 1, 2
 
 PREC = {"fp64": SDP_FP64, "fp32": SDP_FP32, "bf16": SDP_BF16}
@@ -36,6 +37,9 @@ class sdp_params(C.Structure):
         ("verbose", C.c_int),
         ("pcg_graph", C.c_int),
         ("inner_rtol_lp", C.c_double),
+        ("wait_cycles", C.c_longlong),
+        ("k_max", C.c_int),
+        ("eta", C.c_double),
     ]
 
 
@@ -58,6 +62,7 @@ class sdp_ipm_info(C.Structure):
         ("pcg_relres_corr", C.c_double),
         ("converged", C.c_int),
         ("nt_fallback", C.c_int),
+        ("k_split", C.c_int),
     ]
 
 
@@ -94,6 +99,7 @@ SIGNATURES = {
     "sdp_get_W": (C.c_int, [_P, _P]),
     "sdp_get_solution": (C.c_int, [_P, _P, _P, _P]),
     "sdp_set_state": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+    "sdp_get_state": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_int)]),
     "sdp_precond_info": (C.c_int, [_P, _DP, C.POINTER(C.c_int)]),
     "sdp_sizes": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "sdp_launch_count": (C.c_int64, [_P]),

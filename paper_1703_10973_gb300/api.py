@@ -169,6 +169,16 @@ class SDPProblem:
                                               C.c_void_p(S.ctypes.data)), "sdp_get_solution")
         return X, y, S
 
+    def get_state(self):
+        """Checkpoint of the iterate: (X, y, S, iteration counter) on the host."""
+        X = np.empty((self.n, self.n))
+        y = np.empty(self.m)
+        S = np.empty((self.n, self.n))
+        it = C.c_int(0)
+        self._raise(self.lib.sdp_get_state(self.h, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data),
+                                           C.c_void_p(S.ctypes.data), C.byref(it)), "sdp_get_state")
+        return X, y, S, it.value
+
     def set_state(self, X, y, S, it=0):
         X, y, S = _f64(X), _f64(y), _f64(S)
         self._raise(self.lib.sdp_set_state(self.h, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data),
@@ -235,6 +245,8 @@ def hessian_matvec_static(n, m, Ak, Ai, Aj, Av, W, v, out=None, stream=None):
     if out is None:
         out = torch.empty_like(v)
     _check_dev(out, m, "out")
+    if out.data_ptr() == v.data_ptr():
+        raise ValueError("out must not be v: the output is cleared before v is read")
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     st = lib.sdp_hessian_matvec_static(int(n), int(m), nnz, C.c_void_p(Ak.data_ptr()), C.c_void_p(Ai.data_ptr()),

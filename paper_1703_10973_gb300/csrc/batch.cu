@@ -19,8 +19,8 @@
 // The restarted outer loop (refinement on the FP64 true residual) is the
 // single-problem PcgSweeps state machine, stepped for all problems together.
 // Supported: the Hhat preconditioner (the default) with the FP64 matvec or the
-// FP32 split matvec; a problem whose FP32 sweep stalls hands over to FP64 on
-// its own, so one batched iteration can mix both forms.
+// FP32 / BF16 split matvec; a problem whose reduced-precision sweep stalls hands
+// over to FP64 on its own, so one batched iteration can mix the forms.
 #include "internal.cuh"
 
 #include <algorithm>
@@ -65,13 +65,13 @@ struct sdp_batch {
 namespace sdpgb {
 
 static bool batch_supported(sdp_problem* h, std::string* why) {
-  if (h->prm.prec != SDP_FP64 && h->prm.prec != SDP_FP32) {
-    *why = "batched solves run the FP64 or the FP32 split matvec (params.prec = SDP_FP64 or SDP_FP32)";
+  if (h->prm.prec != SDP_FP64 && h->prm.prec != SDP_FP32 && h->prm.prec != SDP_BF16) {
+    *why = "batched solves run the FP64, FP32 or BF16 split matvec";
     return false;
   }
   if (h->prm.precond != SDP_PRECOND_HAT) { *why = "batched solves use the Hhat preconditioner"; return false; }
-  const int k = std::min(h->k, std::max(h->n - 1, 0));
-  if (k < 1 || k > 8) { *why = "batched solves need 1 <= k <= 8"; return false; }
+  const int k = std::min(h->kcap, std::max(h->n - 1, 0));
+  if (k < 1 || k > 8) { *why = "batched solves need a split rank (k, or k_max) in 1..8"; return false; }
   return true;
 }
 
@@ -82,7 +82,7 @@ static void batch_offsets(sdp_batch* b) {
   b->nmax = 0;
   for (int i = 0; i < N; ++i) {
     sdp_problem* h = b->hs[i];
-    const int k = std::min(h->k, h->n - 1), Rk = h->hs_nr * k;
+    const int k = std::min(h->kcap, h->n - 1), Rk = h->hs_nr * k;   // grids for the largest rank
     const int cnt[BK_COUNT] = {batch_blocks_assemble(h->nnzV), batch_blocks_spmm(h->n), batch_blocks_sddmm(h->m),
                                batch_blocks_vec(h->m),         batch_blocks_hat_u(h->n), batch_blocks_tail(h->m),
                                batch_blocks_fwdP(h->hs_np),    batch_blocks_warp_rows(h->hs_nr),
@@ -93,7 +93,7 @@ static void batch_offsets(sdp_batch* b) {
     for (int kd = 0; kd < BK_COUNT; ++kd)
       b->off[(size_t)kd * (N + 1) + i + 1] = b->off[(size_t)kd * (N + 1) + i] + cnt[kd];
     b->nmax = std::max(b->nmax, h->n);
-    if (h->prm.prec == SDP_FP32) b->any_lp = true;
+    if (h->prm.prec == SDP_FP32 || h->prm.prec == SDP_BF16) b->any_lp = true;
   }
   for (int kd = 0; kd < BK_COUNT; ++kd) b->total[kd] = b->off[(size_t)kd * (N + 1) + N];
 }
@@ -115,40 +115,59 @@ static BDesc make_desc(sdp_problem* h, int active, int prec) {
   D.yP = h->hs_yP; D.v1 = h->hs_v1; D.v2 = h->hs_v2; D.uvec = h->uvec; D.Bn = h->Bn;
   D.px = h->px; D.pr = h->pr; D.pp = h->pp; D.pq = h->pq; D.pz = h->pz;
   D.scal = h->scal; D.part = h->pcg_part; D.ticket = h->pcg_ticket;
-  D.lp = (prec == SDP_FP32) ? 1 : 0;
-  D.ks = (D.lp && h->W32_key >= 0) ? h->kpc : 0;
+  D.lp = (prec == SDP_FP32 || prec == SDP_BF16) ? 1 : 0;
+  D.bf = (prec == SDP_BF16) ? 1 : 0;
+  D.ks = (D.lp && (D.bf ? h->W16_key : h->W32_key) >= 0) ? h->kpc : 0;
+  D.W16 = h->W16;
   D.W32 = h->W32; D.T32 = h->T32; D.mvR = h->mv_R; D.mvPart = h->mv_part;
   D.Etop = h->Etop; D.wtop = h->wtop; D.mvG = h->mv_G; D.mvQ = h->mv_Q;
+  // a reduced-precision sweep also solves the core with the FP32 copy of the
+  // Schur-factor inverse (made by pcg_start for this preconditioner)
+  D.lpc = (D.lp && h->hs_Cinv32 && h->hs_lp_gen == h->pc_generation) ? 1 : 0;
+  D.Cinv32 = h->hs_Cinv32; D.CinvT32 = h->hs_CinvT32; D.v1f = h->hs_v1f; D.v2f = h->hs_v2f;
   return D;
 }
 
 // One PCG iteration of every active problem (the body of the batched loop).
-// fp64 (host loop only): per problem, 1 when it runs an FP64-matvec sweep this
-// iteration; the batched FP64 matvec is then timed as class "matvec_b" with the
-// algorithmic work of those problems (T = W V: 2 nnzV n flops; one length-n dot
-// per stored entry: 2 nent n; bytes: W and T once each, the sparse data).
+// mode (host loop only): per problem, 1 when it runs an FP64-matvec sweep this
+// iteration, 2 for a reduced-precision sweep, 0 when inactive; the batched
+// matvecs are then timed as classes "matvec_b" (FP64) and "matvec_lp_b" (split
+// FP32 / BF16) with the algorithmic work of their problems.  FP64: T = W V
+// (2 nnzV n flops) and one length-n dot per stored entry (2 nent n); bytes: W
+// and T once each, the sparse data.  Split form: the same flops in FP32; bytes:
+// W_s read by the SpMM and by the gather (2 n^2 s_W), T written and read
+// (2 n^2 4), the sparse data.
 static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle cond, int* flag,
-                       const std::vector<char>* fp64 = nullptr) {
+                       const std::vector<char>* mode = nullptr) {
   const int N = (int)b->hs.size();
   const int* o = b->doff;
   auto off = [&](int kd) { return o + (size_t)kd * (N + 1); };
-  double fl = 0.0, by = 0.0;
-  if (fp64) {
+  double fl = 0.0, by = 0.0, fl_lp = 0.0, by_lp = 0.0;
+  if (mode) {
     for (int i = 0; i < N; ++i) {
-      if (!(*fp64)[i]) continue;
       const sdp_problem* h = b->hs[i];
-      fl += 2.0 * h->nnzV * (double)h->n + 2.0 * h->nent * (double)h->n;
-      by += 16.0 * h->n * (double)h->n + 12.0 * h->nnzV + 16.0 * h->m;
+      const double f = 2.0 * h->nnzV * (double)h->n + 2.0 * h->nent * (double)h->n;
+      if ((*mode)[i] == 1) {
+        fl += f;
+        by += 16.0 * h->n * (double)h->n + 12.0 * h->nnzV + 16.0 * h->m;
+      } else if ((*mode)[i] == 2) {
+        const double sw = (h->prm.prec == SDP_BF16) ? 2.0 : 4.0;
+        fl_lp += f;
+        by_lp += (2.0 * sw + 8.0) * h->n * (double)h->n + 12.0 * h->nnzV + 16.0 * h->m;
+      }
     }
     ktimer_begin(st, "matvec_b");
   }
   batch_launch_matvec(st, b->ddesc, off(BK_ASM), off(BK_SPMM), off(BK_SDDMM), N, b->total[BK_ASM],
                       b->total[BK_SPMM], b->total[BK_SDDMM], b->nmax);
-  if (fp64) ktimer_end(st, "matvec_b", fl, by);
-  if (b->any_lp)   // same SDDMM partition (and reduction groups) as the FP64 form
+  if (mode) ktimer_end(st, "matvec_b", fl, by);
+  if (b->any_lp) {  // same SDDMM partition (and reduction groups) as the FP64 form
+    if (mode) ktimer_begin(st, "matvec_lp_b");
     batch_launch_matvec_lp(st, b->ddesc, off(BK_SPLG), off(BK_SPLR), off(BK_SPLQ), off(BK_SPMM_LP), off(BK_SDDMM),
                            N, b->total[BK_SPLG], b->total[BK_SPLR], b->total[BK_SPLQ], b->total[BK_SPMM_LP],
                            b->total[BK_SDDMM], b->nmax);
+    if (mode) ktimer_end(st, "matvec_lp_b", fl_lp, by_lp);
+  }
   batch_launch_xr(st, b->ddesc, off(BK_VEC), N, b->total[BK_VEC]);
   batch_launch_hat_u(st, b->ddesc, off(BK_HATU), N, b->total[BK_HATU]);
   batch_launch_core_solve(st, b->ddesc, N, off(BK_FWDP), b->total[BK_FWDP], off(BK_FWDR), b->total[BK_FWDR],
@@ -255,10 +274,10 @@ static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::v
       // flags[0]: some problem active; flags[1 + i]: problem i active (read back
       // after every iteration, so each timed matvec knows its problems)
       std::vector<int> flags(N + 1, 0);
-      std::vector<char> fp64(N, 0);
-      for (int i : running) fp64[i] = (S[i].prec == SDP_FP64);
+      std::vector<char> mode(N, 0);
+      for (int i : running) mode[i] = (S[i].prec == SDP_FP64) ? 1 : 2;
       for (;;) {
-        batch_body(b, b->stream, cudaGraphConditionalHandle{}, b->dflag, &fp64);
+        batch_body(b, b->stream, cudaGraphConditionalHandle{}, b->dflag, &mode);
         if (cudaMemcpyAsync(flags.data(), b->dflag, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, b->stream) !=
                 cudaSuccess ||
             cudaStreamSynchronize(b->stream) != cudaSuccess) {
@@ -266,7 +285,7 @@ static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::v
           return SDP_ERR_CUDA;
         }
         if (!flags[0]) break;
-        for (int i = 0; i < N; ++i) fp64[i] = fp64[i] && flags[1 + i];
+        for (int i = 0; i < N; ++i) mode[i] = flags[1 + i] ? mode[i] : 0;
       }
     } else if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess) {
       b->last_error = std::string("sdp_batch: batched PCG failed: ") + cudaGetErrorString(cudaGetLastError());
@@ -432,6 +451,8 @@ static sdp_status batch_solve_lockstep(sdp_batch* b, sdp_result* results) {
   std::vector<char> done(N, 0);
   std::vector<int> pcg_total(N, 0), its(N, 0);
   std::vector<double> rr(N, 0.0);
+  std::vector<double> fin(N, -1.0);   // seconds from the start of the solve to each problem's end
+  auto since = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
   int ipm_maxit = 0;
   for (auto* h : b->hs) ipm_maxit = std::max(ipm_maxit, h->prm.ipm_maxit);
   for (double& x : b->stage_s) x = 0.0;
@@ -455,10 +476,14 @@ static sdp_status batch_solve_lockstep(sdp_batch* b, sdp_result* results) {
     lap(0);
     std::vector<int> solve;
     for (int i : act) {
-      if (st[i] != SDP_OK) continue;
+      if (st[i] != SDP_OK) {
+        if (fin[i] < 0.0) fin[i] = since();
+        continue;
+      }
       if (conv[i]) done[i] = 1;
       else if (it < b->hs[i]->prm.ipm_maxit) solve.push_back(i);
       else done[i] = 2;   // iteration limit
+      if (done[i] && fin[i] < 0.0) fin[i] = since();
     }
     if (solve.empty()) continue;
     SDP_TRY(batch_newton(b, solve, its, rr, st));
@@ -494,7 +519,7 @@ static sdp_status batch_solve_lockstep(sdp_batch* b, sdp_result* results) {
     r.iters = b->hs[i]->iter;
     r.pcg_iters_total = pcg_total[i];
     r.converged = (done[i] == 1) ? 1 : 0;
-    r.seconds = secs;
+    r.seconds = (fin[i] >= 0.0) ? fin[i] : secs;   // this problem's own completion time
     if (results) results[i] = r;
     if (st[i] != SDP_OK && worst == SDP_OK) {
       worst = st[i];

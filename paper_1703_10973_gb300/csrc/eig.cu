@@ -55,11 +55,11 @@ __device__ double bsum(double v, double* sh) {
 }
 
 // Grid-wide barrier for a cooperative launch.  Every wait is bounded: after
-// about two seconds of clock the waiting CTA sets *flag and returns false; all
-// CTAs then leave the kernel at their next barrier.
+// `spin` cycles of the SM clock (default about two seconds) the waiting CTA sets
+// *flag and returns false; all CTAs then leave the kernel at their next barrier.
 constexpr long long SPIN_CYCLES = 4000000000LL;
 
-__device__ bool grid_barrier(unsigned int* bar, int* flag) {
+__device__ bool grid_barrier(unsigned int* bar, int* flag, long long spin) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -77,8 +77,8 @@ __device__ bool grid_barrier(unsigned int* bar, int* flag) {
       unsigned int spins = 0;
       while (*vgen == gen) {
         if (*(volatile int*)flag) { s_ok = 0; break; }
-        if ((++spins & 255u) == 0u && clock64() - t0 > SPIN_CYCLES) { atomicExch(flag, 1); s_ok = 0; break; }
-        if (spins > 4096u) __nanosleep(64);
+        if (clock64() - t0 > spin) { atomicExch(flag, 1); s_ok = 0; break; }
+        if (++spins > 4096u) __nanosleep(64);
       }
     }
     __threadfence();
@@ -92,7 +92,7 @@ __device__ bool grid_barrier(unsigned int* bar, int* flag) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_sytrd(int n, double* A, int lda, double* d, double* e,
                                                double* tauh, double* p, double* part,
-                                               unsigned int* bar, int* flag) {
+                                               unsigned int* bar, int* flag, long long spin) {
   extern __shared__ double sm[];
   double* v = sm;       // n
   double* w = sm + n;   // n
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_sytrd(int n, double* A, int lda, double
     }
     kp = bsum(kp, red);
     if (threadIdx.x == 0) part[blockIdx.x] = kp;
-    if (!grid_barrier(bar, flag)) return;
+    if (!grid_barrier(bar, flag, spin)) return;
     // --- w = p - (tau/2)(p^T v) v ; A22 -= v w^T + w v^T
     if (threadIdx.x < 32) {
       double K = 0.0;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256) k_sytrd(int n, double* A, int lda, double
         tauh[j] = tau;
       }
     }
-    if (!grid_barrier(bar, flag)) return;
+    if (!grid_barrier(bar, flag, spin)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (n >= 2) {
@@ -400,7 +400,8 @@ static sdp_status sytrd(cudaStream_t st, int n, double* A, EigWork* w) {
   cudaMemsetAsync(w->flag, 0, sizeof(int), st);
   const int blocks = sytrd_blocks(n, smem);
   int lda = n;
-  void* args[] = {&n, &A, &lda, &w->d, &w->e, &w->tauh, &w->p, &w->part, &w->bar, &w->flag};
+  long long spin = (w->spin_cycles > 0) ? w->spin_cycles : SPIN_CYCLES;
+  void* args[] = {&n, &A, &lda, &w->d, &w->e, &w->tauh, &w->p, &w->part, &w->bar, &w->flag, &spin};
   count_launch();
   ktimer_begin(st, "sytrd");
   cudaError_t err = cudaLaunchCooperativeKernel((void*)k_sytrd, dim3(blocks), dim3(256), args, smem, st);
@@ -950,7 +951,7 @@ sdp_status eig_min(cudaStream_t st, int n, double* A, double* lmin_dev, EigWork*
 
 sdp_status eig_extremes(cudaStream_t st, int n, double* A, int k, double* lmin_dev, double* wtop,
                         double* Etop, EigWork* w) {
-  if (k < 0 || k > 31 || k > n) return SDP_ERR_ARG;
+  if (k < 0 || k > SDP_K_MAX + 1 || k > n) return SDP_ERR_ARG;
   SDP_TRY(sytrd(st, n, A, w));
   const int nb = (k > 0) ? split_blocks(st, n, w) : 1;
   if (nb <= 1) {
@@ -958,7 +959,7 @@ sdp_status eig_extremes(cudaStream_t st, int n, double* A, int k, double* lmin_d
     if (k == 0) return SDP_OK;
     int* idx = (int*)w->part;  // small scratch (part is idle here)
     count_launch(1);
-    k_idx_extremes<<<1, 32, 0, st>>>(n, k, idx);
+    k_idx_extremes<<<1, 128, 0, st>>>(n, k, idx);
     launch_stebz(st, n, w->d, w->e, k, idx + 1, 0, wtop);
     eigenvectors(st, n, w, 1, wtop, 0, k, Etop);
   } else {

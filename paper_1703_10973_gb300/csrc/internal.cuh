@@ -78,11 +78,16 @@ struct BDesc {
   const int *pverts, *rverts, *btptr, *btslot, *bp, *bptr, *bcol;
   const double *D, *F, *Cinv, *CinvT;
   double *yP, *v1, *v2, *uvec, *Bn;
+  int lpc;                          // the core solve uses the FP32 copy of the Schur-factor inverse
+  const float *Cinv32, *CinvT32;
+  float *v1f, *v2f;
   double *px, *pr, *pp, *pq, *pz;
   double *scal, *part;
   unsigned int* ticket;
   // FP32 split matvec (a problem in a reduced-precision sweep)
   int lp, ks;                       // lp: this sweep runs the FP32 matvec; ks: split rank (0: none)
+  int bf;                           // the reduced-precision W_s copy is bfloat16 (W16), else float (W32)
+  const __nv_bfloat16* W16;
   const float* W32;
   float *T32, *mvR, *mvPart;
   const double *Etop, *wtop;
@@ -253,6 +258,7 @@ struct EigWork {
   double* val = nullptr;    // n   per-block eigenvalues before sorting
   int* blocks = nullptr;    // 3n+4  block of each row, block starts, block ends, count
   int* src = nullptr;       // n   row that owns each sorted eigenvalue
+  long long spin_cycles = 0;   // bound of a grid-barrier wait (0: the default)
 };
 size_t eig_work_bytes(int n, bool full);
 void eig_work_carve(EigWork* w, void* base, int n, bool full);
@@ -271,12 +277,14 @@ struct SchurPlanHost {
 };
 void schur_plan(int n, const std::vector<int>& krowptr, const std::vector<int>& kcol, SchurPlanHost* out);
 sdp_status schur_build(sdp_problem* h, int k, double tau);
-sdp_status schur_apply(sdp_problem* h, const double* u, double* out, double scale);
+sdp_status schur_apply(sdp_problem* h, const double* u, double* out, double scale, int prec = SDP_FP64);
+// FP32 copy of the Hhat core's dense factor inverse for applies in reduced precision
+sdp_status ensure_lowprec_core(sdp_problem* h);
 bool lanczos_fits(int n);
 sdp_status lanczos_min(cudaStream_t st, int n, const double* M, const double* A2, const double* A3, int ldm,
                        double rtol, double accept_above, double* work, double* out_dev);
-// Smallest eigenvalue and the top-k eigenpairs: wtop[0..k) ascending (= lambda_{n-k..n-1}),
-// Etop rows = eigenvectors; *lmin_dev = lambda_0.
+// Smallest eigenvalue and the top-k eigenpairs (k <= SDP_K_MAX + 1): wtop[0..k) ascending
+// (= lambda_{n-k..n-1}), Etop rows = eigenvectors; *lmin_dev = lambda_0.
 sdp_status eig_extremes(cudaStream_t st, int n, double* A, int k, double* lmin_dev, double* wtop,
                         double* Etop, EigWork* ws);
 // Reads the barrier-timeout flag; nonzero -> SDP_ERR_TIMEOUT.
@@ -289,6 +297,8 @@ int eig_flag(cudaStream_t st, EigWork* ws);
 // ---------------------------------------------------------------------------
 struct sdp_problem {
   int n = 0, m = 0, k = 0;
+  int kcap = 0;            // largest split rank a build can use (k, or k_max with the adaptive rule)
+  int kest = -1;           // split rank chosen by the last build's adaptive rule (-1: fixed k)
   sdp_params prm{};
   cudaStream_t stream = nullptr;
   std::string last_error;
@@ -383,6 +393,13 @@ struct sdp_problem {
   double *hs_D = nullptr, *hs_F = nullptr, *hs_yP = nullptr;     // L_P, F = L_P^{-1} B, y_P
   double *hs_C = nullptr, *hs_Cinv = nullptr, *hs_CinvT = nullptr;   // Schur factor, inverse, its transpose
   double *hs_v1 = nullptr, *hs_v2 = nullptr, *hs_v3 = nullptr;
+  // FP32 copy of the Schur-factor inverse and its transpose for reduced-precision
+  // applies, refreshed once per preconditioner build (key hs_lp_gen)
+  float *hs_Cinv32 = nullptr, *hs_CinvT32 = nullptr, *hs_v1f = nullptr, *hs_v2f = nullptr;
+  int64_t hs_lp_gen = -1;
+  size_t hs_lp_cap = 0;    // Rk the float copies were allocated for
+  size_t hs_cap = 0;       // Rk the Schur buffers were allocated for (they grow, never shrink)
+  int hs_kcap = 0;         // split rank they were allocated for
   double* trpart = nullptr;
 
   // ---- dense IPM work ----
@@ -419,6 +436,7 @@ struct sdp_problem {
   unsigned int* pcg_ticket = nullptr;  // their arrival tickets (one per reduction)
 
   std::vector<void*> owned;   // every cudaMalloc made for this handle
+  std::vector<size_t> owned_bytes;
   int64_t device_bytes = 0;   // their total size
 
   void set_error(sdp_status s, const std::string& msg) {
@@ -426,6 +444,7 @@ struct sdp_problem {
     last_error = msg;
   }
   sdp_status alloc(void** p, size_t bytes);
+  void release(void* p);      // frees one allocation made by alloc (no-op for nullptr)
   template <typename T>
   sdp_status allocT(T** p, size_t count) {
     return alloc(reinterpret_cast<void**>(p), count * sizeof(T));

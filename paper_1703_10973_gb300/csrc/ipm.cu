@@ -56,6 +56,7 @@ sdp_status ipm_alloc(sdp_problem* h) {
   if (!h->eig_base) {
     SDP_TRY(h->alloc(&h->eig_base, eig_work_bytes(n, true)));
     eig_work_carve(&h->eig, h->eig_base, n, true);
+    h->eig.spin_cycles = h->prm.wait_cycles;
   }
   if (n >= LZ_MIN_N && lanczos_fits(n)) SDP_TRY(h->allocT(&h->lz_work, lanczos_work_doubles(n)));
   return SDP_OK;
@@ -441,6 +442,7 @@ sdp_status ipm_phase_a(sdp_problem* h, IpmStepState* s, bool* done) {
   SDP_TRY(precond_build_impl(h));
   ktimer_end(st, "precond_build", 0.0, 0.0);
   inf.tau = h->tau;
+  inf.k_split = h->kpc;
 
   // ---- common part of the right-hand side: Rp <- Rp + A(W Rd W) (nothing to add
   // once a full dual step has made the iterate dual feasible: Rd = 0 exactly)
@@ -515,8 +517,8 @@ sdp_status ipm_phase_c(sdp_problem* h, IpmStepState* s, int its, double rr) {
   SDP_CK(h, cudaGetLastError());
   h->iter++;
   if (h->prm.verbose)
-    fprintf(stderr, "ipm %3d mu %.3e gap %.3e pinf %.3e dinf %.3e ap %.3f ad %.3f sig %.3e pcg %d/%d rel %.1e/%.1e\n",
-            inf.iter, inf.mu, inf.relgap, inf.pinf, inf.dinf, ap, ad, inf.sigma, inf.pcg_iters_pred,
+    fprintf(stderr, "ipm %3d mu %.3e gap %.3e pinf %.3e dinf %.3e ap %.3f ad %.3f sig %.3e k %d pcg %d/%d rel %.1e/%.1e\n",
+            inf.iter, inf.mu, inf.relgap, inf.pinf, inf.dinf, ap, ad, inf.sigma, inf.k_split, inf.pcg_iters_pred,
             inf.pcg_iters_corr, inf.pcg_relres_pred, inf.pcg_relres_corr);
   return SDP_OK;
 }

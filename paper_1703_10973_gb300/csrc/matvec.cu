@@ -467,7 +467,8 @@ __global__ void __launch_bounds__(128) kb_split_R_part(const BDesc* __restrict__
   const BDesc& D = desc[i];
   if (!D.active || !D.lp || D.ks == 0) return;
   const int lb = blockIdx.x - off[i], gx = (D.n + 127) / 128;
-  split_R_part_body<float>(lb % gx, lb / gx, D.n, D.ks, D.mvG, D.W32, D.mvPart);
+  if (D.bf) split_R_part_body<__nv_bfloat16>(lb % gx, lb / gx, D.n, D.ks, D.mvG, D.W16, D.mvPart);
+  else split_R_part_body<float>(lb % gx, lb / gx, D.n, D.ks, D.mvG, D.W32, D.mvPart);
 }
 __global__ void __launch_bounds__(256) kb_split_R_Q(const BDesc* __restrict__ desc, const int* __restrict__ off,
                                                     int N) {
@@ -481,16 +482,25 @@ __global__ void __launch_bounds__(256) kb_spmm_lp(const BDesc* __restrict__ desc
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
   if (!D.active || !D.lp) return;
-  spmm_lp_body<float, BATCH_SPMM_LP_R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W32, D.T32, fsh);
+  if (D.bf)
+    spmm_lp_body<__nv_bfloat16, BATCH_SPMM_LP_R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W16, D.T32,
+                                                 fsh);
+  else
+    spmm_lp_body<float, BATCH_SPMM_LP_R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W32, D.T32, fsh);
 }
 __global__ void __launch_bounds__(256) kb_sddmm_lp(const BDesc* __restrict__ desc, const int* __restrict__ off,
                                                    int N) {
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
   if (!D.active || !D.lp) return;
-  sddmm_lp_body<float>(blockIdx.x - off[i], off[i + 1] - off[i], D.n, D.m, D.eptr, D.ep, D.eq, D.ecoef, D.W32,
-                       D.T32, D.pq, D.pp, D.part, D.ticket, D.scal + S_PQ, D.scal + S_RZ, D.scal + S_RZN, D.ks,
-                       D.Etop, D.mvR, D.mvQ);
+  if (D.bf)
+    sddmm_lp_body<__nv_bfloat16>(blockIdx.x - off[i], off[i + 1] - off[i], D.n, D.m, D.eptr, D.ep, D.eq, D.ecoef,
+                                 D.W16, D.T32, D.pq, D.pp, D.part, D.ticket, D.scal + S_PQ, D.scal + S_RZ,
+                                 D.scal + S_RZN, D.ks, D.Etop, D.mvR, D.mvQ);
+  else
+    sddmm_lp_body<float>(blockIdx.x - off[i], off[i + 1] - off[i], D.n, D.m, D.eptr, D.ep, D.eq, D.ecoef, D.W32,
+                         D.T32, D.pq, D.pp, D.part, D.ticket, D.scal + S_PQ, D.scal + S_RZ, D.scal + S_RZN, D.ks,
+                         D.Etop, D.mvR, D.mvQ);
 }
 int batch_blocks_split_G(int n) { return (int)cdiv((size_t)n * 32, 256); }
 int batch_blocks_split_R(int n) { return (int)cdiv(n, 128) * SPLIT_CHUNKS; }

@@ -197,6 +197,7 @@ static sdp_status pcg_graph(sdp_problem* h, int prec) {
     h->pcg_graph = nullptr;
   }
   SDP_TRY(ensure_lowprec_W(h, prec));
+  if (prec != SDP_FP64) SDP_TRY(ensure_lowprec_core(h));
   cudaGraph_t g = nullptr;
   SDP_CK(h, cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle cond;
@@ -248,8 +249,12 @@ static sdp_status pcg_start(sdp_problem* h, const double* rhs, double rtol, int 
   cudaStream_t st = h->stream;
   const int m = h->m;
   double* scal = h->scal;
-  if (graph) SDP_TRY(pcg_graph(h, prec));
-  else SDP_TRY(ensure_lowprec_W(h, prec));
+  if (graph) {
+    SDP_TRY(pcg_graph(h, prec));
+  } else {
+    SDP_TRY(ensure_lowprec_W(h, prec));
+    if (prec != SDP_FP64) SDP_TRY(ensure_lowprec_core(h));
+  }
   SDP_CK(h, cudaMemcpyAsync(h->pr, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   SDP_CK(h, cudaMemsetAsync(h->px, 0, m * sizeof(double), st));
   dot(st, m, h->pr, h->pr, scal + S_NR0, h->part);
@@ -409,6 +414,11 @@ sdp_status pcg_sweep_end(sdp_problem* h, PcgSweeps* S) {
     S->finished = true;
   } else if (S->total >= S->maxit) {
     S->finished = true;
+  } else if (S->prec != SDP_FP64 && S->tr > 0.1 * tr_prev) {
+    // a reduced-precision sweep that gained less than one digit on the FP64
+    // residual has reached what its rounding allows: the next sweeps run in FP64
+    S->prec = SDP_FP64;
+    h->pcg_prec_fallbacks++;
   }
   return SDP_OK;
 }

@@ -161,6 +161,42 @@ __global__ void k_hat_u(int n, int k, const int* __restrict__ rowptr, const int*
              scoef, ginv, r, U, scale, u);
 }
 
+// The same product for split ranks above 8 (up to 64): one warp per row a; the
+// lanes first assemble V on 32 entries of the row at once, then every entry is
+// broadcast and lane l accumulates columns l and l + 32 of u.
+__global__ void k_hat_u_gen(int n, int k, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                            const int* __restrict__ sptr, const int* __restrict__ scon,
+                            const double* __restrict__ scoef, const double* __restrict__ ginv,
+                            const double* __restrict__ r, const double* __restrict__ U, double scale,
+                            double* __restrict__ u) {
+  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (a >= n) return;
+  double a0 = 0.0, a1 = 0.0;
+  const int l0 = lane, l1 = lane + 32;
+  for (int s0 = rowptr[a]; s0 < rowptr[a + 1]; s0 += 32) {
+    const int cnt = min(32, rowptr[a + 1] - s0);
+    double v = 0.0;
+    int col = 0;
+    if (lane < cnt) {
+      const int s = s0 + lane;
+      for (int c = sptr[s]; c < sptr[s + 1]; ++c) {
+        const int i = scon[c];
+        v = fma(scoef[c] * ginv[i], r[i], v);
+      }
+      col = colidx[s];
+    }
+    for (int t = 0; t < cnt; ++t) {
+      const double vt = __shfl_sync(0xffffffffu, v, t);
+      const int ct = __shfl_sync(0xffffffffu, col, t);
+      const double* ur = U + (size_t)ct * k;
+      if (l0 < k) a0 = fma(vt, ur[l0], a0);
+      if (l1 < k) a1 = fma(vt, ur[l1], a1);
+    }
+  }
+  if (l0 < k) u[(size_t)l0 * n + a] = scale * a0;
+  if (l1 < k) u[(size_t)l1 * n + a] = scale * a1;
+}
+
 // Batched forms of the Hhat apply ends (the core solve is in schur.cu)
 __global__ void kb_hat_u(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
   const int i = batch_find(off, N, blockIdx.x);
@@ -381,17 +417,19 @@ __global__ void k_small_jacobi(int k, double* B, double* Q, double* w) {
 
 static sdp_status precond_alloc(sdp_problem* h) {
   if (h->U) return SDP_OK;
-  const int n = h->n, k = std::max(h->k, 1);
-  const size_t nk = (size_t)n * k;
+  // kcap + 1 eigenpairs are computed for the adaptive rule (it compares
+  // lambda_k with lambda_{k+1}); the split itself uses at most kcap of them
+  const int n = h->n, k = std::max(h->kcap + 1, 1), kc = std::max(h->kcap, 1);
+  const size_t nk = (size_t)n * k, nkc = (size_t)n * kc;
   SDP_TRY(h->allocT(&h->U, nk));
   SDP_TRY(h->allocT(&h->Z, (size_t)n * n));
   if (h->prm.precond != SDP_PRECOND_HAT) {   // dense core (Hhat factors it sparsely, schur.cu)
-    SDP_TRY(h->allocT(&h->Sc, nk * nk));
-    SDP_TRY(h->allocT(&h->Linv, nk * nk));
+    SDP_TRY(h->allocT(&h->Sc, nkc * nkc));
+    SDP_TRY(h->allocT(&h->Linv, nkc * nkc));
   }
-  SDP_TRY(h->allocT(&h->tau_dev, 8 + 2 * 32 * 32));
-  SDP_TRY(h->allocT(&h->wtop, 32));
-  SDP_TRY(h->allocT(&h->Etop, (size_t)32 * n));
+  SDP_TRY(h->allocT(&h->tau_dev, 8 + 2 * (size_t)(SDP_K_MAX + 1) * (SDP_K_MAX + 1)));
+  SDP_TRY(h->allocT(&h->wtop, SDP_K_MAX + 1));
+  SDP_TRY(h->allocT(&h->Etop, (size_t)(SDP_K_MAX + 1) * n));
   SDP_TRY(h->allocT(&h->au, (size_t)std::max(h->ncr, 1) * k));
   SDP_TRY(h->allocT(&h->Kval, std::max(h->nnzK, 1)));
   SDP_TRY(h->allocT(&h->KZ, (size_t)n * n));
@@ -402,7 +440,7 @@ static sdp_status precond_alloc(sdp_problem* h) {
   SDP_TRY(h->allocT(&h->pvec, std::max<size_t>(nk, (size_t)h->nnzV)));
   SDP_TRY(h->allocT(&h->trpart, std::max(trmv_part_doubles((int)nk), (size_t)TS_CHUNKS * nk)));
   SDP_TRY(h->allocT(&h->info, 8));
-  const size_t wneed = std::max(std::max(potrf_work_doubles((int)nk), trsm_work_doubles((int)nk, (int)nk)),
+  const size_t wneed = std::max(std::max(potrf_work_doubles((int)nkc), trsm_work_doubles((int)nkc, (int)nkc)),
                                 std::max(potrf_work_doubles(n), trsm_work_doubles(n, n)));
   if (wneed > h->work_doubles) {
     SDP_TRY(h->allocT(&h->work, wneed));
@@ -412,6 +450,7 @@ static sdp_status precond_alloc(sdp_problem* h) {
   if (!h->eig_base) {
     SDP_TRY(h->alloc(&h->eig_base, eig_work_bytes(n, true)));
     eig_work_carve(&h->eig, h->eig_base, n, true);
+    h->eig.spin_cycles = h->prm.wait_cycles;
   }
   return SDP_OK;
 }
@@ -450,11 +489,35 @@ sdp_status precond_build_impl(sdp_problem* h) {
   SDP_TRY(precond_alloc(h));
   cudaStream_t st = h->stream;
   const int n = h->n;
-  const int k = (h->prm.precond == SDP_PRECOND_DIAG) ? 0 : std::min(h->k, n - 1 > 0 ? n - 1 : 0);
-  const int nk = n * k;
-  // ---- step 1a: eigenvalues of W (smallest and top k with vectors)
+  const bool diag = (h->prm.precond == SDP_PRECOND_DIAG);
+  const bool adaptive = !diag && h->prm.eta > 0.0;
+  // eigenpairs to compute: the fixed k, or kcap + 1 for the adaptive rule
+  const int kq = diag ? 0 : std::min(adaptive ? h->kcap + 1 : h->k, n - 1 > 0 ? n - 1 : 0);
+  // ---- step 1a: eigenvalues of W (smallest and top kq with vectors)
   copy2d(st, n, n, h->W, n, h->M1, n);
-  SDP_TRY(eig_extremes(st, n, h->M1, k, h->tau_dev, h->wtop, h->Etop, &h->eig));
+  SDP_TRY(eig_extremes(st, n, h->M1, kq, h->tau_dev, h->wtop, h->Etop, &h->eig));
+  int k = kq;
+  if (adaptive) {
+    // Section V implementation notes: k~ = max{i <= k_max : lambda_i >= eta lambda_{i+1}},
+    // eigenvalues in decreasing order, lambda_0 = +inf (so i = 0 always qualifies);
+    // wtop holds lambda_{kq}..lambda_1 in ascending order
+    double lam[SDP_K_MAX + 1];
+    SDP_CK(h, cudaMemcpyAsync(lam, h->wtop, kq * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SDP_CK(h, cudaStreamSynchronize(st));
+    k = 0;
+    for (int i = 1; i <= std::min(h->kcap, kq - 1); ++i)
+      if (lam[kq - i] >= h->prm.eta * lam[kq - 1 - i]) k = i;
+    h->kest = k;
+    if (k > 0 && k < kq) {
+      // keep the top k pairs at the front of Etop / wtop (rows kq - k .. kq - 1)
+      SDP_CK(h, cudaMemcpyAsync(h->Bn, h->Etop + (size_t)(kq - k) * n, (size_t)k * n * sizeof(double),
+                                cudaMemcpyDeviceToDevice, st));
+      SDP_CK(h, cudaMemcpyAsync(h->Etop, h->Bn, (size_t)k * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      SDP_CK(h, cudaMemcpyAsync(h->Bn, h->wtop + (kq - k), k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      SDP_CK(h, cudaMemcpyAsync(h->wtop, h->Bn, k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  const int nk = n * k;
   if (k > 0) {
     // refine Etop (k x n): two subspace steps with W, then Rayleigh-Ritz
     double* V = h->Bn;            // k x n scratch (Bn holds n k doubles)
@@ -531,8 +594,14 @@ sdp_status precond_build_impl(sdp_problem* h) {
   return SDP_OK;
 }
 
+// prec != SDP_FP64 with the Hhat core: the two dense triangular products of the
+// core solve read the FP32 copy of the Schur-factor inverse (schur_apply); every
+// other step, and the whole Algorithm 1 apply, runs in FP64.
 sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int prec, double* dot_out) {
-  (void)prec;  // the apply runs in FP64; reduced precision is confined to the matvec
+  if (prec != SDP_FP64 && prec != SDP_FP32 && prec != SDP_BF16) {
+    h->last_error = "precond_apply: unknown precision";
+    return SDP_ERR_ARG;
+  }
   cudaStream_t st = h->stream;
   const int n = h->n, m = h->m, k = h->kpc, nk = n * k;
   const double inv_tau2 = 1.0 / (h->tau * h->tau);
@@ -546,9 +615,13 @@ sdp_status precond_apply_impl(sdp_problem* h, const double* r, double* z, int pr
     // u = sqrt(2 tau) (sum g_i r_i A_i) U (k x n); S^{-1} u through the block
     // factors, returned as ZS = sqrt(2 tau) S_mat (n x k)
     count_launch();
-    k_hat_u<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, k, h->rowptr, h->colidx, h->sptr, h->scon, h->scoef,
-                                                       h->ginv, r, h->U, h->zscale, h->uvec);
-    SDP_TRY(schur_apply(h, h->uvec, h->Bn, h->zscale));
+    if (k > 8)
+      k_hat_u_gen<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, k, h->rowptr, h->colidx, h->sptr, h->scon,
+                                                             h->scoef, h->ginv, r, h->U, h->zscale, h->uvec);
+    else
+      k_hat_u<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, k, h->rowptr, h->colidx, h->sptr, h->scon, h->scoef,
+                                                         h->ginv, r, h->U, h->zscale, h->uvec);
+    SDP_TRY(schur_apply(h, h->uvec, h->Bn, h->zscale, prec));
   } else {
     // u = Z^T (sum g_i r_i A_i) U, stored as k x n (row l = column l of u)
     assemble_V(h, r, h->ginv, h->pvec);

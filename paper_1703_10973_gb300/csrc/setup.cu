@@ -34,8 +34,23 @@ sdp_status sdp_problem::alloc(void** p, size_t bytes) {
     return SDP_ERR_OOM;
   }
   owned.push_back(*p);
+  owned_bytes.push_back(bytes);
   device_bytes += (int64_t)bytes;
   return SDP_OK;
+}
+
+void sdp_problem::release(void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < owned.size(); ++i) {
+    if (owned[i] != p) continue;
+    cudaFree(p);
+    device_bytes -= (int64_t)owned_bytes[i];
+    owned[i] = owned.back();
+    owned.pop_back();
+    owned_bytes[i] = owned_bytes.back();
+    owned_bytes.pop_back();
+    return;
+  }
 }
 
 extern "C" void sdp_default_params(sdp_params* p) {
@@ -54,6 +69,9 @@ extern "C" void sdp_default_params(sdp_params* p) {
   p->verbose = 0;
   p->pcg_graph = 1;
   p->inner_rtol_lp = 1e-4;
+  p->wait_cycles = 0;
+  p->k_max = 0;
+  p->eta = 0.0;
 }
 
 extern "C" const char* sdp_status_str(sdp_status s) {
@@ -349,6 +367,13 @@ extern "C" sdp_status sdp_setup(int n, int m, int64_t nnzC, const int32_t* Ci, c
   if (prm) h->prm = *prm;
   else sdp_default_params(&h->prm);
   h->k = (h->prm.k > 0) ? std::min(h->prm.k, n) : k;
+  if (h->k > SDP_K_MAX || h->prm.k_max < 0 || h->prm.k_max > SDP_K_MAX || !(h->prm.eta >= 0.0)) {
+    delete h;
+    return SDP_ERR_ARG;
+  }
+  // the adaptive rule (eta > 0) picks the split rank per build, up to k_max (or k)
+  h->kcap = (h->prm.eta > 0.0 && h->prm.k_max > 0) ? h->prm.k_max : h->k;
+  h->kcap = std::max(0, std::min(h->kcap, n - 1));
   h->stream = (cudaStream_t)cuda_stream;
   h->launches_at_setup = g_launches.load();
   sdp_status s = build(h, nnzC, Ci, Cj, Cv, nnzA, Ak, Ai, Aj, Av, b);
@@ -397,6 +422,13 @@ extern "C" sdp_status sdp_set_state(sdp_problem* h, const double* X_host, const 
   h->iter = iter;
   h->chol_valid = false;
   h->pc_valid = false;
+  return SDP_OK;
+}
+
+extern "C" sdp_status sdp_get_state(sdp_problem* h, double* X_host, double* y_host, double* S_host, int* iter) {
+  if (!h) return SDP_ERR_ARG;
+  SDP_TRY(sdp_get_solution(h, X_host, y_host, S_host));
+  if (iter) *iter = h->iter;
   return SDP_OK;
 }
 

@@ -158,6 +158,16 @@ extern "C" sdp_status sdp_hessian_matvec_static(int n, int m, int64_t nnzA, cons
   if (nnzA > 0 && (!Ak_dev || !Ai_dev || !Aj_dev || !Av_dev))
     return fail(SDP_ERR_ARG, "hessian_matvec_static: null triplet pointer");
   if (!W_dev || !v_dev || !Hv_dev) return fail(SDP_ERR_ARG, "hessian_matvec_static: null W, v or Hv pointer");
+  // Hv is cleared before v and W are read, so it may share no byte with them
+  auto overlap = [](const void* a, size_t na, const void* b, size_t nb) {
+    const char *pa = static_cast<const char*>(a), *pb = static_cast<const char*>(b);
+    return pa < pb + nb && pb < pa + na;
+  };
+  const size_t hv_bytes = (size_t)m * sizeof(double);
+  if (overlap(Hv_dev, hv_bytes, v_dev, (size_t)m * sizeof(double)) ||
+      overlap(Hv_dev, hv_bytes, W_dev, (size_t)n * n * sizeof(double)))
+    return fail(SDP_ERR_ARG, "hessian_matvec_static: Hv overlaps v or W (the output is cleared before the "
+                             "inputs are read)");
   double* scratch = nullptr;
   unsigned long long* skipped_dev = nullptr;
   cudaError_t e = static_scratch(&scratch, &skipped_dev);

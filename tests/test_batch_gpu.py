@@ -25,7 +25,7 @@ def _instances():
     return [si.mc_instance(s["p"], s["q"], s["r"], s["m"], s["seed"]) for s in specs]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 def test_batch_equals_alone(prec):
     """Batched kernels under the batch graph, and a solve on its own (which runs
     its Newton systems through a one-problem batch), both equal the
@@ -62,21 +62,22 @@ def test_batch_equals_alone(prec):
             assert np.array_equal(xa, xb)
 
 
-def test_batch_rejects_unsupported_precision():
+def test_batch_rejects_unsupported_preconditioner():
+    """Batched PCG applies the Hhat preconditioner only; Algorithm 1's dense core is refused."""
     from paper_1703_10973_gb300 import SDPBatch, SDPProblem, default_params
     from paper_1703_10973_gb300._lib import SDPError
     d = _instances()[0]
-    with SDPProblem.from_data(d, params=default_params(prec="bf16")) as p:
+    with SDPProblem.from_data(d, params=default_params(precond=1)) as p:
         with pytest.raises(SDPError):
             SDPBatch([p])
 
 
 def test_batch_mixed_precisions_match_oracle():
-    """FP32 and FP64 problems in one batch; each reaches the oracle's optimum."""
+    """FP32, FP64 and BF16 problems in one batch; each reaches the oracle's optimum."""
     from oracle import sdp_oracle as o
     from paper_1703_10973_gb300 import SDPBatch, SDPProblem, default_params
     insts = _instances()[1:4]
-    precs = ["fp32", "fp64", "fp32"]
+    precs = ["fp32", "fp64", "bf16"]
     probs = [SDPProblem.from_data(d, params=default_params(prec=pr)) for d, pr in zip(insts, precs)]
     with SDPBatch(probs) as b:
         res = b.solve()

@@ -249,7 +249,31 @@ def test_pcg_host_loop_matches_graph_loop():
     assert np.array_equal(out[0][0], out[1][0])
 
 
-@pytest.mark.parametrize("prec,mu", [("fp32", 1e-3), ("bf16", 1e-1)])
+@pytest.mark.parametrize("mu", [1e-1, 1e-3])
+def test_precond_apply_fp32_core_close_to_fp64(mu):
+    """prec = SDP_FP32 in sdp_precond_apply: the Hhat core solve reads the FP32 copy
+    of the Schur-factor inverse.  Rounding L_C^{-1} to FP32 perturbs the core solve
+    by about kappa(core) 2^-24 relative, so the applied z stays within
+    20 kappa(Hhat) 2^-24 of the exact z (the oracle's dense solve with eq. sparse_prec)."""
+    d = si.mc_instance(30, 26, 2, 400, 12)
+    P = o.Problem.from_data(d)
+    W = _ipm_like_W(d.n, 2, mu, 3)
+    pc = o.precond_hat_build(P, W, 2)
+    Hh = o.precond_dense(P, pc)
+    r = si.random_vec(d.m, 2)
+    zref = np.linalg.solve(Hh, r)
+    with _prob(d, precond=2) as prob:
+        prob.set_W(_dev(W))
+        prob.precond_build()
+        z32 = prob.precond_apply(_dev(r), prec="fp32").cpu().numpy()
+        z64 = prob.precond_apply(_dev(r), prec="fp64").cpu().numpy()
+    tol = 20.0 * np.linalg.cond(Hh) * 2.0 ** -24
+    assert 0.0 < _rel(z32, z64) <= tol            # a different (float) product ran
+    assert _rel(z32, zref) <= tol
+    assert _rel(z64, zref) <= max(1e-12, 20.0 * np.linalg.cond(Hh) * np.finfo(float).eps)
+
+
+@pytest.mark.parametrize("prec,mu", [("fp32", 1e-3), ("bf16", 1e-1), ("bf16", 1e-5), ("fp32", 1e-6)])
 def test_pcg_reduced_precision_refined_to_fp64(prec, mu):
     d = si.mc_instance(12, 14, 2, 100, 10)
     P = o.Problem.from_data(d)
@@ -262,7 +286,12 @@ def test_pcg_reduced_precision_refined_to_fp64(prec, mu):
         y, its, rel, st = prob.pcg_solve(_dev(r), rtol=1e-8, maxit=2000, prec=prec)
     y = y.cpu().numpy()
     assert rel <= 1e-8
-    assert np.linalg.norm(H @ y - r) <= 1.01e-8 * np.linalg.norm(r)
+    # The oracle's residual H y - r is itself computed in FP64: each entry of H y
+    # carries a rounding error up to m eps (|H| |y|)_i (the standard bound for a
+    # dot product of length m), which near the optimum (|H| ~ 1/mu^2) is no
+    # longer small against 1e-8 ||r||.
+    slack = d.m * np.finfo(float).eps * np.linalg.norm(np.abs(H) @ np.abs(y))
+    assert np.linalg.norm(H @ y - r) <= 1.01e-8 * np.linalg.norm(r) + slack
 
 
 # --------------------------------------------------------------------------
@@ -355,6 +384,23 @@ def test_solve_general_sparse_planted():
     assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6 and cert["relgap"] <= 1e-6
 
 
+# The recovered matrix is held to 1e-5 relative Frobenius error.  A relative gap
+# of 1e-6 bounds the objective, not the distance of the iterate to the optimum
+# (near a rank-r optimum that distance shrinks only like the square root of mu),
+# so the GPU solves run to the accuracy of the paper's experiments (Section VI
+# reports 8 to 10 digits): gap and infeasibilities <= 1e-8.  The explicit-Hessian
+# oracle cannot follow there: kappa(H) grows like 1/mu^2 and its Cholesky of H
+# breaks down before mu reaches 1e-9, so it stops at the 1e-6 of the north-star
+# tolerance.  In the exact-recovery regime the optimum is the planted M, which
+# pins the 1e-8 solve; the oracle pins the objective.
+TIGHT = dict(gap_tol=1e-8, infeas_tol=1e-8)
+
+
+def _gap_abs(r):
+    """Absolute duality gap implied by a result's relative gap (the relgap definition)."""
+    return r["relgap"] * (1.0 + abs(r["obj_p"]) + abs(r["obj_d"]))
+
+
 @pytest.mark.parametrize("idx", [3, 14])
 def test_solve_batched_instance_matches_oracle(idx):
     """Batched-workload instances (n >= 64: Lanczos step lengths, Hhat preconditioner,
@@ -364,13 +410,144 @@ def test_solve_batched_instance_matches_oracle(idx):
     P = o.Problem.from_data(d)
     ref = o.ipm_solve(P)
     assert ref.converged
+    M = d.meta["M"]
+    with _prob(d, **TIGHT) as prob:
+        res = prob.solve()
+        X, y, S = prob.get_solution()
+    assert res["converged"] and res["relgap"] <= 1e-8
+    # both objectives lie within their own duality gaps of the optimal value
+    ref_gap = ref.relgap * (1.0 + abs(ref.obj_p) + abs(ref.obj_d))
+    assert abs(res["obj_p"] - ref.obj_p) <= _gap_abs(res) + ref_gap
+    assert abs(res["obj_p"] - ref.obj_p) <= 1e-6 * abs(ref.obj_p)
+    Z = o.mc_recovered(P, X)
+    assert _rel(Z, M) <= 1e-5
+    # the oracle's 1e-6 point is as close to M as its gap allows, and so to Z
+    assert _rel(Z, o.mc_recovered(P, ref.X)) <= 1e-5 + _rel(o.mc_recovered(P, ref.X), M)
+    cert = o.kkt_certificate(P, X, y, S)
+    assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6 and cert["relgap"] <= 1e-6
+
+
+def test_solve_batched_B0_recovers_planted_matrix():
+    """B0 (n = 565, m = 37202), the largest instance of the bench batch, is beyond the
+    explicit-Hessian oracle on test time (an m x m Cholesky of 1.7e13 flops per
+    iteration).  It is pinned by what the mathematics fixes instead: in the exact
+    recovery regime of Section V-A the optimum is the planted M, its objective is
+    ||M||_* (sum of singular values, numpy SVD), and the FP64 KKT certificate holds."""
+    s = si.batched_specs(256)[0]
+    d = si.mc_instance(s["p"], s["q"], s["r"], s["m"], s["seed"])
+    assert d.n == 565
+    P = o.Problem.from_data(d)
+    M = d.meta["M"]
+    nuc = float(np.linalg.svd(M, compute_uv=False).sum())
+    with _prob(d, **TIGHT) as prob:
+        res = prob.solve()
+        X, y, S = prob.get_solution()
+    assert res["converged"] and res["relgap"] <= 1e-8
+    assert abs(res["obj_p"] - nuc) <= 1e-6 * nuc
+    assert _rel(o.mc_recovered(P, X), M) <= 1e-5
+    cert = o.kkt_certificate(P, X, y, S)
+    assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6 and cert["relgap"] <= 1e-6
+    assert cert["lmin_X"] >= -1e-8 * np.abs(X).max() and cert["lmin_S"] >= -1e-8 * np.abs(S).max()
+
+
+# --------------------------------------------------------------------------
+# orders above 1024: the cooperative-grid tridiagonalisation and the large
+# dense factorisations
+# --------------------------------------------------------------------------
+
+def test_solve_maxcut_above_1024_matches_oracle_and_closed_form():
+    """Bipartite max-cut with n = 1100 (> 1024, so every eigendecomposition runs the
+    cooperative-grid tridiagonalisation): the optimum is X = z z^T with value -2|E|,
+    and the oracle (explicit Hessian, m = n) reaches the same objective."""
+    d = si.maxcut_bipartite_instance(550, 550, 7, extra_edges=1500)
+    assert d.n > 1024
+    P = o.Problem.from_data(d)
+    ref = o.ipm_solve(P)
+    assert ref.converged
     with _prob(d) as prob:
         res = prob.solve()
         X, y, S = prob.get_solution()
     assert res["converged"] and res["relgap"] <= 1e-6
-    assert abs(res["obj_p"] - ref.obj_p) <= 1e-6 * abs(ref.obj_p)
-    Z = o.mc_recovered(P, X)
-    assert _rel(Z, o.mc_recovered(P, ref.X)) <= 1e-4
-    assert _rel(Z, d.meta["M"]) <= 1e-4
+    ne = d.meta["n_edges"]
+    # each objective lies within its own duality gap of the optimal value -2|E|
+    ref_gap = ref.relgap * (1.0 + abs(ref.obj_p) + abs(ref.obj_d))
+    assert abs(res["obj_p"] - ref.obj_p) <= _gap_abs(res) + ref_gap
+    assert abs(res["obj_p"] + 2 * ne) <= 1e-6 * 2 * ne
+    z = d.meta["z"]
+    assert np.abs(X - np.outer(z, z)).max() <= 1e-3
+    cert = o.kkt_certificate(P, X, y, S)
+    assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6
+
+
+def test_solve_mc_above_1024_recovers_planted_matrix():
+    """Matrix completion with n = 1040 in the exact-recovery regime (m from the
+    batched sampling rule, 21,675 observations): the solve recovers the planted M
+    to 1e-5 and its objective is ||M||_*.  (The explicit-Hessian oracle would
+    factor a 21,675-order matrix every iteration; the recovery, the nuclear norm
+    and the KKT certificate pin the result instead.)"""
+    m = si.mc_m_rule(520, 520, 1)
+    d = si.mc_instance(520, 520, 1, m, 1041)
+    assert d.n > 1024
+    P = o.Problem.from_data(d)
+    M = d.meta["M"]
+    nuc = float(np.linalg.svd(M, compute_uv=False).sum())
+    with _prob(d, **TIGHT) as prob:
+        res = prob.solve()
+        X, y, S = prob.get_solution()
+    assert res["converged"]
+    assert abs(res["obj_p"] - nuc) <= 1e-6 * nuc
+    assert _rel(o.mc_recovered(P, X), M) <= 1e-5
     cert = o.kkt_certificate(P, X, y, S)
     assert cert["pinf"] <= 1e-6 and cert["dinf"] <= 1e-6 and cert["relgap"] <= 1e-6
+
+
+# --------------------------------------------------------------------------
+# adaptive split rank (Section V implementation notes)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("eta,kmax", [(10.0, 12), (3.0, 12), (3.0, 4), (1.5, 20)])
+def test_adaptive_rank_matches_oracle_rule(eta, kmax):
+    """With eta > 0 the preconditioner build takes k~ = max{i <= k_max : lambda_i >=
+    eta lambda_{i+1}} from the GPU eigenvalues of W; on a W with a prescribed
+    spectrum it equals the oracle's rank_estimate (pinned on known spectra in the
+    CPU tests), and the apply with that rank matches the oracle's Hhat solve."""
+    d = si.mc_instance(40, 36, 3, 700, 19)
+    P = o.Problem.from_data(d)
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((d.n, d.n)))
+    top = np.array([400.0, 350.0, 90.0, 80.0, 70.0, 20.0, 18.0, 17.0, 5.0, 4.5, 4.0, 3.9, 3.8])
+    ev = np.concatenate([top, rng.uniform(1.0, 1.2, d.n - top.size)])
+    W = (Q * ev) @ Q.T
+    want = o.rank_estimate(W, kmax, eta)
+    with _prob(d, precond=2, k_max=kmax, eta=eta) as prob:
+        prob.set_W(_dev(W))
+        prob.precond_build()
+        tau, k = prob.precond_info()
+        r = si.random_vec(d.m, 4)
+        z = prob.precond_apply(_dev(r)).cpu().numpy()
+    assert k == want
+    pc = o.precond_hat_build(P, W, want)
+    Hh = o.precond_dense(P, pc)
+    tol = max(1e-12, 20.0 * np.linalg.cond(Hh) * np.finfo(float).eps)
+    assert _rel(z, np.linalg.solve(Hh, r)) <= tol
+
+
+def test_hhat_core_above_eight_matches_oracle():
+    """Split rank 20 (above the batched kernels' 8): the general-k formation,
+    factorisation and solve of the Hhat core give the oracle's dense solve."""
+    d = si.mc_instance(30, 34, 4, 900, 23)
+    P = o.Problem.from_data(d)
+    W = _ipm_like_W(d.n, 20, 1e-3, 8)
+    pc = o.precond_hat_build(P, W, 20)
+    Hh = o.precond_dense(P, pc)
+    r = si.random_vec(d.m, 6)
+    with _prob(d, precond=2, k=20) as prob:
+        prob.set_W(_dev(W))
+        prob.precond_build()
+        tau, k = prob.precond_info()
+        z = prob.precond_apply(_dev(r)).cpu().numpy()
+        z32 = prob.precond_apply(_dev(r), prec="fp32").cpu().numpy()
+    assert k == 20
+    kap = np.linalg.cond(Hh)
+    assert _rel(z, np.linalg.solve(Hh, r)) <= max(1e-12, 20.0 * kap * np.finfo(float).eps)
+    assert _rel(z32, np.linalg.solve(Hh, r)) <= 20.0 * kap * 2.0 ** -24

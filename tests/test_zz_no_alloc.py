@@ -63,3 +63,66 @@ def test_static_rejects_oversize_n():
     v = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(L.SDPError, match="SDP_STATIC_MAX_N"):
         hessian_matvec_static(n, 1, z, z, z, v, W, v)
+
+
+def test_static_at_max_n_matches_handle_and_oracle():
+    """n = SDP_STATIC_MAX_N fills the whole static scratch; the result agrees with
+    the handle matvec and with the oracle's explicit H (closed form of eq. hesseqn2
+    for one symmetric pair per constraint) times v."""
+    from oracle import sdp_oracle as o
+    from paper_1703_10973_gb300 import _lib as L
+    from paper_1703_10973_gb300 import SDPProblem, hessian_matvec_static
+    n = L.SDP_STATIC_MAX_N
+    d = si.mc_instance(n // 2, n // 2, 2, 3000, 17)
+    assert d.n == n
+    Wn = _spd(d.n, 13)
+    W = torch.from_numpy(Wn).cuda().reshape(-1).contiguous()
+    trip = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.int32)).cuda() for x in (d.Ak, d.Ai, d.Aj)]
+    Av = torch.from_numpy(np.ascontiguousarray(d.Av, dtype=np.float64)).cuda()
+    vn = si.random_vec(d.m, 3)
+    v = torch.from_numpy(vn).cuda()
+    with SDPProblem.from_data(d) as prob:
+        prob.set_W(W)
+        ref = prob.hessian_matvec(v).cpu().numpy()
+    got = hessian_matvec_static(d.n, d.m, *trip, Av, W, v).cpu().numpy()
+    assert _rel(got, ref) <= 1e-12
+    P = o.Problem.from_data(d)
+    exact = o.hessian_auto(P, Wn) @ vn
+    assert _rel(got, exact) <= 1e-12
+
+
+def test_static_reports_out_of_range_triplets():
+    """An index past n is skipped by the kernels (no access), counted and reported."""
+    from paper_1703_10973_gb300 import _lib as L
+    from paper_1703_10973_gb300 import hessian_matvec_static
+    d = si.mc_instance(20, 30, 1, 200, 9)
+    Ai = np.ascontiguousarray(d.Ai, dtype=np.int32).copy()
+    Ai[7] = d.n + 5
+    trip = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.int32)).cuda() for x in (d.Ak, Ai, d.Aj)]
+    Av = torch.from_numpy(np.ascontiguousarray(d.Av, dtype=np.float64)).cuda()
+    W = torch.from_numpy(_spd(d.n, 2)).cuda().reshape(-1).contiguous()
+    v = torch.from_numpy(si.random_vec(d.m, 1)).cuda()
+    with pytest.raises(L.SDPError, match="1 triplets had an index out of range"):
+        hessian_matvec_static(d.n, d.m, *trip, Av, W, v)
+    torch.cuda.synchronize()
+
+
+def test_static_rejects_aliased_output():
+    """Hv is cleared before v is read: an output that overlaps v is refused."""
+    from paper_1703_10973_gb300 import _lib as L
+    from paper_1703_10973_gb300 import hessian_matvec_static
+    import ctypes as C
+    d = si.mc_instance(10, 12, 1, 60, 3)
+    trip = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.int32)).cuda() for x in (d.Ak, d.Ai, d.Aj)]
+    Av = torch.from_numpy(np.ascontiguousarray(d.Av, dtype=np.float64)).cuda()
+    W = torch.from_numpy(_spd(d.n, 2)).cuda().reshape(-1).contiguous()
+    v = torch.from_numpy(si.random_vec(d.m, 1)).cuda()
+    with pytest.raises(ValueError, match="must not be v"):
+        hessian_matvec_static(d.n, d.m, *trip, Av, W, v, out=v)
+    lib = L.load()
+    st = lib.sdp_hessian_matvec_static(d.n, d.m, int(Av.numel()), C.c_void_p(trip[0].data_ptr()),
+                                       C.c_void_p(trip[1].data_ptr()), C.c_void_p(trip[2].data_ptr()),
+                                       C.c_void_p(Av.data_ptr()), C.c_void_p(W.data_ptr()),
+                                       C.c_void_p(v.data_ptr()), C.c_void_p(v.data_ptr() + 8), None)
+    assert st == L.SDP_ERR_ARG
+    assert b"overlaps" in lib.sdp_last_error(None)
