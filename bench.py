@@ -481,7 +481,10 @@ def run(args):
                 "ipm_iters_mean": float(np.mean([r["iters"] for r in res])),
                 "pcg_iters_per_solve_mean": float(np.mean([r["pcg_iters_total"] for r in res])),
                 "gpu_launches": int(launches[arm.prec]),
-                "stage_ms_last_step": arm.stage_ms or None}
+                "stage_ms_last_step": arm.stage_ms or None,
+                "spmm_autotune": ({"rows_per_cta": arm.batch.tuning()[0],
+                                   "ms_per_launch": {str(k): round(v, 4) for k, v in arm.batch.tuning()[1].items()}}
+                                  if arm.batch is not None else None)}
         errs = []
         for i, d in enumerate(insts):
             Z = _recovered(d, Xs[i])
@@ -600,14 +603,22 @@ def run_e2e(args, insts, head):
 
 
 def run_serving(args):
-    """Poisson request stream (the serving specs: p, q log-uniform, r in 1..5), continuous
-    batching with admission by a device-memory budget; the arrival rate is swept as
-    fractions of the capacity measured with every request present at time 0."""
+    """Poisson request stream (the serving specs: p, q log-uniform in [50, 3000], r in
+    1..5), served by continuous batching (BatchServer: requests join running lockstep
+    batches at IPM-iteration boundaries and share every batched PCG launch), with
+    admission by a device-memory budget.  Each arm (--arms) first serves every
+    request at t = 0 (its capacity), then the arrival rate is swept as fractions of
+    that capacity.  Under torchrun each rank serves the requests with rid % world ==
+    rank; the line reports rank 0's requests and the whole job's completions."""
     import torch
     import sdp_inputs as si
-    from paper_1703_10973_gb300 import _build, load
-    from paper_1703_10973_gb300.serve import Request, Server, cuda_solver
+    from paper_1703_10973_gb300 import _build, default_params, load
+    from paper_1703_10973_gb300.serve import BatchServer, Request
     ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     if not os.path.exists(_build.LIB):
         _build.build()
@@ -616,36 +627,115 @@ def run_serving(args):
     insts = [si.mc_instance(s["p"], s["q"], s["r"], s["m"], s["seed"]) for s in specs]
     free, total = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
-    solver = cuda_solver()
-
-    def once(arrivals):
-        srv = Server(budget_bytes=budget, slots=args.streams, solver=solver)
-        res = srv.run([Request(rid=i, data=d, arrival=float(a)) for i, (d, a) in enumerate(zip(insts, arrivals))])
-        return srv.stats, res
-
-    once([0.0] * len(insts))                         # warm-up (module load, first allocations)
+    precs = [x for x in args.arms.split(",") if x]
+    arms, head_cap = {}, None
     with Clocks(local) as clk:
-        cap_stats, cap_res = once([0.0] * len(insts))
-        cap = cap_stats["solves_per_s"]
-        sweep = [dict(rate="all at t=0", **{k: cap_stats[k] for k in ("solves_per_s", "p50_ms", "p99_ms",
-                                                                       "max_concurrent")})]
-        for f in [float(x) for x in args.rates.split(",") if x]:
-            rate = f * cap
-            arr = si.serving_arrivals(len(insts), rate)
-            st, _ = once(arr)
-            sweep.append(dict(rate=rate, rate_frac=f, **{k: st[k] for k in ("solves_per_s", "p50_ms", "p99_ms",
-                                                                             "max_concurrent")}))
+        for prec in precs:
+            extra = {"inner_rtol_lp": args.inner_lp} if args.inner_lp > 0 else {}
+            params = default_params(prec=prec, pcg_maxit=args.pcg_maxit, **extra)
+
+            def once(arrivals):
+                srv = BatchServer(budget_bytes=budget, groups=args.batch_groups or 4, params=params, rank=rank,
+                                  world=ws)
+                res = srv.run([Request(rid=i, data=d, arrival=float(a))
+                               for i, (d, a) in enumerate(zip(insts, arrivals))])
+                return srv.stats, res
+
+            once([0.0] * len(insts))   # warm-up: module load, first allocations, graph captures
+            cap_stats, cap_res = once([0.0] * len(insts))
+            cap = cap_stats["solves_per_s"]
+            done = cap_stats["completed"]
+            if dist is not None:
+                cap = max_over_ranks(-cap, dist, "cuda") * -1.0   # the slowest rank's rate
+            sweep = [dict(rate="all at t=0", **{k: cap_stats[k] for k in ("solves_per_s", "p50_ms", "p99_ms",
+                                                                           "max_concurrent")})]
+            for f in [float(x) for x in args.rates.split(",") if x]:
+                rate = f * cap_stats["solves_per_s"] * ws
+                st, _ = once(si.serving_arrivals(len(insts), rate))
+                sweep.append(dict(rate=rate, rate_frac=f, **{k: st[k] for k in ("solves_per_s", "p50_ms", "p99_ms",
+                                                                                 "max_concurrent")}))
+            arms[prec] = {"value": cap * ws, "unit": UNIT, "latency_ms": {"p50": cap_stats["p50_ms"],
+                                                                          "p99": cap_stats["p99_ms"]},
+                          "converged": all(r.converged for r in cap_res if r.ok), "completed_rank0": done,
+                          "lockstep_steps": cap_stats["lockstep_steps"], "sweep": sweep,
+                          "obj": {r.rid: r.obj_p for r in cap_res if r.ok}}
+            if head_cap is None:
+                head_cap = arms[prec]["value"]
+    ref = arms.get("fp64")
+    for prec, a in arms.items():
+        if ref is not None and a is not ref:
+            a["max_rel_obj_err_vs_fp64"] = max(abs(a["obj"][i] - ref["obj"][i]) / abs(ref["obj"][i])
+                                               for i in a["obj"] if i in ref["obj"])
+    for a in arms.values():
+        a.pop("obj")
     if rank == 0:
-        line = {"metric": METRIC, "value": cap, "unit": UNIT, "n_gpus": ws, "steps": len(sweep),
-                "warmup": 1, "ms_per_step": 1e3 * len(insts) / cap if cap else None, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"serving: first {len(insts)} of the 2000 served requests with n <= "
-                                       f"{args.serve_max_n} (p, q log-uniform in [50, 3000], r in 1..5, seeds 5000+)",
-                           "slots": args.streams, "budget_bytes": budget,
-                           "converged": all(r.converged for r in cap_res if r.ok),
-                           "completed": cap_stats["completed"]},
-                "latency_ms": {"p50": cap_stats["p50_ms"], "p99": cap_stats["p99_ms"]},
-                "serving_sweep": sweep, "clocks": clk.summary()}
+        head = arms[precs[0]]
+        line = {"metric": METRIC, "value": head_cap, "unit": UNIT, "n_gpus": ws, "steps": len(head["sweep"]),
+                "warmup": 1, "ms_per_step": 1e3 * len(insts) / head_cap if head_cap else None,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPES.get(precs[0], precs[0]), "data": "synthetic",
+                "config": {"workload": f"serving: the first {len(insts)} of the 2000 served requests with n <= "
+                                       f"{args.serve_max_n} (p, q log-uniform in [50, 3000], r in 1..5, seeds 5000+), "
+                                       f"continuous batching in {args.batch_groups or 4} lockstep groups",
+                           "form": FORMS.get(precs[0], precs[0]), "arms": precs, "budget_bytes": budget,
+                           "parallelism": f"replicas{ws}", "routing": "rid % world == rank"},
+                "latency_ms": head["latency_ms"], "arms": arms, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_fig1(args):
+    """The paper's Fig. 1 shapes: matrix completion with k = 1 (rank-1 planted M,
+    p = q = n / 2) and m = 25 n or m = 0.025 n^2 observations, n swept up to
+    --fig1-max-n; per shape, a few interior-point iterations from the start point
+    are timed and the median seconds per iteration reported (the quantity Fig. 1
+    plots), with the PCG iterations they took."""
+    import torch
+    import sdp_inputs as si
+    from paper_1703_10973_gb300 import SDPProblem, _build, default_params, load
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    load()
+    sizes = [n for n in (500, 1000, 2000, 3000, 4000, 5024) if n <= args.fig1_max_n]
+    precs = [x for x in args.arms.split(",") if x]
+    rows = []
+    with Clocks(local) as clk:
+        for n in sizes:
+            p = n // 2
+            for shape, m in (("m=25n", 25 * n), ("m=0.025n^2", int(round(0.025 * n * n)))):
+                m = min(m, p * (n - p))
+                d = si.mc_instance(p, n - p, 1, m, 7000 + n)
+                for prec in precs:
+                    params = default_params(prec=prec, pcg_maxit=args.pcg_maxit)
+                    with SDPProblem.from_data(d, params=params) as prob:
+                        times, pcg = [], []
+                        for it in range(args.fig1_iters + 1):
+                            torch.cuda.synchronize()
+                            t0 = time.perf_counter()
+                            info = prob.ipm_step()
+                            torch.cuda.synchronize()
+                            if it > 0:   # the first iteration includes the first allocations
+                                times.append(time.perf_counter() - t0)
+                                pcg.append(info["pcg_iters_pred"] + info["pcg_iters_corr"])
+                            if info["converged"]:
+                                break
+                    rows.append(dict(n=n, m=m, shape=shape, prec=prec, s_per_ipm_iter=statistics.median(times),
+                                     pcg_iters_per_ipm_iter=float(np.mean(pcg)), iters_timed=len(times)))
+                    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    if rank == 0:
+        big = rows[-1]
+        line = {"metric": "seconds per interior-point iteration (Fig. 1 shapes)", "value": big["s_per_ipm_iter"],
+                "unit": "s", "n_gpus": ws, "steps": args.fig1_iters, "warmup": 1,
+                "ms_per_step": 1e3 * big["s_per_ipm_iter"], "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": DTYPES.get(precs[0], precs[0]), "data": "synthetic",
+                "config": {"workload": "matrix completion, rank 1, p = q = n/2, m = 25n and m = 0.025n^2 "
+                                       f"(the paper's Fig. 1 shapes), n in {sizes}; value: the largest shape",
+                           "arms": precs},
+                "sweep": rows, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -656,7 +746,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "C2", "C3", "fig2", "serving"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "C2", "C3", "fig2", "fig1", "serving"])
+    ap.add_argument("--fig1-max-n", type=int, default=5024, help="fig1: largest SDP order of the sweep")
+    ap.add_argument("--fig1-iters", type=int, default=3, help="fig1: timed interior-point iterations per shape")
     ap.add_argument("--arms", default="fp32,fp64",
                     help="precision forms timed on the same instances; the first is the headline value")
     ap.add_argument("--k", type=int, default=0, help="split rank (0 = the instance's planted rank)")
@@ -687,6 +779,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "fig1":
+        return run_fig1(args)
     return run(args)
 
 

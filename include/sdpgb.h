@@ -24,10 +24,13 @@
  *    SDP_BF16 the Hessian matvec rounds the part W_s of the split W = W_l + W_s
  *    (W_l = the top-k eigenpairs of the last preconditioner build, else W itself)
  *    to float or bfloat16 and accumulates in float, adding the low-rank terms in
- *    double; the Hhat preconditioner apply reads a float copy of its dense
- *    Schur-factor inverse (both SDP_FP32 and SDP_BF16) and accumulates that
- *    product in float.  The Algorithm 1 apply always runs in double.  Vectors
- *    crossing the ABI stay double.
+ *    double.  sdp_precond_apply with SDP_FP32 or SDP_BF16 reads a float copy of
+ *    the Hhat core's dense Schur-factor inverse and accumulates that product in
+ *    float; inside PCG (sdp_pcg_solve, sdp_ipm_step, batches) the core is applied
+ *    in double at every precision, because near the optimum the core has
+ *    kappa ~ 1/mu.  The Algorithm 1 apply always runs in double; with a
+ *    reduced-precision params.prec its core is formed on the tensor cores in TF32
+ *    (sdp_mixed_gemm).  Vectors crossing the ABI stay double.
  */
 #ifndef SDPGB_H
 #define SDPGB_H
@@ -299,6 +302,43 @@ sdp_status sdp_batch_set_groups(sdp_batch* b, int groups);
  * most any problem ran).  With groups, out[0..5] are the slowest group's and
  * out[6..7] the sum over groups.  out: 8 doubles.  SDP_ERR_ARG for NULL. */
 sdp_status sdp_batch_stage_seconds(const sdp_batch* b, double* out);
+/* Autotuner of the batched PCG matvec: the first batched Newton solve times the
+ * SpMM tile (rows of W per CTA, R = 1, 2, 4, 8 within shared memory) on the
+ * batch's own data and keeps the fastest (every R gives the same results).
+ * *spmm_rows = the chosen R (0 before the first solve); ms[0..3] = mean
+ * milliseconds per launch of each candidate (0 = not run).  With lockstep
+ * groups, the first group's choice.  Either pointer may be NULL. */
+sdp_status sdp_batch_tuning(const sdp_batch* b, int* spmm_rows, double* ms);
+
+/*
+ * Continuous batching (serving): members join and leave a batch between
+ * interior-point iterations, and every PCG iteration of the members' Newton
+ * systems shares the batched launches.  A batch made by sdp_batch_create with
+ * count = 0 (problems NULL) starts empty.
+ *   sdp_batch_add     -- the set-up problem h joins, from its current iterate, at
+ *                        the next sdp_batch_step (SDP_ERR_UNSUPPORTED for a
+ *                        configuration the batch cannot run, as sdp_batch_create;
+ *                        SDP_ERR_ARG for a member already present or a batch with
+ *                        lockstep groups from sdp_batch_solve).
+ *   sdp_batch_step    -- one interior-point iteration of every running member in
+ *                        lockstep; *running (may be NULL) = members still running.
+ *                        A member stops running when its iterate meets the
+ *                        tolerances, its ipm_maxit is reached or one of its calls
+ *                        fails; the others carry on.  Returns the first batch-wide
+ *                        failure (a member's own failure is reported by
+ *                        sdp_batch_member).
+ *   sdp_batch_member  -- result of member h (seconds = time since it joined) and
+ *                        its state: 0 running, 1 converged, 2 iteration limit,
+ *                        3 failed (the call then returns that member's status).
+ *   sdp_batch_remove  -- h leaves the batch (finished, or cancelled while running:
+ *                        its iterate stays where the last step left it).
+ * Launch structures and the captured PCG loop are rebuilt at the next step after
+ * a change of membership.  A member's iterates are the same as alone.
+ */
+sdp_status sdp_batch_add(sdp_batch* b, sdp_problem* h);
+sdp_status sdp_batch_step(sdp_batch* b, int* running);
+sdp_status sdp_batch_member(const sdp_batch* b, const sdp_problem* h, sdp_result* r, int* state);
+sdp_status sdp_batch_remove(sdp_batch* b, sdp_problem* h);
 
 /*
  * sdp_hessian_matvec_static -- handle-free, allocation-free variant of
@@ -334,6 +374,29 @@ sdp_status sdp_batch_stage_seconds(const sdp_batch* b, double* out);
 sdp_status sdp_hessian_matvec_static(int n, int m, int64_t nnzA, const int32_t* Ak_dev, const int32_t* Ai_dev,
                                      const int32_t* Aj_dev, const double* Av_dev, const double* W_dev,
                                      const double* v_dev, double* Hv_dev, void* cuda_stream);
+
+/*
+ * sdp_mixed_gemm -- the reduced-precision dense product of the Woodbury core
+ * formation (Algorithm 1 step 2: the blocks Z^T (K_ll' Z)), on the tensor cores:
+ *   C_dev (M x N, FP64, row stride ldc) = op(A) op(B),
+ * op(A) = A (M x K) or A^T when transA (A then K x M), op(B) = B (K x N) or B^T
+ * when transB; all row-major FP64 device arrays.  The operands are rounded to
+ * BF16 (prec = SDP_BF16) or TF32 (prec = SDP_FP32) and the products accumulate
+ * in FP32 (tcgen05.mma), so |C - op(A) op(B)| <= (2u + u^2 + K 2^-24) |op(A)| |op(B)|
+ * entrywise with u = 2^-8 + 2^-24 (BF16) or 2^-11 + 2^-24 (TF32, rounded to
+ * nearest from the FP32 copy).  work_dev: caller-owned device
+ * scratch of at least sdp_mixed_gemm_work_bytes(M, N, K) bytes, 256-byte
+ * aligned.  err_dev: one device int, set to 1 if a bounded wait inside the
+ * kernel ran out (the product is then incomplete).  Issued on cuda_stream,
+ * asynchronous.  SDP_ERR_ARG for bad sizes or pointers, SDP_ERR_UNSUPPORTED
+ * when the driver offers no tensor-map encoder.  A handle whose params.prec is
+ * SDP_FP32 or SDP_BF16 forms its Algorithm 1 core with this product in TF32
+ * (BF16 operands left that core unusable as a preconditioner).
+ */
+int64_t sdp_mixed_gemm_work_bytes(int M, int N, int K);
+sdp_status sdp_mixed_gemm(int prec, int M, int N, int K, const double* A_dev, int lda, int transA,
+                          const double* B_dev, int ldb, int transB, double* C_dev, int ldc,
+                          void* work_dev, int64_t work_bytes, int* err_dev, void* cuda_stream);
 
 void sdp_destroy(sdp_problem* h);
 const char* sdp_status_str(sdp_status s);

@@ -115,6 +115,14 @@ SIGNATURES = {
     "sdp_batch_destroy": (None, [_P]),
     "sdp_batch_stage_seconds": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "sdp_batch_set_groups": (C.c_int, [_P, C.c_int]),
+    "sdp_batch_tuning": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "sdp_batch_add": (C.c_int, [_P, _P]),
+    "sdp_batch_step": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "sdp_batch_member": (C.c_int, [_P, _P, C.POINTER(sdp_result), C.POINTER(C.c_int)]),
+    "sdp_batch_remove": (C.c_int, [_P, _P]),
+    "sdp_mixed_gemm_work_bytes": (C.c_int64, [C.c_int, C.c_int, C.c_int]),
+    "sdp_mixed_gemm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _P, C.c_int, C.c_int, _P, C.c_int, C.c_int,
+                                 _P, C.c_int, _P, C.c_int64, _P, _P]),
     "sdp_destroy": (None, [_P]),
     "sdp_status_str": (C.c_char_p, [C.c_int]),
     "sdp_last_error": (C.c_char_p, [_P]),

@@ -262,10 +262,10 @@ def hessian_matvec_static(n, m, Ak, Ai, Aj, Av, W, v, out=None, stream=None):
 class SDPBatch:
     """sdp_batch_*: solve several SDPProblem objects in lockstep with batched PCG launches."""
 
-    def __init__(self, problems, stream=None, groups=0):
+    def __init__(self, problems=(), stream=None, groups=0):
         self.lib = L.load()
         self.problems = list(problems)
-        arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        arr = (C.c_void_p * max(1, len(self.problems)))(*[p.h.value for p in self.problems])
         if stream is None and torch is not None and torch.cuda.is_available():
             stream = torch.cuda.current_stream().cuda_stream
         b = C.c_void_p()
@@ -285,6 +285,46 @@ class SDPBatch:
             raise L.SDPError(st, f"sdp_batch_solve: {self.lib.sdp_status_str(st).decode()}: "
                                  f"{self.lib.sdp_batch_last_error(self.b).decode()}")
         return [{f: getattr(r, f) for f, _ in L.sdp_result._fields_} for r in res]
+
+    # -- continuous batching: members join and leave between IPM iterations --
+    def add(self, prob):
+        st = self.lib.sdp_batch_add(self.b, prob.h)
+        if st != L.SDP_OK:
+            raise L.SDPError(st, f"sdp_batch_add: {self.lib.sdp_status_str(st).decode()}: "
+                                 f"{self.lib.sdp_batch_last_error(self.b).decode()}")
+        self.problems.append(prob)
+
+    def remove(self, prob):
+        st = self.lib.sdp_batch_remove(self.b, prob.h)
+        if st != L.SDP_OK:
+            raise L.SDPError(st, "sdp_batch_remove")
+        self.problems = [p for p in self.problems if p is not prob]
+
+    def step(self):
+        """One lockstep IPM iteration of every running member; returns how many still run."""
+        run = C.c_int(0)
+        st = self.lib.sdp_batch_step(self.b, C.byref(run))
+        if st != L.SDP_OK:
+            raise L.SDPError(st, f"sdp_batch_step: {self.lib.sdp_status_str(st).decode()}: "
+                                 f"{self.lib.sdp_batch_last_error(self.b).decode()}")
+        return run.value
+
+    def tuning(self):
+        """(chosen SpMM rows per CTA, {R: ms per launch}) of the batch's autotuner."""
+        r = C.c_int(0)
+        ms = (C.c_double * 4)()
+        self.lib.sdp_batch_tuning(self.b, C.byref(r), ms)
+        return r.value, {R: ms[i] for i, R in enumerate((1, 2, 4, 8)) if ms[i] > 0}
+
+    MEMBER_STATES = ("running", "converged", "iteration_limit", "failed")
+
+    def member(self, prob):
+        """(result dict, state name, status) of a member."""
+        r = L.sdp_result()
+        state = C.c_int(0)
+        st = self.lib.sdp_batch_member(self.b, prob.h, C.byref(r), C.byref(state))
+        res = {f: getattr(r, f) for f, _ in L.sdp_result._fields_}
+        return res, self.MEMBER_STATES[state.value], st
 
     STAGES = ("nt_precond", "pcg_pred", "step_pred", "pcg_corr", "step_update", "pcg_graph",
               "graph_launches", "batched_iters")

@@ -60,6 +60,18 @@ struct sdp_batch {
   std::vector<std::vector<int>> members;   // problems of each group
   std::vector<cudaStream_t> child_streams;
   std::string last_error;
+  // per-member interior-point state of the lockstep iterations (indices follow hs)
+  std::vector<sdpgb::IpmStepState> ms;
+  std::vector<sdp_status> mst;
+  std::vector<char> mdone;            // 0 running, 1 converged, 2 iteration limit, 3 error
+  std::vector<int> mpcg, mit, mits;   // PCG iterations so far, IPM iterations in this batch, last solve's
+  std::vector<double> mrr, mstart, mfin;   // last true residual; seconds (from the epoch) joined / finished
+  std::chrono::steady_clock::time_point epoch = std::chrono::steady_clock::now();
+  bool dirty = true;                  // membership changed: offsets and the graph are rebuilt before use
+  int spmm_r = 4;                     // rows of W per CTA of the batched SpMM (autotuned)
+  bool tuned = false;                 // spmm_r chosen for the current members
+  float tune_ms[4] = {};              // measured time per candidate R = 1, 2, 4, 8 (0: not run)
+  int ndesc = 0, noff = 0;            // capacities of ddesc and doff
 };
 
 namespace sdpgb {
@@ -80,10 +92,11 @@ static void batch_offsets(sdp_batch* b) {
   const int N = (int)b->hs.size();
   b->off.assign((size_t)BK_COUNT * (N + 1), 0);
   b->nmax = 0;
+  b->any_lp = false;
   for (int i = 0; i < N; ++i) {
     sdp_problem* h = b->hs[i];
     const int k = std::min(h->kcap, h->n - 1), Rk = h->hs_nr * k;   // grids for the largest rank
-    const int cnt[BK_COUNT] = {batch_blocks_assemble(h->nnzV), batch_blocks_spmm(h->n), batch_blocks_sddmm(h->m),
+    const int cnt[BK_COUNT] = {batch_blocks_assemble(h->nnzV), batch_blocks_spmm(h->n, b->spmm_r), batch_blocks_sddmm(h->m),
                                batch_blocks_vec(h->m),         batch_blocks_hat_u(h->n), batch_blocks_tail(h->m),
                                batch_blocks_fwdP(h->hs_np),    batch_blocks_warp_rows(h->hs_nr),
                                batch_blocks_warp_rows(Rk),     batch_blocks_outR(Rk),
@@ -121,9 +134,9 @@ static BDesc make_desc(sdp_problem* h, int active, int prec) {
   D.W16 = h->W16;
   D.W32 = h->W32; D.T32 = h->T32; D.mvR = h->mv_R; D.mvPart = h->mv_part;
   D.Etop = h->Etop; D.wtop = h->wtop; D.mvG = h->mv_G; D.mvQ = h->mv_Q;
-  // a reduced-precision sweep also solves the core with the FP32 copy of the
-  // Schur-factor inverse (made by pcg_start for this preconditioner)
-  D.lpc = (D.lp && h->hs_Cinv32 && h->hs_lp_gen == h->pc_generation) ? 1 : 0;
+  // the core solve runs in FP64 in every sweep (see pcg_body); the FP32 copy of
+  // the Schur-factor inverse serves sdp_precond_apply with prec != SDP_FP64
+  D.lpc = 0;
   D.Cinv32 = h->hs_Cinv32; D.CinvT32 = h->hs_CinvT32; D.v1f = h->hs_v1f; D.v2f = h->hs_v2f;
   return D;
 }
@@ -159,7 +172,7 @@ static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle
     ktimer_begin(st, "matvec_b");
   }
   batch_launch_matvec(st, b->ddesc, off(BK_ASM), off(BK_SPMM), off(BK_SDDMM), N, b->total[BK_ASM],
-                      b->total[BK_SPMM], b->total[BK_SDDMM], b->nmax);
+                      b->total[BK_SPMM], b->total[BK_SDDMM], b->nmax, b->spmm_r);
   if (mode) ktimer_end(st, "matvec_b", fl, by);
   if (b->any_lp) {  // same SDDMM partition (and reduction groups) as the FP64 form
     if (mode) ktimer_begin(st, "matvec_lp_b");
@@ -178,23 +191,42 @@ static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle
   batch_launch_any(st, b->ddesc, N, cond, flag);
 }
 
+// Block offsets, device tables and the captured loop for the current members;
+// rebuilt after a membership change (continuous batching: sdp_batch_add/remove).
 static sdp_status batch_prepare(sdp_batch* b) {
-  if (b->exec || b->host_loop) return SDP_OK;
+  if (!b->dirty && (b->exec || b->host_loop)) return SDP_OK;
   const int N = (int)b->hs.size();
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->host_loop = false;
   batch_offsets(b);
-  if (cudaMalloc(&b->ddesc, sizeof(BDesc) * N) != cudaSuccess ||
-      cudaMalloc(&b->doff, sizeof(int) * b->off.size()) != cudaSuccess) {
-    cudaGetLastError();
-    b->last_error = "sdp_batch: device allocation failed";
-    return SDP_ERR_OOM;
-  }
-  cudaMemcpy(b->doff, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice);
-  if (b->hs[0]->prm.pcg_graph == 0) {
-    if (cudaMalloc(&b->dflag, sizeof(int) * (N + 1)) != cudaSuccess) {
+  if (N > b->ndesc || (int)b->off.size() > b->noff) {
+    cudaFree(b->ddesc);
+    cudaFree(b->doff);
+    cudaFree(b->dflag);
+    b->ddesc = nullptr;
+    b->doff = nullptr;
+    b->dflag = nullptr;
+    b->ndesc = b->noff = 0;
+    const int cap = std::max(N, 2 * b->ndesc);
+    const size_t offcap = (size_t)BK_COUNT * (cap + 1);
+    if (cudaMalloc(&b->ddesc, sizeof(BDesc) * cap) != cudaSuccess ||
+        cudaMalloc(&b->doff, sizeof(int) * offcap) != cudaSuccess ||
+        cudaMalloc(&b->dflag, sizeof(int) * (cap + 1)) != cudaSuccess) {
       cudaGetLastError();
       b->last_error = "sdp_batch: device allocation failed";
       return SDP_ERR_OOM;
     }
+    b->ndesc = cap;
+    b->noff = (int)offcap;
+  }
+  cudaMemcpy(b->doff, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice);
+  b->dirty = false;
+  b->tuned = b->tuned && b->nmax > 0;
+  if (b->hs[0]->prm.pcg_graph == 0) {
     b->host_loop = true;
     return SDP_OK;
   }
@@ -236,6 +268,68 @@ static sdp_status batch_prepare(sdp_batch* b) {
   return SDP_OK;
 }
 
+// Autotuner of the batched SpMM tile: each candidate R (rows of W per CTA: 1, 2,
+// 4, 8, within shared memory) runs on the batch's own data with the descriptors
+// just uploaded, timed with CUDA events (one warm-up, three timed launches);
+// the fastest is kept and the launch structures are rebuilt for it.  T is
+// scratch of the matvec, recomputed by every real launch, so the trial launches
+// change nothing; every R computes each entry of T by the same FMA sequence.
+static sdp_status batch_autotune(sdp_batch* b, const std::vector<BDesc>& hd) {
+  const int N = (int)b->hs.size();
+  // time the FP64 SpMM with every active problem in an FP64 sweep (problems in a
+  // reduced-precision sweep would return at once), then restore the descriptors
+  std::vector<BDesc> td(hd);
+  for (BDesc& D : td) D.lp = 0;
+  if (cudaMemcpyAsync(b->ddesc, td.data(), sizeof(BDesc) * N, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return SDP_ERR_CUDA;
+  const int cand[4] = {1, 2, 4, 8};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SDP_ERR_CUDA;
+  std::vector<int> off(N + 1, 0);
+  int* doff = nullptr;
+  if (cudaMalloc(&doff, sizeof(int) * (N + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return SDP_ERR_OOM;
+  }
+  float best = 0.f;
+  int best_r = b->spmm_r;
+  for (int c = 0; c < 4; ++c) {
+    const int R = cand[c];
+    b->tune_ms[c] = 0.f;
+    if (!batch_spmm_fits(R, b->nmax)) continue;
+    for (int i = 0; i < N; ++i) off[i + 1] = off[i] + batch_blocks_spmm(b->hs[i]->n, R);
+    cudaMemcpyAsync(doff, off.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, b->stream);
+    batch_launch_spmm(b->stream, R, b->ddesc, doff, N, off[N], b->nmax);
+    cudaEventRecord(e0, b->stream);
+    for (int t = 0; t < 3; ++t) batch_launch_spmm(b->stream, R, b->ddesc, doff, N, off[N], b->nmax);
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    b->tune_ms[c] = ms / 3.f;
+    if (best == 0.f || b->tune_ms[c] < best) {
+      best = b->tune_ms[c];
+      best_r = R;
+    }
+  }
+  cudaMemcpyAsync(b->ddesc, hd.data(), sizeof(BDesc) * N, cudaMemcpyHostToDevice, b->stream);
+  cudaStreamSynchronize(b->stream);
+  cudaFree(doff);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess) {
+    b->last_error = "sdp_batch: SpMM autotuning failed";
+    return SDP_ERR_CUDA;
+  }
+  b->tuned = true;
+  if (best_r != b->spmm_r) {
+    b->spmm_r = best_r;
+    b->dirty = true;
+    SDP_TRY(batch_prepare(b));
+  }
+  return SDP_OK;
+}
+
 // The Newton systems H dy = rhs of the listed problems, solved together.
 static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::vector<int>& its,
                                std::vector<double>& rr, std::vector<sdp_status>& st) {
@@ -270,6 +364,7 @@ static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::v
       b->last_error = std::string("sdp_batch: descriptor upload failed: ") + cudaGetErrorString(cudaGetLastError());
       return SDP_ERR_CUDA;
     }
+    if (!b->tuned) SDP_TRY(batch_autotune(b, hd));
     if (b->host_loop) {
       // flags[0]: some problem active; flags[1 + i]: problem i active (read back
       // after every iteration, so each timed matvec knows its problems)
@@ -349,7 +444,7 @@ static void parallel_for(const std::vector<int>& idx, F fn) {
 using namespace sdpgb;
 
 extern "C" sdp_status sdp_batch_create(sdp_problem* const* hs, int count, void* cuda_stream, sdp_batch** out) {
-  if (!out || !hs || count < 1) return SDP_ERR_ARG;
+  if (!out || count < 0 || (count > 0 && !hs)) return SDP_ERR_ARG;
   *out = nullptr;
   std::string why;
   for (int i = 0; i < count; ++i) {
@@ -359,7 +454,7 @@ extern "C" sdp_status sdp_batch_create(sdp_problem* const* hs, int count, void* 
     if (!batch_supported(hs[i], &why)) return SDP_ERR_UNSUPPORTED;
   }
   sdp_batch* b = new sdp_batch();
-  b->hs.assign(hs, hs + count);
+  if (count > 0) b->hs.assign(hs, hs + count);
   b->stream = static_cast<cudaStream_t>(cuda_stream);
   if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -407,7 +502,7 @@ static sdp_status batch_make_groups(sdp_batch* b, int G) {
 }
 
 extern "C" sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results) {
-  if (!b) return SDP_ERR_ARG;
+  if (!b || b->hs.empty()) return SDP_ERR_ARG;
   const int N = (int)b->hs.size();
   const int G = std::min(N, b->groups > 0 ? b->groups : (N + 1) / 2);
   if (G <= 1) return batch_solve_lockstep(b, results);
@@ -443,91 +538,205 @@ extern "C" sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results) {
   return worst;
 }
 
-static sdp_status batch_solve_lockstep(sdp_batch* b, sdp_result* results) {
+// Member state for a (re)start of problem i.
+static void member_reset(sdp_batch* b, int i) {
+  b->ms[i] = IpmStepState{};
+  b->mst[i] = SDP_OK;
+  b->mdone[i] = 0;
+  b->mpcg[i] = b->mit[i] = b->mits[i] = 0;
+  b->mrr[i] = 0.0;
+  b->mstart[i] = std::chrono::duration<double>(std::chrono::steady_clock::now() - b->epoch).count();
+  b->mfin[i] = -1.0;
+}
+static void members_resize(sdp_batch* b) {
+  const size_t N = b->hs.size();
+  b->ms.resize(N);
+  b->mst.resize(N, SDP_OK);
+  b->mdone.resize(N, 0);
+  b->mpcg.resize(N, 0);
+  b->mit.resize(N, 0);
+  b->mits.resize(N, 0);
+  b->mrr.resize(N, 0.0);
+  b->mstart.resize(N, 0.0);
+  b->mfin.resize(N, -1.0);
+}
+
+// One interior-point iteration of every running member, in lockstep: the dense
+// phases of each on its own stream and host thread, the two Newton systems of
+// all of them through the batched PCG.  A member leaves the running set when
+// its iterate meets the tolerances (state 1), its iteration limit is reached
+// (2) or a call fails (3); its finishing time is recorded then.
+static sdp_status lockstep_iter(sdp_batch* b) {
   const int N = (int)b->hs.size();
-  const auto t0 = std::chrono::steady_clock::now();
-  std::vector<IpmStepState> s(N);
-  std::vector<sdp_status> st(N, SDP_OK);
-  std::vector<char> done(N, 0);
-  std::vector<int> pcg_total(N, 0), its(N, 0);
-  std::vector<double> rr(N, 0.0);
-  std::vector<double> fin(N, -1.0);   // seconds from the start of the solve to each problem's end
-  auto since = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
-  int ipm_maxit = 0;
-  for (auto* h : b->hs) ipm_maxit = std::max(ipm_maxit, h->prm.ipm_maxit);
-  for (double& x : b->stage_s) x = 0.0;
+  auto now_s = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - b->epoch).count(); };
   auto tick = std::chrono::steady_clock::now();
   auto lap = [&](int stage) {
-    const auto now = std::chrono::steady_clock::now();
-    b->stage_s[stage] += std::chrono::duration<double>(now - tick).count();
-    tick = now;
+    const auto t = std::chrono::steady_clock::now();
+    b->stage_s[stage] += std::chrono::duration<double>(t - tick).count();
+    tick = t;
   };
-  for (int it = 0; it <= ipm_maxit; ++it) {
-    std::vector<int> act;
-    for (int i = 0; i < N; ++i)
-      if (!done[i] && st[i] == SDP_OK && it <= b->hs[i]->prm.ipm_maxit) act.push_back(i);
-    if (act.empty()) break;
-    std::vector<char> conv(N, 0);
-    parallel_for(act, [&](int i) {
-      bool d = false;
-      st[i] = ipm_phase_a(b->hs[i], &s[i], &d);
-      conv[i] = d;
-    });
-    lap(0);
-    std::vector<int> solve;
-    for (int i : act) {
-      if (st[i] != SDP_OK) {
-        if (fin[i] < 0.0) fin[i] = since();
-        continue;
+  auto fail_check = [&](const std::vector<int>& idx) {
+    std::vector<int> ok;
+    for (int i : idx) {
+      if (b->mst[i] == SDP_OK) {
+        ok.push_back(i);
+      } else if (!b->mdone[i]) {
+        b->mdone[i] = 3;
+        b->mfin[i] = now_s();
       }
-      if (conv[i]) done[i] = 1;
-      else if (it < b->hs[i]->prm.ipm_maxit) solve.push_back(i);
-      else done[i] = 2;   // iteration limit
-      if (done[i] && fin[i] < 0.0) fin[i] = since();
     }
-    if (solve.empty()) continue;
-    SDP_TRY(batch_newton(b, solve, its, rr, st));
-    lap(1);
-    std::vector<int> nxt;
-    for (int i : solve) if (st[i] == SDP_OK) nxt.push_back(i);
-    parallel_for(nxt, [&](int i) {
-      pcg_total[i] += its[i];
-      st[i] = ipm_phase_b(b->hs[i], &s[i], its[i], rr[i]);
-    });
-    lap(2);
-    std::vector<int> nxt2;
-    for (int i : nxt) if (st[i] == SDP_OK) nxt2.push_back(i);
-    SDP_TRY(batch_newton(b, nxt2, its, rr, st));
-    lap(3);
-    std::vector<int> nxt3;
-    for (int i : nxt2) if (st[i] == SDP_OK) nxt3.push_back(i);
-    parallel_for(nxt3, [&](int i) {
-      pcg_total[i] += its[i];
-      st[i] = ipm_phase_c(b->hs[i], &s[i], its[i], rr[i]);
-    });
-    lap(4);
+    return ok;
+  };
+  std::vector<int> act;
+  for (int i = 0; i < N; ++i)
+    if (!b->mdone[i]) act.push_back(i);
+  if (act.empty()) return SDP_OK;
+  std::vector<char> conv(N, 0);
+  parallel_for(act, [&](int i) {
+    bool d = false;
+    b->mst[i] = ipm_phase_a(b->hs[i], &b->ms[i], &d);
+    conv[i] = d;
+  });
+  lap(0);
+  std::vector<int> solve;
+  for (int i : fail_check(act)) {
+    if (conv[i]) b->mdone[i] = 1;
+    else if (b->mit[i] < b->hs[i]->prm.ipm_maxit) solve.push_back(i);
+    else b->mdone[i] = 2;   // iteration limit
+    if (b->mdone[i]) b->mfin[i] = now_s();
   }
-  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (solve.empty()) return SDP_OK;
+  SDP_TRY(batch_newton(b, solve, b->mits, b->mrr, b->mst));
+  lap(1);
+  std::vector<int> nxt = fail_check(solve);
+  parallel_for(nxt, [&](int i) {
+    b->mpcg[i] += b->mits[i];
+    b->mst[i] = ipm_phase_b(b->hs[i], &b->ms[i], b->mits[i], b->mrr[i]);
+  });
+  lap(2);
+  std::vector<int> nxt2 = fail_check(nxt);
+  SDP_TRY(batch_newton(b, nxt2, b->mits, b->mrr, b->mst));
+  lap(3);
+  std::vector<int> nxt3 = fail_check(nxt2);
+  parallel_for(nxt3, [&](int i) {
+    b->mpcg[i] += b->mits[i];
+    b->mst[i] = ipm_phase_c(b->hs[i], &b->ms[i], b->mits[i], b->mrr[i]);
+    if (b->mst[i] == SDP_OK) b->mit[i]++;
+  });
+  lap(4);
+  fail_check(nxt3);
+  return SDP_OK;
+}
+
+static sdp_result member_result(const sdp_batch* b, int i) {
+  sdp_result r{};
+  const IpmStepState& s = b->ms[i];
+  r.obj_p = s.inf.obj_p;
+  r.obj_d = s.inf.obj_d;
+  r.relgap = s.inf.relgap;
+  r.pinf = s.inf.pinf;
+  r.dinf = s.inf.dinf;
+  r.iters = b->hs[i]->iter;
+  r.pcg_iters_total = b->mpcg[i];
+  r.converged = (b->mdone[i] == 1) ? 1 : 0;
+  const double end = (b->mfin[i] >= 0.0) ? b->mfin[i]
+                                         : std::chrono::duration<double>(std::chrono::steady_clock::now() - b->epoch).count();
+  r.seconds = end - b->mstart[i];   // this member's own time in the batch
+  return r;
+}
+
+static sdp_status batch_solve_lockstep(sdp_batch* b, sdp_result* results) {
+  const int N = (int)b->hs.size();
+  members_resize(b);
+  for (int i = 0; i < N; ++i) member_reset(b, i);
+  for (double& x : b->stage_s) x = 0.0;
+  int ipm_maxit = 0;
+  for (auto* h : b->hs) ipm_maxit = std::max(ipm_maxit, h->prm.ipm_maxit);
+  for (int it = 0; it <= ipm_maxit + 1; ++it) {
+    bool any = false;
+    for (int i = 0; i < N; ++i) any = any || !b->mdone[i];
+    if (!any) break;
+    SDP_TRY(lockstep_iter(b));
+  }
   sdp_status worst = SDP_OK;
   for (int i = 0; i < N; ++i) {
-    sdp_result r{};
-    r.obj_p = s[i].inf.obj_p;
-    r.obj_d = s[i].inf.obj_d;
-    r.relgap = s[i].inf.relgap;
-    r.pinf = s[i].inf.pinf;
-    r.dinf = s[i].inf.dinf;
-    r.iters = b->hs[i]->iter;
-    r.pcg_iters_total = pcg_total[i];
-    r.converged = (done[i] == 1) ? 1 : 0;
-    r.seconds = (fin[i] >= 0.0) ? fin[i] : secs;   // this problem's own completion time
+    const sdp_result r = member_result(b, i);
     if (results) results[i] = r;
-    if (st[i] != SDP_OK && worst == SDP_OK) {
-      worst = st[i];
+    if (b->mst[i] != SDP_OK && worst == SDP_OK) {
+      worst = b->mst[i];
       b->last_error = "problem " + std::to_string(i) + ": " + b->hs[i]->last_error;
     }
-    if (st[i] == SDP_OK && !r.converged && worst == SDP_OK) worst = SDP_ERR_MAXIT;
+    if (b->mst[i] == SDP_OK && !r.converged && worst == SDP_OK) worst = SDP_ERR_MAXIT;
   }
   return worst;
+}
+
+static int member_index(const sdp_batch* b, const sdp_problem* h) {
+  for (size_t i = 0; i < b->hs.size(); ++i)
+    if (b->hs[i] == h) return (int)i;
+  return -1;
+}
+
+extern "C" sdp_status sdp_batch_tuning(const sdp_batch* b, int* spmm_rows, double* ms) {
+  if (!b) return SDP_ERR_ARG;
+  const sdp_batch* t = b->child.empty() ? b : b->child[0];
+  if (spmm_rows) *spmm_rows = t->tuned ? t->spmm_r : 0;
+  if (ms)
+    for (int c = 0; c < 4; ++c) ms[c] = t->tune_ms[c];
+  return SDP_OK;
+}
+
+extern "C" sdp_status sdp_batch_add(sdp_batch* b, sdp_problem* h) {
+  if (!b || !h || member_index(b, h) >= 0 || !b->child.empty()) return SDP_ERR_ARG;
+  std::string why;
+  if (!batch_supported(h, &why)) {
+    b->last_error = why;
+    return SDP_ERR_UNSUPPORTED;
+  }
+  b->hs.push_back(h);
+  members_resize(b);
+  member_reset(b, (int)b->hs.size() - 1);
+  b->dirty = true;
+  return SDP_OK;
+}
+
+extern "C" sdp_status sdp_batch_remove(sdp_batch* b, sdp_problem* h) {
+  if (!b) return SDP_ERR_ARG;
+  const int i = member_index(b, h);
+  if (i < 0) return SDP_ERR_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  auto erase = [i](auto& v) { v.erase(v.begin() + i); };
+  erase(b->hs);
+  erase(b->ms);
+  erase(b->mst);
+  erase(b->mdone);
+  erase(b->mpcg);
+  erase(b->mit);
+  erase(b->mits);
+  erase(b->mrr);
+  erase(b->mstart);
+  erase(b->mfin);
+  b->dirty = true;
+  return SDP_OK;
+}
+
+extern "C" sdp_status sdp_batch_step(sdp_batch* b, int* running) {
+  if (!b || !b->child.empty()) return SDP_ERR_ARG;
+  members_resize(b);
+  sdp_status s = b->hs.empty() ? SDP_OK : lockstep_iter(b);
+  int run = 0;
+  for (char d : b->mdone) run += (d == 0);
+  if (running) *running = run;
+  return s;
+}
+
+extern "C" sdp_status sdp_batch_member(const sdp_batch* b, const sdp_problem* h, sdp_result* r, int* state) {
+  if (!b) return SDP_ERR_ARG;
+  const int i = member_index(b, h);
+  if (i < 0 || i >= (int)b->mdone.size()) return SDP_ERR_ARG;
+  if (r) *r = member_result(b, i);
+  if (state) *state = b->mdone[i];
+  return (b->mdone[i] == 3) ? b->mst[i] : SDP_OK;
 }
 
 extern "C" const char* sdp_batch_last_error(const sdp_batch* b) { return b ? b->last_error.c_str() : ""; }

@@ -316,6 +316,176 @@ __global__ void __launch_bounds__(SY_THREADS) k_sytrd_cluster(int n, double* A, 
   }
 }
 
+// Shared-memory-resident cluster form for orders whose matrix fits in the
+// distributed shared memory of one cluster: row i lives in CTA i mod cs (slot
+// i / cs) for the whole reduction, so the matrix-vector product and the rank-2
+// update of every column read and write shared memory instead of streaming the
+// trailing matrix through L2.  Per column j: every CTA copies row j from the CTA
+// that owns it (a distributed-shared-memory read) and rebuilds the reflector;
+// p_i = tau A22[i, :] v for the owned rows, broadcast into every CTA's p;
+// cluster barrier; w = p - (tau / 2)(p^T v) v; owned rows updated; the owner of
+// row j stores the reflector in it; cluster barrier.  Row j is read by the other
+// CTAs before the first barrier and overwritten by its owner after it, and row
+// j + 1 is complete at the second barrier, before anyone reads it.  The rows
+// return to global memory at the end (the back-transformation reads them).
+__global__ void __launch_bounds__(SY_THREADS) k_sytrd_cluster_smem(int n, double* A, int lda, double* d, double* e,
+                                                                    double* tauh) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cs = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ double sm[];
+  const int slots = (n + cs - 1) / cs;
+  double* rows = sm;                         // slots x n, row-major
+  double* v = rows + (size_t)slots * n;      // n
+  double* w = v + n;                         // n
+  double* p = w + n;                         // n   (written by every CTA)
+  __shared__ double kpart[32];
+  __shared__ double red[32];
+  __shared__ double s_tau, s_beta, s_scale;
+  const int wpb = blockDim.x / 32, wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int sl = 0; sl < slots; ++sl) {
+    const int i = sl * cs + rank;
+    if (i >= n) break;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) rows[(size_t)sl * n + c] = __ldcg(A + (size_t)i * lda + c);
+  }
+  cluster.sync();
+  for (int j = 0; j < n - 2; ++j) {
+    const int len = n - j - 1;
+    const double* rowj = cluster.map_shared_rank(rows, j % cs) + (size_t)(j / cs) * n + j + 1;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      const double x = rowj[i];
+      v[i] = x;
+      if (i > 0) s = fma(x, x, s);
+    }
+    s = bsum(s, red);
+    if (threadIdx.x == 0) {
+      const double x0 = v[0];
+      double tau = 0.0, beta = x0, scale = 0.0;
+      if (s > 0.0) {
+        beta = -copysign(sqrt(fma(x0, x0, s)), x0);
+        tau = (beta - x0) / beta;
+        scale = 1.0 / (x0 - beta);
+      }
+      s_tau = tau; s_beta = beta; s_scale = scale;
+    }
+    __syncthreads();
+    const double tau = s_tau, scale = s_scale;
+    for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) v[i] *= scale;
+    if (threadIdx.x == 0) v[0] = 1.0;
+    __syncthreads();
+    // owned rows i = sl cs + rank > j
+    const int sl0 = (j + 1 > rank) ? (j + 1 - rank + cs - 1) / cs : 0;
+    double kp = 0.0;
+    for (int sl = sl0 + wid; sl < slots; sl += wpb) {
+      const int i = sl * cs + rank;
+      if (i >= n) break;
+      const double* ai = rows + (size_t)sl * n + j + 1;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int l = lane;
+      for (; l + 96 < len; l += 128) {
+        a0 = fma(ai[l], v[l], a0);
+        a1 = fma(ai[l + 32], v[l + 32], a1);
+        a2 = fma(ai[l + 64], v[l + 64], a2);
+        a3 = fma(ai[l + 96], v[l + 96], a3);
+      }
+      for (; l < len; l += 32) a0 = fma(ai[l], v[l], a0);
+      const double acc = wsum((a0 + a1) + (a2 + a3)) * tau;
+      if (lane < cs) {
+        double* dst = cluster.map_shared_rank(p, lane);
+        dst[i - j - 1] = acc;
+      }
+      if (lane == 0) kp = fma(acc, v[i - j - 1], kp);
+    }
+    kp = bsum(kp, red);
+    const double kp0 = __shfl_sync(0xffffffffu, kp, 0);
+    if (threadIdx.x < cs) {
+      double* dst = cluster.map_shared_rank(kpart, (int)threadIdx.x);
+      dst[rank] = kp0;
+    }
+    cluster.sync();
+    double K = 0.0;
+    for (int c = 0; c < cs; ++c) K += kpart[c];
+    K *= 0.5 * tau;
+    for (int l = threadIdx.x; l < len; l += blockDim.x) w[l] = p[l] - K * v[l];
+    __syncthreads();
+    for (int sl = sl0 + wid; sl < slots; sl += wpb) {
+      const int i = sl * cs + rank;
+      if (i >= n) break;
+      double* ai = rows + (size_t)sl * n + j + 1;
+      const double vi = v[i - j - 1], wi = w[i - j - 1];
+      for (int l = lane; l < len; l += 32) ai[l] = fma(-vi, w[l], fma(-wi, v[l], ai[l]));
+    }
+    if (rank == j % cs) {
+      double* rj = rows + (size_t)(j / cs) * n;
+      for (int l = threadIdx.x; l < len; l += blockDim.x) rj[j + 1 + l] = v[l];
+      if (threadIdx.x == 0) {
+        d[j] = rj[j];
+        e[j] = s_beta;
+        tauh[j] = tau;
+      }
+    }
+    cluster.sync();
+  }
+  if (threadIdx.x == 0) {
+    if (n >= 2 && rank == (n - 2) % cs) {
+      const double* r2 = rows + (size_t)((n - 2) / cs) * n;
+      d[n - 2] = r2[n - 2];
+      e[n - 2] = r2[n - 1];
+      tauh[n - 2] = 0.0;
+    }
+    if (rank == (n - 1) % cs) {
+      d[n - 1] = rows[(size_t)((n - 1) / cs) * n + n - 1];
+      e[n - 1] = 0.0;
+      if (n >= 2) tauh[n - 1] = 0.0;
+    }
+  }
+  for (int sl = 0; sl < slots; ++sl) {
+    const int i = sl * cs + rank;
+    if (i >= n) break;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) A[(size_t)i * lda + c] = rows[(size_t)sl * n + c];
+  }
+}
+
+// Cluster size of the shared-memory form for order n: 16 when the matrix and the
+// work vectors fit in 16 CTAs' shared memory and the device runs such a
+// cluster; 0 otherwise.
+static size_t sytrd_smem_bytes(int n, int cs) {
+  return ((size_t)((n + cs - 1) / cs) * n + 3 * (size_t)n) * sizeof(double);
+}
+static int sytrd_smem_cluster(int n) {
+  static int max_optin = -1;
+  static int ok16 = -1;
+  if (max_optin < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  const int cs = 16;
+  const size_t need = sytrd_smem_bytes(n, cs);
+  if (need + 2048 > (size_t)max_optin) return 0;
+  if (ok16 < 0) {
+    allow_max_smem((const void*)k_sytrd_cluster_smem);
+    cudaFuncSetAttribute((const void*)k_sytrd_cluster_smem, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(SY_THREADS);
+    cfg.dynamicSmemBytes = (size_t)max_optin - 2048;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    ok16 = (cudaOccupancyMaxActiveClusters(&ncl, (const void*)k_sytrd_cluster_smem, &cfg) == cudaSuccess && ncl > 0)
+               ? 1 : 0;
+    cudaGetLastError();
+  }
+  return ok16 ? cs : 0;
+}
+
 // Cluster size for k_sytrd_cluster: 16 where the device allows it, else 8
 // (0 = cluster launch unavailable).
 static int sytrd_cluster_size(size_t smem) {
@@ -368,6 +538,30 @@ static int sytrd_blocks(int n, size_t smem) {
 constexpr int SY_CLUSTER_MAX_N = 1024;
 
 static sdp_status sytrd(cudaStream_t st, int n, double* A, EigWork* w) {
+  if (n >= 3 && n <= SY_CLUSTER_MAX_N) {
+    const int cs = sytrd_smem_cluster(n);
+    if (cs > 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(SY_THREADS);
+      cfg.dynamicSmemBytes = sytrd_smem_bytes(n, cs);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int lda = n;
+      count_launch();
+      ktimer_begin(st, "sytrd");
+      cudaError_t err = cudaLaunchKernelEx(&cfg, k_sytrd_cluster_smem, n, A, lda, w->d, w->e, w->tauh);
+      ktimer_end(st, "sytrd", 4.0 / 3.0 * n * (double)n * n, 16.0 * n * (double)n);
+      if (err == cudaSuccess) return SDP_OK;
+      cudaGetLastError();
+    }
+  }
   if (n <= SY_CLUSTER_MAX_N) {
     const size_t csm = 3 * (size_t)n * sizeof(double);
     const int cs = sytrd_cluster_size(200 * 1024);

@@ -280,6 +280,12 @@ sdp_status schur_build(sdp_problem* h, int k, double tau);
 sdp_status schur_apply(sdp_problem* h, const double* u, double* out, double scale, int prec = SDP_FP64);
 // FP32 copy of the Hhat core's dense factor inverse for applies in reduced precision
 sdp_status ensure_lowprec_core(sdp_problem* h);
+// tc_gemm.cu: C (FP64) = op(A) op(B) on the tensor cores with the operands
+// rounded to BF16 (prec SDP_BF16) or TF32 (SDP_FP32), FP32 accumulation
+bool tc_available();
+size_t tc_work_bytes(int M, int N, int K);
+sdp_status tc_gemm(cudaStream_t st, int prec, int M, int N, int K, const double* A, int lda, bool transA,
+                   const double* B, int ldb, bool transB, double* C, int ldc, void* work, int* err_dev);
 bool lanczos_fits(int n);
 sdp_status lanczos_min(cudaStream_t st, int n, const double* M, const double* A2, const double* A3, int ldm,
                        double rtol, double accept_above, double* work, double* out_dev);
@@ -378,6 +384,7 @@ struct sdp_problem {
   double* au = nullptr;    // ncr*k   (A_i u_l) restricted to support rows
   double* Kval = nullptr;  // nnzK
   double* KZ = nullptr;    // n*n
+  void* tc_work = nullptr; // packed tensor-core operands of the mixed core formation
   double* pvec = nullptr;  // scratch vectors for the apply
   double* Bn = nullptr;    // n*k
   double* uvec = nullptr;  // nk
@@ -475,7 +482,9 @@ sdp_status pcg_impl(sdp_problem* h, const double* r, double* y, double rtol, int
 sdp_status ipm_alloc(sdp_problem* h);
 // Batched PCG pieces (one launch for all problems of a batch; block offsets per problem)
 int batch_blocks_assemble(int nnzV);
-int batch_blocks_spmm(int n);
+int batch_blocks_spmm(int n, int R);
+void batch_launch_spmm(cudaStream_t st, int R, const BDesc* desc, const int* off, int N, int nb, int nmax);
+bool batch_spmm_fits(int R, int nmax);
 int batch_blocks_sddmm(int m);
 int batch_blocks_vec(int m);
 int batch_blocks_hat_u(int n);
@@ -491,7 +500,7 @@ void batch_launch_matvec_lp(cudaStream_t st, const BDesc* desc, const int* off_g
                             const int* off_q, const int* off_spmm, const int* off_sddmm, int N, int nb_g, int nb_r,
                             int nb_q, int nb_spmm, int nb_sddmm, int nmax);
 void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm, const int* off_spmm,
-                         const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax);
+                         const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax, int spmm_r);
 void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb);
 void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
 // flag != nullptr (host-driven loop): flag[0] = some problem active, flag[1 + i] = problem i

@@ -246,7 +246,6 @@ __global__ void __launch_bounds__(256) k_sddmm_f64(int n, int m, const int* __re
 // ---------------------------------------------------------------------------
 // Batched forms (one launch for every problem of a batch; see batch.cu)
 // ---------------------------------------------------------------------------
-constexpr int BATCH_SPMM_R = 4;
 __global__ void kb_assemble(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
@@ -254,13 +253,30 @@ __global__ void kb_assemble(const BDesc* __restrict__ desc, const int* __restric
   const int lb = blockIdx.x - off[i];
   assemble_body(lb * blockDim.x + threadIdx.x, D.nnzV, D.sptr, D.scon, D.scoef, D.pp, nullptr, D.Vval);
 }
+// R rows of W per CTA: chosen per batch by the autotuner (batch.cu); every R
+// gives each entry of T by the same sequence of FMAs, so results do not depend on it
+template <int R>
 __global__ void __launch_bounds__(256) kb_spmm(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
   extern __shared__ double wsh[];
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
   if (!D.active || D.lp) return;
-  spmm_f64_body<BATCH_SPMM_R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W, D.T, wsh);
+  spmm_f64_body<R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W, D.T, wsh);
 }
+static void launch_kb_spmm(cudaStream_t st, int R, const BDesc* desc, const int* off, int N, int nb, int nmax) {
+  const size_t smem = (size_t)R * nmax * sizeof(double);
+  switch (R) {
+    case 1: allow_max_smem((const void*)kb_spmm<1>); kb_spmm<1><<<nb, 256, smem, st>>>(desc, off, N); break;
+    case 2: allow_max_smem((const void*)kb_spmm<2>); kb_spmm<2><<<nb, 256, smem, st>>>(desc, off, N); break;
+    case 8: allow_max_smem((const void*)kb_spmm<8>); kb_spmm<8><<<nb, 256, smem, st>>>(desc, off, N); break;
+    default: allow_max_smem((const void*)kb_spmm<4>); kb_spmm<4><<<nb, 256, smem, st>>>(desc, off, N); break;
+  }
+}
+void batch_launch_spmm(cudaStream_t st, int R, const BDesc* desc, const int* off, int N, int nb, int nmax) {
+  count_launch();
+  if (nb > 0) launch_kb_spmm(st, R, desc, off, N, nb, nmax);
+}
+bool batch_spmm_fits(int R, int nmax) { return (size_t)R * nmax * sizeof(double) <= 200 * 1024; }
 __global__ void __launch_bounds__(256) kb_sddmm(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
@@ -269,15 +285,13 @@ __global__ void __launch_bounds__(256) kb_sddmm(const BDesc* __restrict__ desc, 
                  D.pp, D.part, D.ticket, D.scal + S_PQ, D.scal + S_RZ, D.scal + S_RZN);
 }
 int batch_blocks_assemble(int nnzV) { return (int)cdiv(nnzV, 256); }
-int batch_blocks_spmm(int n) { return (int)cdiv(n, BATCH_SPMM_R); }
+int batch_blocks_spmm(int n, int R) { return (int)cdiv(n, R); }
 int batch_blocks_sddmm(int m) { return (int)cdiv(m, SDDMM_PER_BLOCK); }
 void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm, const int* off_spmm,
-                         const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax) {
-  const size_t smem = (size_t)BATCH_SPMM_R * nmax * sizeof(double);
-  allow_max_smem((const void*)kb_spmm);
+                         const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax, int spmm_r) {
   count_launch(3);
   if (nb_asm > 0) kb_assemble<<<nb_asm, 256, 0, st>>>(desc, off_asm, N);
-  if (nb_spmm > 0) kb_spmm<<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N);
+  if (nb_spmm > 0) launch_kb_spmm(st, spmm_r, desc, off_spmm, N, nb_spmm, nmax);
   if (nb_sddmm > 0) kb_sddmm<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
 }
 

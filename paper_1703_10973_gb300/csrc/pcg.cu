@@ -176,7 +176,10 @@ static sdp_status pcg_body(sdp_problem* h, int prec, cudaGraphConditionalHandle 
   count_launch();
   k_pcg_xr_check<<<g, 256, 0, st>>>(m, h->px, h->pr, h->pp, h->pq, scal, h->pcg_part, h->pcg_ticket, cond,
                                     use_cond ? 1 : 0);
-  SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec, scal + S_RZN));
+  // the core solve stays in FP64 inside PCG: near the optimum the Hhat core has
+  // kappa ~ 1 / mu, and its FP32 inverse (what sdp_precond_apply uses for
+  // prec != FP64) cost about twice the PCG iterations in measurements
+  SDP_TRY(precond_apply_impl(h, h->pr, h->pz, SDP_FP64, scal + S_RZN));
   count_launch();
   k_pcg_p<<<g, 256, 0, st>>>(m, h->pp, h->pz, scal);
   return SDP_OK;
@@ -197,7 +200,6 @@ static sdp_status pcg_graph(sdp_problem* h, int prec) {
     h->pcg_graph = nullptr;
   }
   SDP_TRY(ensure_lowprec_W(h, prec));
-  if (prec != SDP_FP64) SDP_TRY(ensure_lowprec_core(h));
   cudaGraph_t g = nullptr;
   SDP_CK(h, cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle cond;
@@ -249,12 +251,8 @@ static sdp_status pcg_start(sdp_problem* h, const double* rhs, double rtol, int 
   cudaStream_t st = h->stream;
   const int m = h->m;
   double* scal = h->scal;
-  if (graph) {
-    SDP_TRY(pcg_graph(h, prec));
-  } else {
-    SDP_TRY(ensure_lowprec_W(h, prec));
-    if (prec != SDP_FP64) SDP_TRY(ensure_lowprec_core(h));
-  }
+  if (graph) SDP_TRY(pcg_graph(h, prec));
+  else SDP_TRY(ensure_lowprec_W(h, prec));
   SDP_CK(h, cudaMemcpyAsync(h->pr, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   SDP_CK(h, cudaMemsetAsync(h->px, 0, m * sizeof(double), st));
   dot(st, m, h->pr, h->pr, scal + S_NR0, h->part);
@@ -264,7 +262,7 @@ static sdp_status pcg_start(sdp_problem* h, const double* rhs, double rtol, int 
     return SDP_ERR_NUMERIC;
   }
   if (*nr0sq == 0.0) return SDP_OK;
-  SDP_TRY(precond_apply_impl(h, h->pr, h->pz, prec, scal + S_RZ));
+  SDP_TRY(precond_apply_impl(h, h->pr, h->pz, SDP_FP64, scal + S_RZ));
   SDP_CK(h, cudaMemcpyAsync(h->pp, h->pz, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   count_launch();
   k_pcg_init<<<1, 1, 0, st>>>(scal, rtol, maxit);
@@ -360,7 +358,11 @@ sdp_status pcg_sweep_begin(sdp_problem* h, PcgSweeps* S, bool graph, bool* run) 
     S->finished = true;
     return SDP_OK;
   }
-  S->budget = std::max(1, std::min(S->maxit - S->total, 500));
+  // iterations of one sweep: a restart discards the Krylov space, so a sweep must
+  // be long enough to resolve the k(k+1)/2 outlying eigenvalues that H - Hhat
+  // (rank <= k(k+1)/2, Section V) leaves, on top of the bulk
+  const int kk = h->pc_hat ? h->kpc : 0;
+  S->budget = std::max(1, std::min(S->maxit - S->total, std::max(500, kk * (kk + 1) / 2 + 500)));
   S->graph = graph;
   SDP_TRY(pcg_start(h, h->pbest, S->prec == SDP_FP64 ? S->inner_fp64 : S->inner_lp, S->budget, S->prec, graph,
                     &S->nr0sq));

@@ -467,9 +467,20 @@ static sdp_status read_info(sdp_problem* h, const char* what) {
 }
 
 // Sc = Z^T K_ll' Z block by block, plus shift on the diagonal.
-static void form_core(sdp_problem* h, int k, double shift) {
+// With a reduced-precision handle (params.prec = SDP_FP32 or SDP_BF16) the dense
+// Z^T (K Z) products run on the tensor cores (tc_gemm) with TF32 operands and
+// FP32 accumulation; the core is still factored in FP64.  BF16 operands (8-bit
+// significands) are not used here: the core has kappa >= 1e2 already at mu ~ 0.1,
+// and a BF16-formed core left PCG without convergence in the tests.
+static sdp_status form_core(sdp_problem* h, int k, double shift) {
   cudaStream_t st = h->stream;
   const int n = h->n, nk = n * k;
+  const bool mixed = (h->prm.prec == SDP_FP32 || h->prm.prec == SDP_BF16) && tc_available();
+  int* tc_err = h->info + 4;
+  if (mixed) {
+    if (!h->tc_work) SDP_TRY(h->alloc(&h->tc_work, tc_work_bytes(n, n, n)));
+    SDP_CK(h, cudaMemsetAsync(tc_err, 0, sizeof(int), st));
+  }
   for (int l = 0; l < k; ++l) {
     for (int l2 = l; l2 < k; ++l2) {
       count_launch(2);
@@ -478,11 +489,22 @@ static void form_core(sdp_problem* h, int k, double shift) {
       const unsigned gx = std::max(1u, std::min(cdiv(n, 128), 64u));
       k_csr_mm<<<dim3(gx, n), 128, 0, st>>>(n, h->krowptr, h->kcol, h->Kval, h->Z, n, n, h->KZ, n);
       double* blk = h->Sc + (size_t)l * n * nk + (size_t)l2 * n;
-      gemm(st, true, false, n, n, n, 1.0, h->Z, n, h->KZ, n, 0.0, blk, nk);
+      if (mixed) SDP_TRY(tc_gemm(st, SDP_FP32, n, n, n, h->Z, n, true, h->KZ, n, false, blk, nk, h->tc_work, tc_err));
+      else gemm(st, true, false, n, n, n, 1.0, h->Z, n, h->KZ, n, 0.0, blk, nk);
       if (l2 != l) transpose(st, n, n, blk, nk, h->Sc + (size_t)l2 * n * nk + (size_t)l * n, nk);
     }
   }
   if (shift != 0.0) add_diag(st, nk, h->Sc, nk, shift);
+  if (mixed) {
+    int e = 0;
+    SDP_CK(h, cudaMemcpyAsync(&e, tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SDP_CK(h, cudaStreamSynchronize(st));
+    if (e) {
+      h->last_error = "precond_build: a bounded wait of the tensor-core core formation ran out";
+      return SDP_ERR_TIMEOUT;
+    }
+  }
+  return SDP_OK;
 }
 
 sdp_status precond_build_impl(sdp_problem* h) {
@@ -579,7 +601,7 @@ sdp_status precond_build_impl(sdp_problem* h) {
   if (hat) {
     SDP_TRY(schur_build(h, k, tau));
   } else {
-    form_core(h, k, tau * tau);
+    SDP_TRY(form_core(h, k, tau * tau));
     potrf_floor(st, nk, h->Sc, nk, h->info, h->work, tau * tau);
     int inf2[2] = {0, 0};
     SDP_CK(h, cudaMemcpyAsync(inf2, h->info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));

