@@ -568,9 +568,14 @@ def run_e2e(args, insts, head):
     outs = [(np.empty((d.n, d.n)), np.empty(d.m)) for d in insts]
     torch.cuda.synchronize()
     te = time.perf_counter()
+    from concurrent.futures import ThreadPoolExecutor
+
+    def setup(i):   # host-side set-up of each problem in its own thread (the C call releases the GIL)
+        return SDPProblem.from_data(insts[i], params=head.params, stream=head.streams[i % len(head.streams)].cuda_stream)
+
+    pool = ThreadPoolExecutor(max_workers=min(16, len(insts)))
     for _ in range(args.e2e_steps):
-        ps = [SDPProblem.from_data(insts[i], params=head.params, stream=head.streams[i % len(head.streams)].cuda_stream)
-              for i in range(len(insts))]
+        ps = list(pool.map(setup, range(len(insts))))
         if args.batched_launch:
             with SDPBatch(ps, stream=head.bstream.cuda_stream, groups=args.batch_groups) as b2:
                 b2.solve(allow_maxit=True)
@@ -591,13 +596,16 @@ def run_e2e(args, insts, head):
                 t.join()
             if errs:
                 raise errs[0]
-        for i, p2 in enumerate(ps):
+        def fetch(i):
             X, y = outs[i]
-            st = p2.lib.sdp_get_solution(p2.h, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data), None)
+            st = ps[i].lib.sdp_get_solution(ps[i].h, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data), None)
             assert st == 0
-            p2.close()
+            ps[i].close()
+
+        list(pool.map(fetch, range(len(ps))))
     torch.cuda.synchronize()
     el = time.perf_counter() - te
+    pool.shutdown()
     return {"value": args.e2e_steps * len(insts) / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h)}
 
@@ -740,13 +748,89 @@ def run_fig1(args):
     return 0
 
 
+def run_probe(args):
+    """Small fixed cases for profilers (one JSON line each, timed with CUDA events):
+    --probe tc     sdp_mixed_gemm on N x N x N random operands (--probe-n), BF16 then TF32;
+    --probe batch  the 16 bench instances joined to an empty batch (sdp_batch_add),
+                   --ipm-steps lockstep IPM iterations (sdp_batch_step), host-driven PCG;
+    --probe ipm    --ipm-steps IPM iterations of the largest bench instance (B0) alone."""
+    import ctypes as C
+    import torch
+    import sdp_inputs as si
+    from paper_1703_10973_gb300 import SDPBatch, SDPProblem, _build, default_params, load
+    from paper_1703_10973_gb300 import _lib as L
+    _, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    lib = load()
+    out = {"probe": args.probe}
+    if args.probe == "tc":
+        N = args.probe_n
+        for prec in ("bf16", "fp32"):
+            A = torch.randn(N, N, dtype=torch.float64, device="cuda")
+            B = torch.randn(N, N, dtype=torch.float64, device="cuda")
+            Cm = torch.empty(N, N, dtype=torch.float64, device="cuda")
+            wb = int(lib.sdp_mixed_gemm_work_bytes(N, N, N))
+            work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+            err = torch.zeros(1, dtype=torch.int32, device="cuda")
+            call = (L.PREC[prec], N, N, N, C.c_void_p(A.data_ptr()), N, 0, C.c_void_p(B.data_ptr()), N, 0,
+                    C.c_void_p(Cm.data_ptr()), N, C.c_void_p(work.data_ptr()), wb, C.c_void_p(err.data_ptr()),
+                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
+            for _ in range(2):
+                assert lib.sdp_mixed_gemm(*call) == L.SDP_OK
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                lib.sdp_mixed_gemm(*call)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 5
+            ref = A @ B
+            out[prec] = {"ms_per_call": ms, "tflops_incl_packing": 2 * N ** 3 / (ms * 1e-3) / 1e12,
+                         "max_rel_err": float((Cm - ref).abs().max() / ref.abs().max()), "flag": int(err.item())}
+    elif args.probe == "batch":
+        insts, desc = workload("batched", args.batch)
+        prm = default_params(pcg_graph=args.pcg_graph, prec=args.arms.split(",")[0])
+        streams = [torch.cuda.Stream() for _ in insts]
+        probs = [SDPProblem.from_data(d, params=prm, stream=s.cuda_stream) for d, s in zip(insts, streams)]
+        b = SDPBatch([])
+        for p in probs:
+            b.add(p)
+        t0 = time.perf_counter()
+        for _ in range(args.ipm_steps):
+            b.step()
+        torch.cuda.synchronize()
+        out.update(workload=desc, seconds=time.perf_counter() - t0, tuning=b.tuning()[0])
+        b.close()
+        for p in probs:
+            p.close()
+    else:
+        s0 = si.batched_specs(256)[0]
+        d = si.mc_instance(s0["p"], s0["q"], s0["r"], s0["m"], s0["seed"])
+        with SDPProblem.from_data(d, params=default_params(pcg_graph=args.pcg_graph)) as p:
+            t0 = time.perf_counter()
+            for _ in range(args.ipm_steps):
+                p.ipm_step()
+            torch.cuda.synchronize()
+            out.update(workload=f"B0 (n={d.n}, m={d.m})", seconds=time.perf_counter() - t0)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "C2", "C3", "fig2", "fig1", "serving"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "C2", "C3", "fig2", "fig1", "serving",
+                                                              "probe"])
+    ap.add_argument("--probe", default="tc", choices=["tc", "batch", "ipm"],
+                    help="probe workload: a small fixed case for profilers")
+    ap.add_argument("--probe-n", type=int, default=2048, help="probe tc: GEMM order")
+    ap.add_argument("--ipm-steps", type=int, default=2, help="probe batch / ipm: interior-point iterations")
     ap.add_argument("--fig1-max-n", type=int, default=5024, help="fig1: largest SDP order of the sweep")
     ap.add_argument("--fig1-iters", type=int, default=3, help="fig1: timed interior-point iterations per shape")
     ap.add_argument("--arms", default="fp32,fp64",
@@ -781,6 +865,8 @@ def main():
         return run_serving(args)
     if args.workload == "fig1":
         return run_fig1(args)
+    if args.workload == "probe":
+        return run_probe(args)
     return run(args)
 
 

@@ -305,8 +305,8 @@ sdp_status sdp_batch_stage_seconds(const sdp_batch* b, double* out);
 /* Autotuner of the batched PCG matvec: the first batched Newton solve times the
  * SpMM tile (rows of W per CTA, R = 1, 2, 4, 8 within shared memory) on the
  * batch's own data and keeps the fastest (every R gives the same results).
- * *spmm_rows = the chosen R (0 before the first solve); ms[0..3] = mean
- * milliseconds per launch of each candidate (0 = not run).  With lockstep
+ * *spmm_rows = the chosen R (0 before the first solve); ms[0..3] = least
+ * milliseconds per launch of each candidate over five rounds (0 = not run).  With lockstep
  * groups, the first group's choice.  Either pointer may be NULL. */
 sdp_status sdp_batch_tuning(const sdp_batch* b, int* spmm_rows, double* ms);
 

@@ -16,6 +16,8 @@ Programs" (arXiv 1703.10973), in the paper's notation:
 * eq. (AtIUUtAt)/(SMW2): preconditioner Ht = tau^2 A^T A + UU UU^T and its inverse.
 * eq. (Umv): UU x = [A_i . (Z X U^T)]_i,  UU^T y = Z^T (sum y_i A_i) U.
 * Algorithm 1: formation, factorisation, PCG solution.
+* eq. (sparse_prec), Lemma aug_prec, eq. (aug_prec): the Section V preconditioner Hhat
+  and its augmented system, solved by LDL^T without pivoting.
 * Section II / II-B: NT scaling (X = W S W) and the direct method (form H, Cholesky).
 
 Readings where the paper is silent or inconsistent (each listed in the design notes):
@@ -360,6 +362,53 @@ def precond_hat_dense(P: Problem, W, k):
     A = P.A_matrix()
     mid = sp.tau ** 2 * np.eye(n * n) + 2.0 * sp.tau * np.kron(sp.U @ sp.U.T, np.eye(n))
     return A.T @ mid @ A
+
+
+def aug_prec_matrix(P: Problem, W, k):
+    """The sparse augmented system of eq. (aug_prec) for Hhat (Section V):
+        [[tau^2 A^T A,                 tau^{3/2} A^T (U kron I)],
+         [tau^{3/2} (U kron I)^T A,   -tau^2 / 2 I_{nk}        ]],
+    with A the n^2 x m matrix [vec A_1, ..., vec A_m] and (U kron I) the n^2 x nk
+    matrix (row-major vec, columns (l, c) -> l n + c).  Eliminating its second block
+    row leaves A^T (tau^2 I + 2 tau (U U^T kron I)) A = Hhat."""
+    sp = split_W(W, k, "eig")
+    n = W.shape[0]
+    A = P.A_matrix()
+    UI = np.kron(sp.U, np.eye(n))
+    t = sp.tau
+    top = np.hstack([t ** 2 * (A.T @ A), t ** 1.5 * (A.T @ UI)])
+    bot = np.hstack([t ** 1.5 * (UI.T @ A), -0.5 * t ** 2 * np.eye(n * k)])
+    return np.vstack([top, bot])
+
+
+def ldl_nopivot_solve(K, b):
+    """Solve K x = b by a plain LDL^T factorisation without pivoting (the recipe of
+    Section V for eq. (aug_prec)): K = L D L^T with unit lower L and diagonal D,
+    computed column by column; then forward, diagonal and backward substitution."""
+    K = np.array(K, dtype=float)
+    N = K.shape[0]
+    L = np.eye(N)
+    D = np.zeros(N)
+    for j in range(N):
+        D[j] = K[j, j] - np.dot(L[j, :j] ** 2, D[:j])
+        for i in range(j + 1, N):
+            L[i, j] = (K[i, j] - np.dot(L[i, :j] * L[j, :j], D[:j])) / D[j]
+    y = np.zeros(N)
+    for i in range(N):
+        y[i] = b[i] - np.dot(L[i, :i], y[:i])
+    z = y / D
+    x = np.zeros(N)
+    for i in range(N - 1, -1, -1):
+        x[i] = z[i] - np.dot(L[i + 1:, i], x[i + 1:])
+    return x
+
+
+def aug_prec_solve(P: Problem, W, k, b):
+    """Hhat^{-1} b through eq. (aug_prec): the first m entries of the solution of the
+    augmented system with right-hand side [b; 0], by LDL^T without pivoting."""
+    K = aug_prec_matrix(P, W, k)
+    rhs = np.concatenate([np.asarray(b, dtype=float), np.zeros(K.shape[0] - P.m)])
+    return ldl_nopivot_solve(K, rhs)[: P.m]
 
 
 def precond_apply(P: Problem, pc: Precond, r):

@@ -99,8 +99,8 @@ static void batch_offsets(sdp_batch* b) {
     const int cnt[BK_COUNT] = {batch_blocks_assemble(h->nnzV), batch_blocks_spmm(h->n, b->spmm_r), batch_blocks_sddmm(h->m),
                                batch_blocks_vec(h->m),         batch_blocks_hat_u(h->n), batch_blocks_tail(h->m),
                                batch_blocks_fwdP(h->hs_np),    batch_blocks_warp_rows(h->hs_nr),
-                               batch_blocks_warp_rows(Rk),     batch_blocks_outR(Rk),
-                               batch_blocks_warp_rows(h->hs_np),
+                               batch_blocks_warp_rows(Rk),     batch_blocks_out_bwd(Rk, h->hs_np),
+                               0,
                                batch_blocks_split_G(h->n),     batch_blocks_split_R(h->n),
                                batch_blocks_split_Q(h->n, k),  batch_blocks_spmm_lp(h->n)};
     for (int kd = 0; kd < BK_COUNT; ++kd)
@@ -118,7 +118,7 @@ static BDesc make_desc(sdp_problem* h, int active, int prec) {
   D.active = active;
   D.zscale = h->zscale;
   D.inv_tau2 = 1.0 / (h->tau * h->tau);
-  D.rowptr = h->rowptr; D.colidx = h->colidx; D.sptr = h->sptr; D.scon = h->scon;
+  D.rowptr = h->rowptr; D.rowperm = h->rowperm; D.colidx = h->colidx; D.sptr = h->sptr; D.scon = h->scon;
   D.eptr = h->eptr; D.ep = h->ep; D.eq = h->eq;
   D.scoef = h->scoef; D.ecoef = h->ecoef; D.ginv = h->ginv;
   D.W = h->W; D.U = h->U; D.T = h->T; D.Vval = h->Vval;
@@ -171,14 +171,19 @@ static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle
     }
     ktimer_begin(st, "matvec_b");
   }
+  // A mixed batch in the graph gathers both forms in one launch after the
+  // reduced-precision pieces; the instrumented host loop keeps them apart so that
+  // each class is timed on its own.  Same partitions either way, same results.
+  const bool merge = b->any_lp && !mode;
   batch_launch_matvec(st, b->ddesc, off(BK_ASM), off(BK_SPMM), off(BK_SDDMM), N, b->total[BK_ASM],
-                      b->total[BK_SPMM], b->total[BK_SDDMM], b->nmax, b->spmm_r);
+                      b->total[BK_SPMM], merge ? 0 : b->total[BK_SDDMM], b->nmax, b->spmm_r);
   if (mode) ktimer_end(st, "matvec_b", fl, by);
   if (b->any_lp) {  // same SDDMM partition (and reduction groups) as the FP64 form
     if (mode) ktimer_begin(st, "matvec_lp_b");
     batch_launch_matvec_lp(st, b->ddesc, off(BK_SPLG), off(BK_SPLR), off(BK_SPLQ), off(BK_SPMM_LP), off(BK_SDDMM),
                            N, b->total[BK_SPLG], b->total[BK_SPLR], b->total[BK_SPLQ], b->total[BK_SPMM_LP],
-                           b->total[BK_SDDMM], b->nmax);
+                           b->total[BK_SDDMM], b->nmax, !merge);
+    if (merge) batch_launch_sddmm_mixed(st, b->ddesc, off(BK_SDDMM), N, b->total[BK_SDDMM]);
     if (mode) ktimer_end(st, "matvec_lp_b", fl_lp, by_lp);
   }
   batch_launch_xr(st, b->ddesc, off(BK_VEC), N, b->total[BK_VEC]);
@@ -187,8 +192,7 @@ static void batch_body(sdp_batch* b, cudaStream_t st, cudaGraphConditionalHandle
                           off(BK_GEMV), b->total[BK_GEMV], off(BK_OUTR), b->total[BK_OUTR], off(BK_BWDP),
                           b->total[BK_BWDP]);
   batch_launch_tail(st, b->ddesc, off(BK_TAIL), N, b->total[BK_TAIL]);
-  batch_launch_p(st, b->ddesc, off(BK_VEC), N, b->total[BK_VEC]);
-  batch_launch_any(st, b->ddesc, N, cond, flag);
+  batch_launch_p(st, b->ddesc, off(BK_VEC), N, b->total[BK_VEC], cond, flag);
 }
 
 // Block offsets, device tables and the captured loop for the current members;
@@ -270,8 +274,9 @@ static sdp_status batch_prepare(sdp_batch* b) {
 
 // Autotuner of the batched SpMM tile: each candidate R (rows of W per CTA: 1, 2,
 // 4, 8, within shared memory) runs on the batch's own data with the descriptors
-// just uploaded, timed with CUDA events (one warm-up, three timed launches);
-// the fastest is kept and the launch structures are rebuilt for it.  T is
+// just uploaded, timed with CUDA events (five interleaved rounds of one warm-up
+// and one timed launch, minimum kept); the fastest is kept and the launch
+// structures are rebuilt for it.  T is
 // scratch of the matvec, recomputed by every real launch, so the trial launches
 // change nothing; every R computes each entry of T by the same FMA sequence.
 static sdp_status batch_autotune(sdp_batch* b, const std::vector<BDesc>& hd) {
@@ -291,25 +296,33 @@ static sdp_status batch_autotune(sdp_batch* b, const std::vector<BDesc>& hd) {
     cudaGetLastError();
     return SDP_ERR_OOM;
   }
+  // candidates interleaved over five rounds, the minimum per candidate kept: other
+  // lockstep groups run their dense phases on the GPU meanwhile, and the minimum
+  // is the least disturbed of the samples
   float best = 0.f;
   int best_r = b->spmm_r;
+  for (int c = 0; c < 4; ++c) b->tune_ms[c] = 0.f;
+  for (int round = 0; round < 5; ++round) {
+    for (int c = 0; c < 4; ++c) {
+      const int R = cand[c];
+      if (!batch_spmm_fits(R, b->nmax)) continue;
+      for (int i = 0; i < N; ++i) off[i + 1] = off[i] + batch_blocks_spmm(b->hs[i]->n, R);
+      cudaMemcpyAsync(doff, off.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, b->stream);
+      batch_launch_spmm(b->stream, R, b->ddesc, doff, N, off[N], b->nmax);   // warm-up
+      cudaEventRecord(e0, b->stream);
+      batch_launch_spmm(b->stream, R, b->ddesc, doff, N, off[N], b->nmax);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (b->tune_ms[c] == 0.f || ms < b->tune_ms[c]) b->tune_ms[c] = ms;
+    }
+  }
   for (int c = 0; c < 4; ++c) {
-    const int R = cand[c];
-    b->tune_ms[c] = 0.f;
-    if (!batch_spmm_fits(R, b->nmax)) continue;
-    for (int i = 0; i < N; ++i) off[i + 1] = off[i] + batch_blocks_spmm(b->hs[i]->n, R);
-    cudaMemcpyAsync(doff, off.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, b->stream);
-    batch_launch_spmm(b->stream, R, b->ddesc, doff, N, off[N], b->nmax);
-    cudaEventRecord(e0, b->stream);
-    for (int t = 0; t < 3; ++t) batch_launch_spmm(b->stream, R, b->ddesc, doff, N, off[N], b->nmax);
-    cudaEventRecord(e1, b->stream);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    b->tune_ms[c] = ms / 3.f;
+    if (b->tune_ms[c] == 0.f) continue;
     if (best == 0.f || b->tune_ms[c] < best) {
       best = b->tune_ms[c];
-      best_r = R;
+      best_r = cand[c];
     }
   }
   cudaMemcpyAsync(b->ddesc, hd.data(), sizeof(BDesc) * N, cudaMemcpyHostToDevice, b->stream);

@@ -71,7 +71,7 @@ struct BDesc {
   int n, m, k, np, nr, Rk, nnzV;
   int active;                       // the problem's PCG loop is still running
   double zscale, inv_tau2;
-  const int *rowptr, *colidx, *sptr, *scon, *eptr, *ep, *eq;
+  const int *rowptr, *rowperm, *colidx, *sptr, *scon, *eptr, *ep, *eq;
   const double *scoef, *ecoef, *ginv;
   const double *W, *U;
   double *T, *Vval;
@@ -313,6 +313,7 @@ struct sdp_problem {
   // ---- sparse constraint operator (device) ----
   int nnzV = 0;            // CSR pattern of V = sum v_i A_i (both triangles)
   int* rowptr = nullptr;   // n+1
+  int* rowperm = nullptr;  // n   rows by decreasing length (SpMM thread -> row)
   int* colidx = nullptr;   // nnzV
   int* sptr = nullptr;     // nnzV+1  slot -> contributors
   int* scon = nullptr;     // contributors: constraint
@@ -492,20 +493,23 @@ int batch_blocks_tail(int m);
 int batch_blocks_fwdP(int np);
 int batch_blocks_warp_rows(int rows);
 int batch_blocks_outR(int Rk);
+int batch_blocks_out_bwd(int Rk, int np);
 int batch_blocks_split_G(int n);
 int batch_blocks_split_R(int n);
 int batch_blocks_split_Q(int n, int k);
 int batch_blocks_spmm_lp(int n);
 void batch_launch_matvec_lp(cudaStream_t st, const BDesc* desc, const int* off_g, const int* off_r,
                             const int* off_q, const int* off_spmm, const int* off_sddmm, int N, int nb_g, int nb_r,
-                            int nb_q, int nb_spmm, int nb_sddmm, int nmax);
+                            int nb_q, int nb_spmm, int nb_sddmm, int nmax, bool with_sddmm = true);
 void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm, const int* off_spmm,
                          const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax, int spmm_r);
+// the reduced-precision matvec pieces; with_sddmm = false leaves the gather to batch_launch_sddmm_mixed
 void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb);
-void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
-// flag != nullptr (host-driven loop): flag[0] = some problem active, flag[1 + i] = problem i
-// active, instead of setting the graph condition
-void batch_launch_any(cudaStream_t st, const BDesc* desc, int N, cudaGraphConditionalHandle cond, int* flag);
+// direction update; also sets the loop condition (graph) or the host-loop flags
+void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb,
+                    cudaGraphConditionalHandle cond, int* flag);
+// the FP64 and reduced-precision gathers of a mixed batch in one launch
+void batch_launch_sddmm_mixed(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
 void batch_launch_hat_u(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
 void batch_launch_tail(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb);
 void batch_launch_core_solve(cudaStream_t st, const BDesc* desc, int N, const int* off_fwdP, int nb_fwdP,

@@ -68,17 +68,21 @@ void assemble_V(sdp_problem* h, const double* v, const double* scale, double* Vv
 // K1: T = W V, R rows of W per CTA staged in shared memory
 // ---------------------------------------------------------------------------
 constexpr int SPMM_UNROLL = 8;
+// Thread t of the CTA handles row perm[t] of V (rows by decreasing length, so
+// that the lanes of a warp walk rows of about the same length).
 template <int R>
 __device__ __forceinline__ void spmm_f64_body(int blk, int n, const int* __restrict__ rowptr,
-                                              const int* __restrict__ colidx, const double* __restrict__ Vval,
-                                              const double* __restrict__ W, double* __restrict__ T, double* wsh) {
+                                              const int* __restrict__ perm, const int* __restrict__ colidx,
+                                              const double* __restrict__ Vval, const double* __restrict__ W,
+                                              double* __restrict__ T, double* wsh) {
   const int r0 = blk * R;
   for (int t = threadIdx.x; t < R * n; t += blockDim.x) {
     const int rr = t / n, c = t % n;
     wsh[t] = (r0 + rr < n) ? W[(size_t)(r0 + rr) * n + c] : 0.0;
   }
   __syncthreads();
-  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int l = perm[t];
     double acc[R];
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) acc[rr] = 0.0;
@@ -112,24 +116,27 @@ __device__ __forceinline__ void spmm_f64_body(int blk, int n, const int* __restr
 }
 template <int R>
 __global__ void __launch_bounds__(256) k_spmm_wv_f64(int n, const int* __restrict__ rowptr,
+                                                     const int* __restrict__ perm,
                                                      const int* __restrict__ colidx,
                                                      const double* __restrict__ Vval,
                                                      const double* __restrict__ W, double* __restrict__ T) {
   extern __shared__ double wsh[];  // R x n
-  spmm_f64_body<R>(blockIdx.x, n, rowptr, colidx, Vval, W, T, wsh);
+  spmm_f64_body<R>(blockIdx.x, n, rowptr, perm, colidx, Vval, W, T, wsh);
 }
 
 template <typename TW, int R>
 __device__ __forceinline__ void spmm_lp_body(int blk, int n, const int* __restrict__ rowptr,
-                                             const int* __restrict__ colidx, const double* __restrict__ Vval,
-                                             const TW* __restrict__ W, float* __restrict__ T, float* fsh) {
+                                             const int* __restrict__ perm, const int* __restrict__ colidx,
+                                             const double* __restrict__ Vval, const TW* __restrict__ W,
+                                             float* __restrict__ T, float* fsh) {
   const int r0 = blk * R;
   for (int t = threadIdx.x; t < R * n; t += blockDim.x) {
     const int rr = t / n, c = t % n;
     fsh[t] = (r0 + rr < n) ? tof<TW>(W[(size_t)(r0 + rr) * n + c]) : 0.f;
   }
   __syncthreads();
-  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int l = perm[t];
     float acc[R];
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) acc[rr] = 0.f;
@@ -161,11 +168,12 @@ __device__ __forceinline__ void spmm_lp_body(int blk, int n, const int* __restri
 }
 template <typename TW, int R>
 __global__ void __launch_bounds__(256) k_spmm_wv_lp(int n, const int* __restrict__ rowptr,
+                                                    const int* __restrict__ perm,
                                                     const int* __restrict__ colidx,
                                                     const double* __restrict__ Vval,
                                                     const TW* __restrict__ W, float* __restrict__ T) {
   extern __shared__ float fsh[];  // R x n
-  spmm_lp_body<TW, R>(blockIdx.x, n, rowptr, colidx, Vval, W, T, fsh);
+  spmm_lp_body<TW, R>(blockIdx.x, n, rowptr, perm, colidx, Vval, W, T, fsh);
 }
 
 // ---------------------------------------------------------------------------
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(256) kb_spmm(const BDesc* __restrict__ desc, c
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
   if (!D.active || D.lp) return;
-  spmm_f64_body<R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W, D.T, wsh);
+  spmm_f64_body<R>(blockIdx.x - off[i], D.n, D.rowptr, D.rowperm, D.colidx, D.Vval, D.W, D.T, wsh);
 }
 static void launch_kb_spmm(cudaStream_t st, int R, const BDesc* desc, const int* off, int N, int nb, int nmax) {
   const size_t smem = (size_t)R * nmax * sizeof(double);
@@ -287,9 +295,11 @@ __global__ void __launch_bounds__(256) kb_sddmm(const BDesc* __restrict__ desc, 
 int batch_blocks_assemble(int nnzV) { return (int)cdiv(nnzV, 256); }
 int batch_blocks_spmm(int n, int R) { return (int)cdiv(n, R); }
 int batch_blocks_sddmm(int m) { return (int)cdiv(m, SDDMM_PER_BLOCK); }
+// nb_sddmm = 0 leaves the gather out (a mixed batch launches it with the
+// reduced-precision one, batch_launch_sddmm_mixed)
 void batch_launch_matvec(cudaStream_t st, const BDesc* desc, const int* off_asm, const int* off_spmm,
                          const int* off_sddmm, int N, int nb_asm, int nb_spmm, int nb_sddmm, int nmax, int spmm_r) {
-  count_launch(3);
+  count_launch(nb_sddmm > 0 ? 3 : 2);
   if (nb_asm > 0) kb_assemble<<<nb_asm, 256, 0, st>>>(desc, off_asm, N);
   if (nb_spmm > 0) launch_kb_spmm(st, spmm_r, desc, off_spmm, N, nb_spmm, nmax);
   if (nb_sddmm > 0) kb_sddmm<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
@@ -497,10 +507,11 @@ __global__ void __launch_bounds__(256) kb_spmm_lp(const BDesc* __restrict__ desc
   const BDesc& D = desc[i];
   if (!D.active || !D.lp) return;
   if (D.bf)
-    spmm_lp_body<__nv_bfloat16, BATCH_SPMM_LP_R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W16, D.T32,
-                                                 fsh);
+    spmm_lp_body<__nv_bfloat16, BATCH_SPMM_LP_R>(blockIdx.x - off[i], D.n, D.rowptr, D.rowperm, D.colidx, D.Vval,
+                                                 D.W16, D.T32, fsh);
   else
-    spmm_lp_body<float, BATCH_SPMM_LP_R>(blockIdx.x - off[i], D.n, D.rowptr, D.colidx, D.Vval, D.W32, D.T32, fsh);
+    spmm_lp_body<float, BATCH_SPMM_LP_R>(blockIdx.x - off[i], D.n, D.rowptr, D.rowperm, D.colidx, D.Vval, D.W32,
+                                         D.T32, fsh);
 }
 __global__ void __launch_bounds__(256) kb_sddmm_lp(const BDesc* __restrict__ desc, const int* __restrict__ off,
                                                    int N) {
@@ -520,17 +531,41 @@ int batch_blocks_split_G(int n) { return (int)cdiv((size_t)n * 32, 256); }
 int batch_blocks_split_R(int n) { return (int)cdiv(n, 128) * SPLIT_CHUNKS; }
 int batch_blocks_split_Q(int n, int k) { return (int)cdiv(std::max((size_t)n * k, (size_t)k * k * 32), 256); }
 int batch_blocks_spmm_lp(int n) { return (int)cdiv(n, BATCH_SPMM_LP_R); }
+// Both gathers of a mixed batch in one launch: the two forms share the block
+// partition (and the reduction groups), so each problem runs the same code as
+// in its own launch.
+__global__ void __launch_bounds__(256) kb_sddmm_mixed(const BDesc* __restrict__ desc, const int* __restrict__ off,
+                                                      int N) {
+  const int i = batch_find(off, N, blockIdx.x);
+  const BDesc& D = desc[i];
+  if (!D.active) return;
+  const int lb = blockIdx.x - off[i], nb = off[i + 1] - off[i];
+  if (!D.lp)
+    sddmm_f64_body(lb, nb, D.n, D.m, D.eptr, D.ep, D.eq, D.ecoef, D.W, D.T, D.pq, D.pp, D.part, D.ticket,
+                   D.scal + S_PQ, D.scal + S_RZ, D.scal + S_RZN);
+  else if (D.bf)
+    sddmm_lp_body<__nv_bfloat16>(lb, nb, D.n, D.m, D.eptr, D.ep, D.eq, D.ecoef, D.W16, D.T32, D.pq, D.pp, D.part,
+                                 D.ticket, D.scal + S_PQ, D.scal + S_RZ, D.scal + S_RZN, D.ks, D.Etop, D.mvR, D.mvQ);
+  else
+    sddmm_lp_body<float>(lb, nb, D.n, D.m, D.eptr, D.ep, D.eq, D.ecoef, D.W32, D.T32, D.pq, D.pp, D.part, D.ticket,
+                         D.scal + S_PQ, D.scal + S_RZ, D.scal + S_RZN, D.ks, D.Etop, D.mvR, D.mvQ);
+}
+void batch_launch_sddmm_mixed(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb) {
+  count_launch();
+  if (nb > 0) kb_sddmm_mixed<<<nb, 256, 0, st>>>(desc, off, N);
+}
+
 void batch_launch_matvec_lp(cudaStream_t st, const BDesc* desc, const int* off_g, const int* off_r,
                             const int* off_q, const int* off_spmm, const int* off_sddmm, int N, int nb_g, int nb_r,
-                            int nb_q, int nb_spmm, int nb_sddmm, int nmax) {
+                            int nb_q, int nb_spmm, int nb_sddmm, int nmax, bool with_sddmm) {
   const size_t smem = (size_t)BATCH_SPMM_LP_R * nmax * sizeof(float);
   allow_max_smem((const void*)kb_spmm_lp);
-  count_launch(5);
+  count_launch(with_sddmm ? 5 : 4);
   if (nb_g > 0) kb_split_G<<<nb_g, 256, 0, st>>>(desc, off_g, N);
   if (nb_r > 0) kb_split_R_part<<<nb_r, 128, 0, st>>>(desc, off_r, N);
   if (nb_q > 0) kb_split_R_Q<<<nb_q, 256, 0, st>>>(desc, off_q, N);
   if (nb_spmm > 0) kb_spmm_lp<<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N);
-  if (nb_sddmm > 0) kb_sddmm_lp<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
+  if (with_sddmm && nb_sddmm > 0) kb_sddmm_lp<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
 }
 
 // Reduced-precision copy of W, or of W_s when a preconditioner with top
@@ -593,14 +628,16 @@ static void launch_spmm_f64(sdp_problem* h, const double* Vval) {
   const size_t smem = (size_t)R * h->n * sizeof(double);
   allow_max_smem((const void*)k_spmm_wv_f64<R>);
   count_launch();
-  k_spmm_wv_f64<R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->colidx, Vval, h->W, h->T);
+  k_spmm_wv_f64<R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->rowperm, h->colidx, Vval, h->W,
+                                                              h->T);
 }
 template <typename TW, int R>
 static void launch_spmm_lp(sdp_problem* h, const double* Vval, const TW* W) {
   const size_t smem = (size_t)R * h->n * sizeof(float);
   allow_max_smem((const void*)k_spmm_wv_lp<TW, R>);
   count_launch();
-  k_spmm_wv_lp<TW, R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->colidx, Vval, W, h->T32);
+  k_spmm_wv_lp<TW, R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->rowperm, h->colidx, Vval, W,
+                                                                 h->T32);
 }
 
 sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec, double* dot_out, double* pro_dst,

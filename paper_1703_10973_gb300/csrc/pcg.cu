@@ -92,48 +92,41 @@ __global__ void kb_pcg_xr(BDesc* __restrict__ desc, const int* __restrict__ off,
                               D.part, D.ticket, &decided);
   if (decided && !go) D.active = 0;
 }
-__global__ void kb_pcg_p(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+// The direction update also decides the batch loop: block 0 reads every
+// problem's active flag (final since kb_pcg_xr ran earlier in the stream) and
+// sets the graph condition, or with flag != nullptr (host-driven loop) writes
+// flag[0] = some problem active, flag[1 + i] = problem i active.
+__global__ void kb_pcg_p(const BDesc* __restrict__ desc, const int* __restrict__ off, int N,
+                         cudaGraphConditionalHandle cond, int* flag) {
+  if (blockIdx.x == 0) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const int a = desc[i].active ? 1 : 0;
+      if (flag) flag[1 + i] = a;
+      if (a) any = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (flag) flag[0] = any;
+      else cudaGraphSetConditional(cond, any ? 1u : 0u);
+    }
+  }
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
   if (!D.active) return;
   pcg_p_body(blockIdx.x - off[i], off[i + 1] - off[i], D.m, D.pp, D.pz, D.scal);
-}
-__global__ void kb_any_active(const BDesc* __restrict__ desc, int N, cudaGraphConditionalHandle cond) {
-  __shared__ int any;
-  if (threadIdx.x == 0) any = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x)
-    if (desc[i].active) any = 1;
-  __syncthreads();
-  if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
-}
-// Host-driven form (no graph): flag[0] = some problem active, flag[1 + i] =
-// problem i active, read back after every iteration.
-__global__ void kb_any_active_flag(const BDesc* __restrict__ desc, int N, int* flag) {
-  __shared__ int any;
-  if (threadIdx.x == 0) any = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const int a = desc[i].active ? 1 : 0;
-    flag[1 + i] = a;
-    if (a) any = 1;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) flag[0] = any;
 }
 int batch_blocks_vec(int m) { return (int)std::min(cdiv(m, 256), 2048u); }
 void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb) {
   count_launch();
   if (nb > 0) kb_pcg_xr<<<nb, 256, 0, st>>>(desc, off, N);
 }
-void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb) {
+void batch_launch_p(cudaStream_t st, const BDesc* desc, const int* off, int N, int nb,
+                    cudaGraphConditionalHandle cond, int* flag) {
   count_launch();
-  if (nb > 0) kb_pcg_p<<<nb, 256, 0, st>>>(desc, off, N);
-}
-void batch_launch_any(cudaStream_t st, const BDesc* desc, int N, cudaGraphConditionalHandle cond, int* flag) {
-  count_launch();
-  if (flag) kb_any_active_flag<<<1, 256, 0, st>>>(desc, N, flag);
-  else kb_any_active<<<1, 256, 0, st>>>(desc, N, cond);
+  kb_pcg_p<<<nb > 0 ? nb : 1, 256, 0, st>>>(desc, off, N, cond, flag);
 }
 
 __global__ void k_pcg_init(double* scal, double rtol, int maxit) {

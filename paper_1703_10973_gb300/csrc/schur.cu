@@ -614,6 +614,18 @@ __global__ void kb_outR(const BDesc* __restrict__ desc, const int* __restrict__ 
   HS_BATCH_PROLOGUE
   outR_body(lb * blockDim.x + threadIdx.x, Dd.nr, Dd.k, Dd.rverts, Dd.v1, Dd.zscale, Dd.Bn);
 }
+// The last step of the core solve in one launch: the first ceil(Rk / 256)
+// blocks of a problem scatter x_R (outR), the rest substitute on the P rows
+// (bwdP); both only read x_R.
+__global__ void kb_out_bwd(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
+  HS_BATCH_PROLOGUE
+  const int nout = (Dd.Rk + 255) / 256;
+  if (lb < nout) outR_body(lb * blockDim.x + threadIdx.x, Dd.nr, Dd.k, Dd.rverts, Dd.v1, Dd.zscale, Dd.Bn);
+  else
+    bwdP_body(((lb - nout) * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, Dd.np, Dd.k, Dd.pverts, Dd.bptr,
+              Dd.bcol, Dd.F, Dd.D, Dd.yP, Dd.v1, Dd.zscale, Dd.Bn);
+}
+int batch_blocks_out_bwd(int Rk, int np) { return (int)(cdiv(Rk, 256) + cdiv((size_t)np * 32, 256)); }
 __global__ void kb_bwdP(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
   HS_BATCH_PROLOGUE
   bwdP_body((lb * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31, Dd.np, Dd.k, Dd.pverts, Dd.bptr, Dd.bcol, Dd.F,
@@ -640,13 +652,12 @@ void batch_launch_core_solve(cudaStream_t st, const BDesc* desc, int N, const in
     kb_gemv_lower<<<nb_gemv, 256, 0, st>>>(desc, off_gemv, N);
     kb_gemv_upper<<<nb_gemv, 256, 0, st>>>(desc, off_gemv, N);
   }
+  // off_outR / nb_outR: the merged out_bwd partition (batch_blocks_out_bwd)
+  (void)off_bwdP;
+  (void)nb_bwdP;
   if (nb_outR > 0) {
     count_launch();
-    kb_outR<<<nb_outR, 128, 0, st>>>(desc, off_outR, N);
-  }
-  if (nb_bwdP > 0) {
-    count_launch();
-    kb_bwdP<<<nb_bwdP, 256, 0, st>>>(desc, off_bwdP, N);
+    kb_out_bwd<<<nb_outR, 256, 0, st>>>(desc, off_outR, N);
   }
 }
 

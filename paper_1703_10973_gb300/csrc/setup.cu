@@ -298,7 +298,15 @@ static sdp_status build(sdp_problem* h, int64_t nnzC, const int32_t* Ci, const i
   std::vector<double> ginv(m);
   for (int k = 0; k < m; ++k) ginv[k] = 1.0 / g[k];
 
+  // rows of V by decreasing length: the SpMM gives consecutive threads of a warp
+  // rows of about the same length, so no lane idles while the longest finishes
+  std::vector<int> rowperm(n);
+  for (int r = 0; r < n; ++r) rowperm[r] = r;
+  std::stable_sort(rowperm.begin(), rowperm.end(), [&](int a, int b2) {
+    return rowptr[a + 1] - rowptr[a] > rowptr[b2 + 1] - rowptr[b2];
+  });
   SDP_TRY(upload(h, &h->rowptr, rowptr));
+  SDP_TRY(upload(h, &h->rowperm, rowperm));
   SDP_TRY(upload(h, &h->colidx, colidx));
   SDP_TRY(upload(h, &h->sptr, sptr));
   SDP_TRY(upload(h, &h->scon, scon));

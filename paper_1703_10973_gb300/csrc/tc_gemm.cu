@@ -318,7 +318,7 @@ sdp_status tc_gemm(cudaStream_t st, int prec, int M, int N, int K, const double*
   count_launch(2);
   if (bf16) {
     k_tc_pack<__nv_bfloat16><<<dim3(cdiv(Kp, 32), cdiv(Mp, 32)), tb, 0, st>>>(
-        transA ? M : M, K, A, lda, transA, Mp, Kp, reinterpret_cast<__nv_bfloat16*>(wa));
+        M, K, A, lda, transA, Mp, Kp, reinterpret_cast<__nv_bfloat16*>(wa));
     // the B operand is op(B)^T (N x K): row n, column k = op(B)[k][n]
     k_tc_pack<__nv_bfloat16><<<dim3(cdiv(Kp, 32), cdiv(Np, 32)), tb, 0, st>>>(
         N, K, B, ldb, !transB, Np, Kp, reinterpret_cast<__nv_bfloat16*>(wb));

@@ -554,3 +554,23 @@ def test_hhat_core_above_eight_matches_oracle():
     kap = np.linalg.cond(Hh)
     assert _rel(z, np.linalg.solve(Hh, r)) <= max(1e-12, 20.0 * kap * np.finfo(float).eps)
     assert _rel(z32, np.linalg.solve(Hh, r)) <= 20.0 * kap * 2.0 ** -24
+
+
+@pytest.mark.parametrize("mu", [1e-2, 1e-5])
+def test_hhat_apply_solves_the_augmented_system(mu):
+    """The GPU Hhat apply (SMW with the block-sparse core) returns the solution of the
+    sparse augmented system of eq. (aug_prec) as the oracle's LDL^T without
+    pivoting computes it (the elimination the paper recommends for Hhat, whose
+    first step leaves exactly the core the GPU factors)."""
+    d = si.mc_instance(9, 11, 2, 60, 6)
+    P = o.Problem.from_data(d)
+    W = _ipm_like_W(d.n, 2, mu, 3)
+    r = si.random_vec(d.m, 2)
+    x = o.aug_prec_solve(P, W, 2, r)
+    Hh = o.precond_hat_dense(P, W, 2)
+    with _prob(d, precond=2) as prob:
+        prob.set_W(_dev(W))
+        prob.precond_build()
+        z = prob.precond_apply(_dev(r)).cpu().numpy()
+    tol = max(1e-12, 20.0 * np.linalg.cond(Hh) * np.finfo(float).eps)
+    assert _rel(z, x) <= tol

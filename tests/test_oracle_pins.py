@@ -493,3 +493,32 @@ def test_rank_estimate_tracks_rank_of_X_when_recovery_fails():
     assert rank_x > 3
     W = o.nt_scaling(res.X, res.S)
     assert o.rank_estimate(W, kmax=6, eta=10.0) == rank_x
+
+
+def test_aug_prec_ldl_equals_hhat_and_its_core():
+    """eq. (aug_prec): the augmented system of Section V, factored by LDL^T without
+    pivoting, solves Hhat x = b (against the explicit Kronecker form of eq.
+    sparse_prec), and eliminating its first block (tau^2 A^T A, diagonal under
+    Assumption 2) leaves -1/2 of the core tau^2 I + 2 tau K that the SMW apply
+    factors -- the paper's remark that elimination without pivoting on the
+    augmented system takes the same steps as the SMW formula."""
+    d = si.mc_instance(6, 7, 2, 30, 3)
+    P = o.Problem.from_data(d)
+    rng = np.random.default_rng(1)
+    Q, _ = np.linalg.qr(rng.standard_normal((d.n, d.n)))
+    W = (Q * np.concatenate([rng.uniform(1, 3, d.n - 2), [50.0, 40.0]])) @ Q.T
+    b = rng.standard_normal(d.m)
+    x = o.aug_prec_solve(P, W, 2, b)
+    Hh = o.precond_hat_dense(P, W, 2)
+    assert np.linalg.norm(Hh @ x - b) <= 1e-12 * np.linalg.norm(b)
+    K = o.aug_prec_matrix(P, W, 2)
+    m = d.m
+    schur = K[m:, m:] - K[m:, :m] @ np.linalg.solve(K[:m, :m], K[:m, m:])
+    pc = o.precond_hat_build(P, W, 2)
+    assert np.allclose(schur, -0.5 * pc.Sc, rtol=1e-12, atol=1e-12 * np.abs(pc.Sc).max())
+    # a wrong scaling of the off-diagonal blocks breaks the identity
+    K2 = K.copy()
+    K2[m:, :m] *= 2.0
+    K2[:m, m:] *= 2.0
+    x2 = o.ldl_nopivot_solve(K2, np.concatenate([b, np.zeros(K.shape[0] - m)]))[:m]
+    assert np.linalg.norm(Hh @ x2 - b) > 1e-3 * np.linalg.norm(b)
