@@ -291,7 +291,7 @@ class Arm:
         self.probs = [SDPProblem.from_data(d, params=self.params, stream=self.streams[i % n].cuda_stream)
                       for i, d in enumerate(insts)]
         self.batch = None
-        self.bstream = torch.cuda.Stream()
+        self.bstream = torch.cuda.Stream(priority=-1)   # PCG stages ahead of the dense phases
         if args.batched_launch:
             self.batch = SDPBatch(self.probs, stream=self.bstream.cuda_stream, groups=args.batch_groups)
         self.step_ms, self.lat_ms, self.res = [], [], None

@@ -269,7 +269,8 @@ int64_t sdp_launch_count(const sdp_problem* h);
  * sdp_batch_solve runs their interior-point iterations in lockstep: the dense
  * per-problem phases on each problem's stream (one host thread per problem),
  * and every PCG iteration of all their Newton systems as one sequence of
- * batched launches on cuda_stream, captured once as a CUDA graph that loops on
+ * batched launches on cuda_stream (during those solves the problems' own work
+ * also runs on cuda_stream; give it a high priority), captured once as a CUDA graph that loops on
  * the device while any problem's PCG is running.  A problem's iterates are the
  * same in a batch as alone.  results: count entries (NULL allowed); the
  * seconds field of each is the host wall time from the start of the call to

@@ -344,9 +344,35 @@ static sdp_status batch_autotune(sdp_batch* b, const std::vector<BDesc>& hd) {
 }
 
 // The Newton systems H dy = rhs of the listed problems, solved together.
+// While their Newton systems are solved, the listed problems issue all their
+// work (sweep set-up, true residuals, the batched graph) on the batch's stream:
+// their own streams are idle then, and a batch stream of high priority keeps
+// this latency-bound work ahead of other lockstep groups' dense phases.  The
+// guard hands each problem its own stream back, after the batch stream is idle.
+struct StreamSwap {
+  sdp_batch* b;
+  std::vector<std::pair<sdp_problem*, cudaStream_t>> saved;
+  StreamSwap(sdp_batch* bb, const std::vector<int>& idx) : b(bb) {
+    if (!b->stream) return;
+    for (int i : idx) {
+      sdp_problem* h = b->hs[i];
+      if (h->stream == b->stream) continue;
+      cudaStreamSynchronize(h->stream);
+      saved.push_back({h, h->stream});
+      h->stream = b->stream;
+    }
+  }
+  ~StreamSwap() {
+    if (saved.empty()) return;
+    cudaStreamSynchronize(b->stream);
+    for (auto& sv : saved) sv.first->stream = sv.second;
+  }
+};
+
 static sdp_status batch_newton(sdp_batch* b, const std::vector<int>& idx, std::vector<int>& its,
                                std::vector<double>& rr, std::vector<sdp_status>& st) {
   const int N = (int)b->hs.size();
+  StreamSwap swap(b, idx);
   std::vector<PcgSweeps> S(N);
   std::vector<char> live(N, 0);
   for (int i : idx) {
@@ -494,7 +520,9 @@ static sdp_status batch_make_groups(sdp_batch* b, int G) {
   for (int t = 0; t < N; ++t) b->members[t % G].push_back(order[t]);
   for (int g = 0; g < G; ++g) {
     cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    int lo = 0, hi = 0;   // the PCG of a group runs on its stream: highest priority
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, hi) != cudaSuccess) {
       cudaGetLastError();
       b->last_error = "sdp_batch: stream creation failed";
       return SDP_ERR_CUDA;

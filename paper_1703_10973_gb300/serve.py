@@ -245,7 +245,7 @@ class BatchServer:
         errors = []
 
         def group(g):
-            bstream = torch.cuda.Stream()
+            bstream = torch.cuda.Stream(priority=-1)   # the batched PCG ahead of other groups' dense phases
             batch = SDPBatch([], stream=bstream.cuda_stream)
             members = {}                     # id(prob) -> (prob, request, start, stream)
             free_streams = []

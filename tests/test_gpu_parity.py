@@ -390,8 +390,8 @@ def test_solve_general_sparse_planted():
 # so the GPU solves run to the accuracy of the paper's experiments (Section VI
 # reports 8 to 10 digits): gap and infeasibilities <= 1e-8.  The explicit-Hessian
 # oracle cannot follow there: kappa(H) grows like 1/mu^2 and its Cholesky of H
-# breaks down before mu reaches 1e-9, so it stops at the 1e-6 of the north-star
-# tolerance.  In the exact-recovery regime the optimum is the planted M, which
+# breaks down before mu reaches 1e-9, so it stops at the 1e-6 gap of the
+# objective tolerance.  In the exact-recovery regime the optimum is the planted M, which
 # pins the 1e-8 solve; the oracle pins the objective.
 TIGHT = dict(gap_tol=1e-8, infeas_tol=1e-8)
 
