@@ -80,7 +80,8 @@ typedef struct {
   int prec;            /* sdp_prec used inside PCG by sdp_ipm_step / sdp_solve     */
   int precond;         /* sdp_precond_kind; SDP_PRECOND_HAT                        */
   double inner_rtol;   /* PCG tolerance of one restart (sweep); 1e-9                */
-  int verbose;         /* 1 = one line per IPM iteration on stderr                 */
+  int verbose;         /* 1 = one line per IPM iteration on stderr; 2 = also one   */
+                       /* line per PCG restart (sweep)                           */
   int pcg_graph;       /* 1 = the PCG loop runs on the device as a CUDA graph with */
                        /* a conditional while node (default); 0 = host-driven     */
                        /* loop launching the same kernels (for profilers that do  */
@@ -286,8 +287,8 @@ sdp_status sdp_batch_solve(sdp_batch* b, sdp_result* results);
 const char* sdp_batch_last_error(const sdp_batch* b);
 void sdp_batch_destroy(sdp_batch* b);
 /* Lockstep groups of a batch (default 0 = pairs: ceil(count / 2) groups).
- * sdp_batch_solve deals the problems, largest first, round-robin into the
- * groups and solves every group as its own lockstep batch on its own stream
+ * sdp_batch_solve deals the problems, largest first, into the groups in a
+ * snake order (0..G-1, G-1..0, ...) and solves every group as its own lockstep batch on its own stream
  * and host thread, so that one group's dense phases overlap another group's
  * batched PCG.  1 = all problems in one lockstep.  Results do not depend on
  * the grouping (each problem's iterates are the same as alone).

@@ -126,7 +126,7 @@ static BDesc make_desc(sdp_problem* h, int active, int prec) {
   D.bp = h->hs_bp; D.bptr = h->hs_bptr; D.bcol = h->hs_bcol;
   D.D = h->hs_D; D.F = h->hs_F; D.Cinv = h->hs_Cinv; D.CinvT = h->hs_CinvT;
   D.yP = h->hs_yP; D.v1 = h->hs_v1; D.v2 = h->hs_v2; D.uvec = h->uvec; D.Bn = h->Bn;
-  D.px = h->px; D.pr = h->pr; D.pp = h->pp; D.pq = h->pq; D.pz = h->pz;
+  D.px = h->px; D.pr = h->pr; D.pp = h->pp; D.pq = h->pq; D.pz = h->pz; D.pxb = h->pxb;
   D.scal = h->scal; D.part = h->pcg_part; D.ticket = h->pcg_ticket;
   D.lp = (prec == SDP_FP32 || prec == SDP_BF16) ? 1 : 0;
   D.bf = (prec == SDP_BF16) ? 1 : 0;
@@ -506,8 +506,9 @@ extern "C" sdp_status sdp_batch_create(sdp_problem* const* hs, int count, void* 
 
 static sdp_status batch_solve_lockstep(sdp_batch* b, sdp_result* results);
 
-// Groups: problems sorted by order, largest first, dealt round-robin, so that
-// the groups carry similar work; each group is a lockstep batch of its own on
+// Groups: problems sorted by order, largest first, dealt in a snake (0..G-1,
+// G-1..0, ...), so that the group holding the largest problem gets the
+// smallest of the next round and the groups carry similar work; each group is a lockstep batch of its own on
 // its own stream and host thread.  One group's dense phases then overlap
 // another group's batched PCG instead of all problems alternating together
 // between latency-bound phases and the throughput-bound PCG.
@@ -517,7 +518,10 @@ static sdp_status batch_make_groups(sdp_batch* b, int G) {
   for (int i = 0; i < N; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->hs[x]->n > b->hs[y]->n; });
   b->members.assign(G, {});
-  for (int t = 0; t < N; ++t) b->members[t % G].push_back(order[t]);
+  for (int t = 0; t < N; ++t) {
+    const int r = t % G;
+    b->members[((t / G) % 2 == 0) ? r : G - 1 - r].push_back(order[t]);
+  }
   for (int g = 0; g < G; ++g) {
     cudaStream_t s = nullptr;
     int lo = 0, hi = 0;   // the PCG of a group runs on its stream: highest priority

@@ -447,6 +447,198 @@ __global__ void __launch_bounds__(SY_THREADS) k_sytrd_cluster_smem(int n, double
   }
 }
 
+// One-triangle shared-memory cluster form.  Row i keeps only its lower part
+// A[i][0..i] (packed) in CTA i mod cs, so the matrix of order up to ~880 fits
+// one 16-CTA cluster, and the symmetric rank-2 update touches one triangle:
+// 2 len^2 FMAs per column instead of the 3 len^2 of the full-storage form.
+// With lower storage, p = A22 v splits into a row part (the owner's dot of its
+// lower row with v) and a column part (for column c, the sum over rows i > c
+// of A[i][c] v_i, which every CTA forms over its own rows).  Per column j:
+//   0: every CTA builds the reflector from the column j that the owners of
+//      rows i > j broadcast into vn at the end of column j - 1;
+//   1: row parts (warp per owned row) and the CTA's column parts (thread per
+//      column); cluster barrier;
+//   2: the owner of row i adds its row part to the 16 CTAs' column parts for i
+//      (fixed order), scales by tau and broadcasts p_i and its share of p^T v;
+//      cluster barrier;
+//   3: w = p - (tau / 2)(p^T v) v; owned rows updated on c in [j + 1, i];
+//      the reflector is stored in column j of the owned rows, and column
+//      j + 1 is broadcast into vn; cluster barrier.
+// Remote buffers and the barriers that order them: vn is written in step 3
+// and read in step 0 of the next column (barrier 3 between; the next writes
+// come after barriers 1 and 2); part is read remotely between barriers 1 and
+// 2 and reused as w after barrier 2; p and kpart are written remotely
+// between barriers 1 and 2 and read after barrier 2.  Every sum runs in a
+// fixed order, so the result does not depend on timing.  At the end the
+// rows are written back with the lower part mirrored into the upper one:
+// row j then holds the reflector in A[j][j+1..], as the back-transformation
+// expects.
+__device__ __forceinline__ size_t sy_off(int sl, int cs, int rank) {
+  return (size_t)cs * sl * (sl - 1) / 2 + (size_t)sl * (rank + 1);
+}
+__global__ void __launch_bounds__(SY_THREADS) k_sytrd_cluster_lower(int n, double* A, int lda, double* d, double* e,
+                                                                     double* tauh) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cs = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ double sm[];
+  const int slots = (n - rank + cs - 1) / cs;      // owned rows i = sl cs + rank < n
+  // the vectors come first, at the same offset in every CTA (a remote access
+  // maps the local offset); the packed rows, whose length depends on the
+  // rank, follow them
+  double* v = sm;               // n: the reflector of the current column
+  double* vn = v + n;           // n: the next column (written remotely)
+  double* part = vn + n;        // n: column parts (read remotely), then w
+  double* p = part + n;         // n: tau A22 v (written remotely)
+  double* rowp = p + n;         // ceil(n / cs): row parts of the owned rows
+  double* rows = rowp + (n + cs - 1) / cs;
+  __shared__ double kpart[32];
+  __shared__ double red[32];
+  __shared__ double s_tau, s_beta, s_scale;
+  const int wpb = blockDim.x / 32, wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int sl = 0; sl < slots; ++sl) {
+    const int i = sl * cs + rank;
+    double* ri = rows + sy_off(sl, cs, rank);
+    for (int c = threadIdx.x; c <= i; c += blockDim.x) ri[c] = __ldcg(A + (size_t)i * lda + c);
+  }
+  cluster.sync();
+  // column 0 into every CTA's vn
+  for (int sl = wid; sl < slots; sl += wpb) {
+    const int i = sl * cs + rank;
+    if (i >= 1 && lane < cs) cluster.map_shared_rank(vn, lane)[i - 1] = rows[sy_off(sl, cs, rank)];
+  }
+  cluster.sync();
+  for (int j = 0; j < n - 2; ++j) {
+    const int len = n - j - 1;
+    // ---- 0: reflector from the broadcast column
+    double s = 0.0;
+    for (int l = threadIdx.x; l < len; l += blockDim.x) {
+      const double x = vn[l];
+      v[l] = x;
+      if (l > 0) s = fma(x, x, s);
+    }
+    s = bsum(s, red);
+    if (threadIdx.x == 0) {
+      const double x0 = v[0];
+      double tau = 0.0, beta = x0, scale = 0.0;
+      if (s > 0.0) {
+        beta = -copysign(sqrt(fma(x0, x0, s)), x0);
+        tau = (beta - x0) / beta;
+        scale = 1.0 / (x0 - beta);
+      }
+      s_tau = tau; s_beta = beta; s_scale = scale;
+    }
+    __syncthreads();
+    const double tau = s_tau, scale = s_scale;
+    for (int l = 1 + threadIdx.x; l < len; l += blockDim.x) v[l] *= scale;
+    if (threadIdx.x == 0) v[0] = 1.0;
+    __syncthreads();
+    // ---- 1: row parts and column parts
+    const int sl0 = (j + 1 > rank) ? (j + 1 - rank + cs - 1) / cs : 0;   // first owned row > j
+    for (int sl = sl0 + wid; sl < slots; sl += wpb) {
+      const int i = sl * cs + rank;
+      const double* ri = rows + sy_off(sl, cs, rank) + j + 1;
+      const int cnt = i - j;                         // c = j + 1 .. i
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int l = lane;
+      for (; l + 96 < cnt; l += 128) {
+        a0 = fma(ri[l], v[l], a0);
+        a1 = fma(ri[l + 32], v[l + 32], a1);
+        a2 = fma(ri[l + 64], v[l + 64], a2);
+        a3 = fma(ri[l + 96], v[l + 96], a3);
+      }
+      for (; l < cnt; l += 32) a0 = fma(ri[l], v[l], a0);
+      const double rp = wsum((a0 + a1) + (a2 + a3));
+      if (lane == 0) rowp[sl] = rp;
+    }
+    for (int l = threadIdx.x; l < len; l += blockDim.x) {
+      const int c = j + 1 + l;
+      int sl = (c >= rank) ? (c - rank) / cs + 1 : 0;   // first owned row > c
+      double acc = 0.0;
+      size_t o = sy_off(sl, cs, rank);
+      for (int i = sl * cs + rank; i < n; i += cs) {
+        acc = fma(rows[o + c], v[i - j - 1], acc);
+        o += (size_t)i + 1;                          // row i holds i + 1 entries
+      }
+      part[l] = acc;
+    }
+    cluster.sync();
+    // ---- 2: p_i for the owned rows, broadcast
+    double kp = 0.0;
+    for (int sl = sl0 + wid; sl < slots; sl += wpb) {
+      const int i = sl * cs + rank;
+      const int li = i - j - 1;
+      double x = (lane < cs) ? cluster.map_shared_rank(part, lane)[li] : 0.0;
+      x = wsum(x);
+      const double pi = (rowp[sl] + x) * tau;
+      if (lane < cs) cluster.map_shared_rank(p, lane)[li] = pi;
+      if (lane == 0) kp = fma(pi, v[li], kp);
+    }
+    kp = bsum(kp, red);
+    const double kp0 = __shfl_sync(0xffffffffu, kp, 0);
+    if (threadIdx.x < cs) cluster.map_shared_rank(kpart, (int)threadIdx.x)[rank] = kp0;
+    cluster.sync();
+    // ---- 3: update, reflector, next column
+    double K = 0.0;
+    for (int c = 0; c < cs; ++c) K += kpart[c];
+    K *= 0.5 * tau;
+    double* w = part;
+    for (int l = threadIdx.x; l < len; l += blockDim.x) w[l] = p[l] - K * v[l];
+    __syncthreads();
+    for (int sl = sl0 + wid; sl < slots; sl += wpb) {
+      const int i = sl * cs + rank;
+      const int li = i - j - 1;
+      double* ri = rows + sy_off(sl, cs, rank);
+      const double vi = v[li], wi = w[li];
+      const int cnt = i - j;
+      double* rr = ri + j + 1;
+      for (int l = lane; l < cnt; l += 32) rr[l] = fma(-vi, w[l], fma(-wi, v[l], rr[l]));
+      __syncwarp();
+      if (lane == 0) ri[j] = vi;                       // reflector entry (row i, column j)
+      if (i > j + 1 && lane < cs) cluster.map_shared_rank(vn, lane)[i - j - 2] = ri[j + 1];
+    }
+    if (threadIdx.x == 0) {
+      if (rank == j % cs) d[j] = rows[sy_off(j / cs, cs, rank) + j];
+      if (rank == 0) {
+        e[j] = s_beta;
+        tauh[j] = tau;
+      }
+    }
+    cluster.sync();
+  }
+  if (threadIdx.x == 0) {
+    if (rank == (n - 2) % cs) {
+      d[n - 2] = rows[sy_off((n - 2) / cs, cs, rank) + n - 2];
+      tauh[n - 2] = 0.0;
+    }
+    if (rank == (n - 1) % cs) {
+      const double* r1 = rows + sy_off((n - 1) / cs, cs, rank);
+      d[n - 1] = r1[n - 1];
+      e[n - 2] = r1[n - 2];
+      e[n - 1] = 0.0;
+      tauh[n - 1] = 0.0;
+    }
+  }
+  for (int sl = 0; sl < slots; ++sl) {
+    const int i = sl * cs + rank;
+    const double* ri = rows + sy_off(sl, cs, rank);
+    for (int c = threadIdx.x; c <= i; c += blockDim.x) {
+      const double x = ri[c];
+      A[(size_t)i * lda + c] = x;
+      A[(size_t)c * lda + i] = x;
+    }
+  }
+}
+
+static size_t sytrd_lower_smem_bytes(int n, int cs) {
+  size_t most = 0;   // packed rows of the rank that holds the most
+  for (int rank = 0; rank < cs; ++rank) {
+    const int slots = (n - rank + cs - 1) / cs;
+    most = std::max(most, (size_t)cs * slots * (slots - 1) / 2 + (size_t)slots * (rank + 1));
+  }
+  return (4 * (size_t)n + (size_t)(n + cs - 1) / cs + most) * sizeof(double);
+}
+
 // Cluster size of the shared-memory form for order n: 16 when the matrix and the
 // work vectors fit in 16 CTAs' shared memory and the device runs such a
 // cluster; 0 otherwise.
@@ -481,6 +673,41 @@ static int sytrd_smem_cluster(int n) {
     int ncl = 0;
     ok16 = (cudaOccupancyMaxActiveClusters(&ncl, (const void*)k_sytrd_cluster_smem, &cfg) == cudaSuccess && ncl > 0)
                ? 1 : 0;
+    cudaGetLastError();
+  }
+  return ok16 ? cs : 0;
+}
+
+// Cluster size of the one-triangle form for order n (16, or 0 when the packed
+// rows and work vectors do not fit 16 CTAs' shared memory or the device does
+// not run such a cluster).
+static int sytrd_lower_cluster(int n) {
+  static int max_optin = -1;
+  static int ok16 = -1;
+  if (max_optin < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  const int cs = 16;
+  if (sytrd_lower_smem_bytes(n, cs) + 2048 > (size_t)max_optin) return 0;
+  if (ok16 < 0) {
+    allow_max_smem((const void*)k_sytrd_cluster_lower);
+    cudaFuncSetAttribute((const void*)k_sytrd_cluster_lower, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(SY_THREADS);
+    cfg.dynamicSmemBytes = (size_t)max_optin - 2048;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    ok16 = (cudaOccupancyMaxActiveClusters(&ncl, (const void*)k_sytrd_cluster_lower, &cfg) == cudaSuccess &&
+            ncl > 0) ? 1 : 0;
     cudaGetLastError();
   }
   return ok16 ? cs : 0;
@@ -537,6 +764,10 @@ static int sytrd_blocks(int n, size_t smem) {
 // once the O(n^3) work needs the whole GPU).
 constexpr int SY_CLUSTER_MAX_N = 1024;
 
+// Order of preference: full rows in cluster shared memory (n <= 656; two
+// barriers per column, the fastest while it fits), the one-triangle form
+// (n <= 880; a third barrier per column but a third less FP64 work), the
+// L2-streaming cluster form, the cooperative grid form.
 static sdp_status sytrd(cudaStream_t st, int n, double* A, EigWork* w) {
   if (n >= 3 && n <= SY_CLUSTER_MAX_N) {
     const int cs = sytrd_smem_cluster(n);
@@ -557,6 +788,30 @@ static sdp_status sytrd(cudaStream_t st, int n, double* A, EigWork* w) {
       count_launch();
       ktimer_begin(st, "sytrd");
       cudaError_t err = cudaLaunchKernelEx(&cfg, k_sytrd_cluster_smem, n, A, lda, w->d, w->e, w->tauh);
+      ktimer_end(st, "sytrd", 4.0 / 3.0 * n * (double)n * n, 16.0 * n * (double)n);
+      if (err == cudaSuccess) return SDP_OK;
+      cudaGetLastError();
+    }
+  }
+  if (n >= 3 && n <= SY_CLUSTER_MAX_N) {
+    const int cs = sytrd_lower_cluster(n);
+    if (cs > 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(SY_THREADS);
+      cfg.dynamicSmemBytes = sytrd_lower_smem_bytes(n, cs);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int lda = n;
+      count_launch();
+      ktimer_begin(st, "sytrd");
+      cudaError_t err = cudaLaunchKernelEx(&cfg, k_sytrd_cluster_lower, n, A, lda, w->d, w->e, w->tauh);
       ktimer_end(st, "sytrd", 4.0 / 3.0 * n * (double)n * n, 16.0 * n * (double)n);
       if (err == cudaSuccess) return SDP_OK;
       cudaGetLastError();

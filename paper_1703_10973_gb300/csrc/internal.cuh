@@ -62,7 +62,7 @@ __device__ inline bool lb_reduce(double v, double* part, unsigned int* ticket, d
 
 // Scalar slots of a PCG run (device array scal[])
 enum { S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZN = 3, S_TMP = 4, S_NR0 = 5, S_TOL2 = 6, S_IT = 7, S_MAXIT = 8,
-       S_BRK = 9, S_GO = 10 };
+       S_BRK = 9, S_GO = 10, S_RRB = 11, S_NEWB = 12 };
 
 // One problem of a batched PCG launch (FP64 or FP32 split matvec, Hhat preconditioner): the
 // device pointers and sizes the batched kernels read, refreshed by the host
@@ -81,7 +81,7 @@ struct BDesc {
   int lpc;                          // the core solve uses the FP32 copy of the Schur-factor inverse
   const float *Cinv32, *CinvT32;
   float *v1f, *v2f;
-  double *px, *pr, *pp, *pq, *pz;
+  double *px, *pr, *pp, *pq, *pz, *pxb;
   double *scal, *part;
   unsigned int* ticket;
   // FP32 split matvec (a problem in a reduced-precision sweep)
@@ -439,7 +439,7 @@ struct sdp_problem {
 
   // ---- PCG vectors ----
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr, *px = nullptr,
-         *pbest = nullptr, *pcorr = nullptr;
+         *pbest = nullptr, *pcorr = nullptr, *pxb = nullptr;
   double* pcg_part = nullptr;          // per-block partials of the fused PCG reductions
   unsigned int* pcg_ticket = nullptr;  // their arrival tickets (one per reduction)
 

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 
 namespace sdpgb {
 
@@ -23,10 +24,20 @@ static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) 
 // preconditioned operator indefinite in some direction) leaves x and r at the
 // last good iterate, sets scal[S_BRK] and ends the loop; the restarted outer
 // solve then continues from the true residual.
+//
+// CG minimises the H-norm of the error, not the residual norm, which on an
+// ill-conditioned system can rise far above its starting value before it
+// falls.  A run therefore keeps the iterate of smallest recursive residual
+// (xb, with ||r||^2 in scal[S_RRB]): the iteration that finds a new minimum sets
+// scal[S_NEWB] and the direction update that follows copies x into xb, so a
+// run that ends above its best returns the best.
 
 // p = z + beta p  with beta = rz_new / rz
 __device__ __forceinline__ void pcg_p_body(int lb, int nb, int m, double* __restrict__ p,
-                                           const double* __restrict__ z, double* scal) {
+                                           const double* __restrict__ z, const double* __restrict__ x,
+                                           double* __restrict__ xb, double* scal) {
+  if (scal[S_NEWB] != 0.0)
+    for (int i = lb * blockDim.x + threadIdx.x; i < m; i += nb * blockDim.x) xb[i] = x[i];
   if (scal[S_GO] == 0.0) return;   // the loop has stopped: r may be exactly zero
   const double rzn = scal[S_RZN], rz = scal[S_RZ];
   if (!(rzn > 0.0 && isfinite(rzn) && rz > 0.0)) {
@@ -36,8 +47,9 @@ __device__ __forceinline__ void pcg_p_body(int lb, int nb, int m, double* __rest
   const double beta = rzn / rz;
   for (int i = lb * blockDim.x + threadIdx.x; i < m; i += nb * blockDim.x) p[i] = fma(beta, p[i], z[i]);
 }
-__global__ void k_pcg_p(int m, double* __restrict__ p, const double* __restrict__ z, double* scal) {
-  pcg_p_body(blockIdx.x, gridDim.x, m, p, z, scal);
+__global__ void k_pcg_p(int m, double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ x,
+                        double* __restrict__ xb, double* scal) {
+  pcg_p_body(blockIdx.x, gridDim.x, m, p, z, x, xb, scal);
 }
 
 // x += a p;  r -= a q  (a = rz / pq), ||r||^2, iteration count and the loop
@@ -66,6 +78,9 @@ __device__ __forceinline__ bool pcg_xr_body(int lb, int nb, int m, double* __res
     const double it = scal[S_IT] + 1.0;
     scal[S_IT] = it;
     if (!ok) scal[S_BRK] = 1.0;
+    const bool best = tot < scal[S_RRB];
+    if (best) scal[S_RRB] = tot;
+    scal[S_NEWB] = best ? 1.0 : 0.0;
     const bool go = ok && (tot > scal[S_TOL2]) && (it < scal[S_MAXIT]) && isfinite(tot) && scal[S_BRK] == 0.0;
     scal[S_GO] = go ? 1.0 : 0.0;
     *decided = true;
@@ -116,7 +131,7 @@ __global__ void kb_pcg_p(const BDesc* __restrict__ desc, const int* __restrict__
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
   if (!D.active) return;
-  pcg_p_body(blockIdx.x - off[i], off[i + 1] - off[i], D.m, D.pp, D.pz, D.scal);
+  pcg_p_body(blockIdx.x - off[i], off[i + 1] - off[i], D.m, D.pp, D.pz, D.px, D.pxb, D.scal);
 }
 int batch_blocks_vec(int m) { return (int)std::min(cdiv(m, 256), 2048u); }
 void batch_launch_xr(cudaStream_t st, BDesc* desc, const int* off, int N, int nb) {
@@ -136,6 +151,8 @@ __global__ void k_pcg_init(double* scal, double rtol, int maxit) {
   scal[S_MAXIT] = (double)maxit;
   scal[S_BRK] = 0.0;
   scal[S_GO] = 1.0;
+  scal[S_RRB] = scal[S_NR0];   // the start x = 0 is the best so far
+  scal[S_NEWB] = 0.0;
 }
 
 static sdp_status pcg_alloc(sdp_problem* h) {
@@ -146,6 +163,7 @@ static sdp_status pcg_alloc(sdp_problem* h) {
   SDP_TRY(h->allocT(&h->pp, m));
   SDP_TRY(h->allocT(&h->pq, m));
   SDP_TRY(h->allocT(&h->px, m));
+  SDP_TRY(h->allocT(&h->pxb, m));
   SDP_TRY(h->allocT(&h->pbest, m));
   SDP_TRY(h->allocT(&h->pcorr, m));
   SDP_TRY(h->allocT(&h->pcg_part, (size_t)m / 8 + 4096));
@@ -174,7 +192,7 @@ static sdp_status pcg_body(sdp_problem* h, int prec, cudaGraphConditionalHandle 
   // prec != FP64) cost about twice the PCG iterations in measurements
   SDP_TRY(precond_apply_impl(h, h->pr, h->pz, SDP_FP64, scal + S_RZN));
   count_launch();
-  k_pcg_p<<<g, 256, 0, st>>>(m, h->pp, h->pz, scal);
+  k_pcg_p<<<g, 256, 0, st>>>(m, h->pp, h->pz, h->px, h->pxb, scal);
   return SDP_OK;
 }
 
@@ -248,6 +266,7 @@ static sdp_status pcg_start(sdp_problem* h, const double* rhs, double rtol, int 
   else SDP_TRY(ensure_lowprec_W(h, prec));
   SDP_CK(h, cudaMemcpyAsync(h->pr, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   SDP_CK(h, cudaMemsetAsync(h->px, 0, m * sizeof(double), st));
+  SDP_CK(h, cudaMemsetAsync(h->pxb, 0, m * sizeof(double), st));
   dot(st, m, h->pr, h->pr, scal + S_NR0, h->part);
   *nr0sq = read_scalar(h, scal + S_NR0);
   if (!std::isfinite(*nr0sq)) {
@@ -278,22 +297,24 @@ static sdp_status pcg_run(sdp_problem* h, int prec, bool graph) {
   return SDP_OK;
 }
 
-// End of a run: x = the iterate, iteration count, recursive relative residual.
+// End of a run: x = the iterate of smallest recursive residual (the last one
+// when its iteration set a new minimum, else the copy in pxb), iteration
+// count, that iterate's recursive relative residual.
 static sdp_status pcg_finish(sdp_problem* h, double* x, double nr0sq, bool graph, int* iters, double* rel,
                              bool* brk) {
   cudaStream_t st = h->stream;
   const int m = h->m;
-  double v[11];
-  SDP_CK(h, cudaMemcpyAsync(v, h->scal, 11 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  SDP_CK(h, cudaMemcpyAsync(x, h->px, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  double v[13];
+  SDP_CK(h, cudaMemcpyAsync(v, h->scal, 13 * sizeof(double), cudaMemcpyDeviceToHost, st));
   SDP_CK(h, cudaStreamSynchronize(st));
+  SDP_CK(h, cudaMemcpyAsync(x, v[S_NEWB] != 0.0 ? h->px : h->pxb, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const int its = (int)v[S_IT];
   if (graph) g_launches.fetch_add((int64_t)its * h->pcg_body_launches);
-  const double rr = v[S_RR];
+  const double rr = v[S_RRB];
   *iters = its;
   *rel = std::sqrt(rr / nr0sq);
   if (brk) *brk = (v[S_BRK] != 0.0);
-  if (!std::isfinite(rr)) {
+  if (!std::isfinite(rr) || !std::isfinite(v[S_RR])) {
     h->last_error = "pcg: non-finite residual";
     return SDP_ERR_NUMERIC;
   }
@@ -353,9 +374,12 @@ sdp_status pcg_sweep_begin(sdp_problem* h, PcgSweeps* S, bool graph, bool* run) 
   }
   // iterations of one sweep: a restart discards the Krylov space, so a sweep must
   // be long enough to resolve the k(k+1)/2 outlying eigenvalues that H - Hhat
-  // (rank <= k(k+1)/2, Section V) leaves, on top of the bulk
+  // (rank <= k(k+1)/2, Section V) leaves, on top of the bulk; each later sweep gets twice the budget of the
+  // one before (up to 8x), since the residual a sweep leaves is concentrated
+  // on the slowest part of the spectrum
   const int kk = h->pc_hat ? h->kpc : 0;
-  S->budget = std::max(1, std::min(S->maxit - S->total, std::max(500, kk * (kk + 1) / 2 + 500)));
+  const int base = std::max(500, kk * (kk + 1) / 2 + 500);
+  S->budget = std::max(1, std::min(S->maxit - S->total, base << std::min(S->sweep, 3)));
   S->graph = graph;
   SDP_TRY(pcg_start(h, h->pbest, S->prec == SDP_FP64 ? S->inner_fp64 : S->inner_lp, S->budget, S->prec, graph,
                     &S->nr0sq));
@@ -387,6 +411,10 @@ sdp_status pcg_sweep_end(sdp_problem* h, PcgSweeps* S) {
   const double tr_prev = S->tr;
   if (it > 0) axpby(st, m, 1.0, S->y, 1.0, h->pcorr, S->y);
   SDP_TRY(true_residual(h, S->r, S->y, h->pbest, &S->tr));
+  if (h->prm.verbose >= 2)
+    std::fprintf(stderr, "  pcg sweep %d %s: %d its (budget %d), recursive %.2e, breakdown %d, true %.2e -> %.2e\n",
+                 S->sweep - 1, S->prec == SDP_FP64 ? "fp64" : (S->prec == SDP_FP32 ? "fp32" : "bf16"), it,
+                 S->budget, rr, brk ? 1 : 0, tr_prev, S->tr);
   if (!(S->tr < tr_prev)) {
     // the sweep did not reduce the FP64 residual: drop its correction; a
     // reduced-precision inner solve hands over to FP64, an FP64 one stops
