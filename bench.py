@@ -397,6 +397,12 @@ def instrumented_step(args, insts, prec, kk, stream):
     return rep, wall
 
 
+# All-active batched FP64 matvec of the 16 bench instances: algorithmic flops
+# (2 nnz(V) n + 2 nent n summed) and the DRAM bytes ncu measured for its SpMM and SDDMM.
+MATVEC_B_ALL_ACTIVE_FLOPS = 0.558157e9 + 0.279079e9
+MATVEC_B_NCU_BYTES = 36.78e6 + 36.97e6
+
+
 def roofline_of(cls, rep, wall):
     """Roofline object of kernel class `cls` from the instrumented step's records."""
     kt = rep.get(cls)
@@ -518,6 +524,16 @@ def run(args):
                     rooflines[f"{prec}:{cls}"] = r
         want = args.timed_kernel if args.timed_kernel != "auto" else "matvec_b"
         roof = rooflines.get(f"fp64:{want}") or next(iter(rooflines.values()), None)
+        if roof is not None and roof["kernel"] == "matvec_b" and args.workload == "batched" and args.batch == 16:
+            # DRAM bytes of one all-active batched matvec of these 16 instances (ncu
+            # captures: SpMM 36.8 MB, SDDMM 37.0 MB; the V assembly is not captured),
+            # scaled to the average launch by the flops it did
+            t_all, f_all = MATVEC_B_NCU_BYTES, MATVEC_B_ALL_ACTIVE_FLOPS
+            per_launch_flops = roof["achieved"] * 1e12 * roof["avg_us"] * 1e-6
+            roof["traffic"] = t_all * per_launch_flops / f_all
+            roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of kb_spmm + kb_sddmm with all "
+                                      "16 problems active (profiles/ncu_batched_spmm_16mc.md, "
+                                      "profiles/ncu_batched_sddmm_16mc.md), scaled by the average launch's flops")
 
     # ---- end to end through the public API: host triplets in, solution out (headline arm)
     e2e = None

@@ -208,18 +208,18 @@ static sdp_status batch_prepare(sdp_batch* b) {
   b->host_loop = false;
   batch_offsets(b);
   if (N > b->ndesc || (int)b->off.size() > b->noff) {
-    cudaFree(b->ddesc);
-    cudaFree(b->doff);
-    cudaFree(b->dflag);
+    pool_free(b->ddesc, b->stream);
+    pool_free(b->doff, b->stream);
+    pool_free(b->dflag, b->stream);
     b->ddesc = nullptr;
     b->doff = nullptr;
     b->dflag = nullptr;
     b->ndesc = b->noff = 0;
     const int cap = std::max(N, 2 * b->ndesc);
     const size_t offcap = (size_t)BK_COUNT * (cap + 1);
-    if (cudaMalloc(&b->ddesc, sizeof(BDesc) * cap) != cudaSuccess ||
-        cudaMalloc(&b->doff, sizeof(int) * offcap) != cudaSuccess ||
-        cudaMalloc(&b->dflag, sizeof(int) * (cap + 1)) != cudaSuccess) {
+    if (pool_malloc((void**)&b->ddesc, sizeof(BDesc) * cap, b->stream) != cudaSuccess ||
+        pool_malloc((void**)&b->doff, sizeof(int) * offcap, b->stream) != cudaSuccess ||
+        pool_malloc((void**)&b->dflag, sizeof(int) * (cap + 1), b->stream) != cudaSuccess) {
       cudaGetLastError();
       b->last_error = "sdp_batch: device allocation failed";
       return SDP_ERR_OOM;
@@ -292,7 +292,7 @@ static sdp_status batch_autotune(sdp_batch* b, const std::vector<BDesc>& hd) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SDP_ERR_CUDA;
   std::vector<int> off(N + 1, 0);
   int* doff = nullptr;
-  if (cudaMalloc(&doff, sizeof(int) * (N + 1)) != cudaSuccess) {
+  if (pool_malloc((void**)&doff, sizeof(int) * (N + 1), b->stream) != cudaSuccess) {
     cudaGetLastError();
     return SDP_ERR_OOM;
   }
@@ -327,7 +327,7 @@ static sdp_status batch_autotune(sdp_batch* b, const std::vector<BDesc>& hd) {
   }
   cudaMemcpyAsync(b->ddesc, hd.data(), sizeof(BDesc) * N, cudaMemcpyHostToDevice, b->stream);
   cudaStreamSynchronize(b->stream);
-  cudaFree(doff);
+  pool_free(doff, b->stream);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (cudaGetLastError() != cudaSuccess) {
@@ -804,9 +804,9 @@ extern "C" void sdp_batch_destroy(sdp_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->capture) cudaStreamDestroy(b->capture);
-  if (b->ddesc) cudaFree(b->ddesc);
-  if (b->doff) cudaFree(b->doff);
-  if (b->dflag) cudaFree(b->dflag);
+  pool_free(b->ddesc, b->stream);
+  pool_free(b->doff, b->stream);
+  pool_free(b->dflag, b->stream);
   for (sdp_batch* c : b->child) sdp_batch_destroy(c);
   for (cudaStream_t s : b->child_streams) cudaStreamDestroy(s);
   delete b;

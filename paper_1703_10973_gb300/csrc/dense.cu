@@ -128,10 +128,54 @@ double gemm_useful_fma(int M, int N, int K, int flags, int tile) {
   return f;
 }
 
+// Thin products C = alpha A op(B) + beta C with at most THIN_N columns (A not
+// transposed): one warp per row of C, lanes over K, one accumulator per column,
+// so a probe-vector check or a product with k eigenvectors costs about M K N
+// FMAs instead of a 32 x 32 tile per 32 rows whose columns are mostly padding.
+constexpr int THIN_N = 8;
+template <bool TB>
+__global__ void __launch_bounds__(256) k_gemm_thin(int M, int N, int K, double alpha, const double* __restrict__ A,
+                                                   int lda, const double* __restrict__ B, int ldb, double beta,
+                                                   double* __restrict__ C, int ldc) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  if (r >= M) return;
+  const double* a = A + (size_t)r * lda;
+  double acc[THIN_N];
+#pragma unroll
+  for (int j = 0; j < THIN_N; ++j) acc[j] = 0.0;
+  for (int k = lane; k < K; k += 32) {
+    const double x = a[k];
+#pragma unroll
+    for (int j = 0; j < THIN_N; ++j)
+      if (j < N) acc[j] = fma(x, TB ? B[(size_t)j * ldb + k] : B[(size_t)k * ldb + j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < THIN_N; ++j) {
+    double v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == j && j < N) {
+      double c = alpha * v;
+      if (beta != 0.0) c = fma(beta, C[(size_t)r * ldc + j], c);
+      C[(size_t)r * ldc + j] = c;
+    }
+  }
+}
+
 void gemm(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
           int lda, const double* B, int ldb, double beta, double* C, int ldc, int flags,
           int batch, long long sA, long long sB, long long sC) {
   if (M <= 0 || N <= 0) return;
+  if (!tA && N <= THIN_N && K > 0 && flags == 0 && batch == 1) {
+    const bool timed = ktimer_on("gemm_f64");
+    if (timed) ktimer_begin(st, "gemm_f64");
+    count_launch();
+    const unsigned grid = cdiv((size_t)M * 32, 256);
+    if (tB) k_gemm_thin<true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else k_gemm_thin<false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (timed) ktimer_end(st, "gemm_f64", 2.0 * M * N * (double)K, 8.0 * ((double)M * K + (double)K * N + 2.0 * M * N));
+    return;
+  }
   if (K <= 0) {  // C = beta C
     if (beta == 0.0) {
       for (int b = 0; b < batch; ++b) copy2d(st, M, N, nullptr, 0, C + b * sC, ldc);

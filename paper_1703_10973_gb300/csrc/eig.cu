@@ -764,35 +764,14 @@ static int sytrd_blocks(int n, size_t smem) {
 // once the O(n^3) work needs the whole GPU).
 constexpr int SY_CLUSTER_MAX_N = 1024;
 
-// Order of preference: full rows in cluster shared memory (n <= 656; two
-// barriers per column, the fastest while it fits), the one-triangle form
-// (n <= 880; a third barrier per column but a third less FP64 work), the
-// L2-streaming cluster form, the cooperative grid form.
+// Order of preference: the one-triangle form in cluster shared memory
+// (n <= 880); the full-row form (n <= 656, where the device cannot run the
+// first); the L2-streaming cluster form; the cooperative grid form.  Alone, the
+// full-row form is as fast at n ~ 565 and faster for small n (two barriers per
+// column instead of three), but in a batch of concurrent problems the
+// one-triangle form's half-size shared-memory footprint leaves room on its 16
+// SMs for the other problems' kernels, which measured faster end to end.
 static sdp_status sytrd(cudaStream_t st, int n, double* A, EigWork* w) {
-  if (n >= 3 && n <= SY_CLUSTER_MAX_N) {
-    const int cs = sytrd_smem_cluster(n);
-    if (cs > 0) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(cs);
-      cfg.blockDim = dim3(SY_THREADS);
-      cfg.dynamicSmemBytes = sytrd_smem_bytes(n, cs);
-      cfg.stream = st;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = cs;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int lda = n;
-      count_launch();
-      ktimer_begin(st, "sytrd");
-      cudaError_t err = cudaLaunchKernelEx(&cfg, k_sytrd_cluster_smem, n, A, lda, w->d, w->e, w->tauh);
-      ktimer_end(st, "sytrd", 4.0 / 3.0 * n * (double)n * n, 16.0 * n * (double)n);
-      if (err == cudaSuccess) return SDP_OK;
-      cudaGetLastError();
-    }
-  }
   if (n >= 3 && n <= SY_CLUSTER_MAX_N) {
     const int cs = sytrd_lower_cluster(n);
     if (cs > 0) {
@@ -812,6 +791,30 @@ static sdp_status sytrd(cudaStream_t st, int n, double* A, EigWork* w) {
       count_launch();
       ktimer_begin(st, "sytrd");
       cudaError_t err = cudaLaunchKernelEx(&cfg, k_sytrd_cluster_lower, n, A, lda, w->d, w->e, w->tauh);
+      ktimer_end(st, "sytrd", 4.0 / 3.0 * n * (double)n * n, 16.0 * n * (double)n);
+      if (err == cudaSuccess) return SDP_OK;
+      cudaGetLastError();
+    }
+  }
+  if (n >= 3 && n <= SY_CLUSTER_MAX_N) {
+    const int cs = sytrd_smem_cluster(n);
+    if (cs > 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(SY_THREADS);
+      cfg.dynamicSmemBytes = sytrd_smem_bytes(n, cs);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int lda = n;
+      count_launch();
+      ktimer_begin(st, "sytrd");
+      cudaError_t err = cudaLaunchKernelEx(&cfg, k_sytrd_cluster_smem, n, A, lda, w->d, w->e, w->tauh);
       ktimer_end(st, "sytrd", 4.0 / 3.0 * n * (double)n * n, 16.0 * n * (double)n);
       if (err == cudaSuccess) return SDP_OK;
       cudaGetLastError();
@@ -1293,6 +1296,13 @@ void eig_work_carve(EigWork* w, void* base, int n, bool full) {
   w->info = ip; ip += 4;
   w->blocks = ip; ip += 3 * n + 4;
   w->src = ip; ip += n;
+}
+
+// The barrier counters, the timeout flag and the info word start at zero: the
+// flag is read after every eigensolver call, also when no grid-barrier kernel
+// ran (freshly allocated device memory holds whatever was there before).
+void eig_work_clear(cudaStream_t st, EigWork* w) {
+  cudaMemsetAsync(w->bar, 0, 12 * sizeof(int), st);   // bar[4], flag[4], info[4]
 }
 
 int eig_flag(cudaStream_t st, EigWork* w) {

@@ -294,6 +294,7 @@ sdp_status lanczos_min(cudaStream_t st, int n, const double* M, const double* A2
 sdp_status eig_extremes(cudaStream_t st, int n, double* A, int k, double* lmin_dev, double* wtop,
                         double* Etop, EigWork* ws);
 // Reads the barrier-timeout flag; nonzero -> SDP_ERR_TIMEOUT.
+void eig_work_clear(cudaStream_t st, EigWork* w);
 int eig_flag(cudaStream_t st, EigWork* ws);
 
 }  // namespace sdpgb
@@ -460,6 +461,12 @@ struct sdp_problem {
 };
 
 namespace sdpgb {
+// setup.cu: device memory of problems and batches, from one stream-ordered
+// pool per device that keeps what is freed.  pool_malloc returns memory that
+// every stream may use (it waits for the allocation on st); pool_free orders
+// the free on st, so the caller must have finished every use on other streams.
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st);
+void pool_free(void* p, cudaStream_t st);
 // matvec.cu
 // Optional epilogue (PCG): *dot_out = v . Hv, after *pro_dst = *pro_src.
 sdp_status matvec_impl(sdp_problem* h, const double* v, double* Hv, int prec, double* dot_out = nullptr,

@@ -68,20 +68,28 @@ void assemble_V(sdp_problem* h, const double* v, const double* scale, double* Vv
 // K1: T = W V, R rows of W per CTA staged in shared memory
 // ---------------------------------------------------------------------------
 constexpr int SPMM_UNROLL = 8;
-// Thread t of the CTA handles row perm[t] of V (rows by decreasing length, so
-// that the lanes of a warp walk rows of about the same length).
+// FP64: a CTA (SPMM_COLS threads) takes R rows of W and one chunk of SPMM_COLS
+// rows of V: block blk = (row block) * chunks + chunk, so a problem has
+// ceil(n / R) * ceil(n / SPMM_COLS) CTAs -- enough to fill the GPU when only a
+// few problems of a batch are still iterating.  Thread t of chunk c handles
+// row perm[c * SPMM_COLS + t] of V (rows by decreasing length, so that the
+// lanes of a warp walk rows of about the same length).  Every entry of T is
+// one thread's sum in the row's CSR order, whatever R and the chunking.
+constexpr int SPMM_COLS = 256;
+__host__ __device__ __forceinline__ int spmm_chunks(int n) { return (n + SPMM_COLS - 1) / SPMM_COLS; }
 template <int R>
 __device__ __forceinline__ void spmm_f64_body(int blk, int n, const int* __restrict__ rowptr,
                                               const int* __restrict__ perm, const int* __restrict__ colidx,
                                               const double* __restrict__ Vval, const double* __restrict__ W,
                                               double* __restrict__ T, double* wsh) {
-  const int r0 = blk * R;
-  for (int t = threadIdx.x; t < R * n; t += blockDim.x) {
-    const int rr = t / n, c = t % n;
-    wsh[t] = (r0 + rr < n) ? W[(size_t)(r0 + rr) * n + c] : 0.0;
+  const int nc = spmm_chunks(n);
+  const int r0 = (blk / nc) * R, t = (blk % nc) * SPMM_COLS + (int)threadIdx.x;
+  for (int e = threadIdx.x; e < R * n; e += blockDim.x) {
+    const int rr = e / n, c = e % n;
+    wsh[e] = (r0 + rr < n) ? W[(size_t)(r0 + rr) * n + c] : 0.0;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+  if (t < n) {
     const int l = perm[t];
     double acc[R];
 #pragma unroll
@@ -129,10 +137,12 @@ __device__ __forceinline__ void spmm_lp_body(int blk, int n, const int* __restri
                                              const int* __restrict__ perm, const int* __restrict__ colidx,
                                              const double* __restrict__ Vval, const TW* __restrict__ W,
                                              float* __restrict__ T, float* fsh) {
+  // no column chunks here: in FP32 the FMAs are cheap next to staging R rows
+  // of W, so every CTA walks all rows of V for its R rows of W
   const int r0 = blk * R;
-  for (int t = threadIdx.x; t < R * n; t += blockDim.x) {
-    const int rr = t / n, c = t % n;
-    fsh[t] = (r0 + rr < n) ? tof<TW>(W[(size_t)(r0 + rr) * n + c]) : 0.f;
+  for (int e = threadIdx.x; e < R * n; e += blockDim.x) {
+    const int rr = e / n, c = e % n;
+    fsh[e] = (r0 + rr < n) ? tof<TW>(W[(size_t)(r0 + rr) * n + c]) : 0.f;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(256) kb_sddmm(const BDesc* __restrict__ desc, 
                  D.pp, D.part, D.ticket, D.scal + S_PQ, D.scal + S_RZ, D.scal + S_RZN);
 }
 int batch_blocks_assemble(int nnzV) { return (int)cdiv(nnzV, 256); }
-int batch_blocks_spmm(int n, int R) { return (int)cdiv(n, R); }
+int batch_blocks_spmm(int n, int R) { return (int)cdiv(n, R) * spmm_chunks(n); }
 int batch_blocks_sddmm(int m) { return (int)cdiv(m, SDDMM_PER_BLOCK); }
 // nb_sddmm = 0 leaves the gather out (a mixed batch launches it with the
 // reduced-precision one, batch_launch_sddmm_mixed)
@@ -476,9 +486,12 @@ __global__ void k_split_Ws(int n, int k, const double* __restrict__ W, const dou
   Ws[t] = v;
 }
 
-// Batched FP32 forms: the same bodies over the same per-problem partitions as
-// the single-problem launches (problems in an FP64 sweep return at once).
-constexpr int BATCH_SPMM_LP_R = 8;
+// Batched FP32 forms: the same bodies as the single-problem launches (problems
+// in an FP64 sweep return at once).  Each entry of T is one thread's sum in the
+// row's CSR order whatever the rows per CTA, so the batched SpMM takes 16 rows
+// of W per CTA (a quarter of the CSR re-reads of 4) and still matches a problem
+// alone bit for bit.
+constexpr int BATCH_SPMM_LP_R = 16;
 __global__ void __launch_bounds__(256) kb_split_G(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
@@ -607,8 +620,9 @@ sdp_status ensure_lowprec_W(sdp_problem* h, int prec) {
 }
 
 // Rows of W per CTA of the SpMM: as many as shared memory allows (each CTA
-// streams the whole CSR of V once), but few enough that the grid still covers
-// the SMs -- the FP64 form is bound by the SMs' DFMA rate, not by bandwidth.
+// streams its chunk of the CSR of V once), but few enough that the grid still
+// covers the SMs -- the FP64 form is bound by the SMs' DFMA rate, not by
+// bandwidth.
 static int rows_per_cta(int n, size_t elem) {
   static int sms = 0;
   if (!sms) {
@@ -628,7 +642,7 @@ static void launch_spmm_f64(sdp_problem* h, const double* Vval) {
   const size_t smem = (size_t)R * h->n * sizeof(double);
   allow_max_smem((const void*)k_spmm_wv_f64<R>);
   count_launch();
-  k_spmm_wv_f64<R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->rowperm, h->colidx, Vval, h->W,
+  k_spmm_wv_f64<R><<<cdiv(h->n, R) * spmm_chunks(h->n), SPMM_COLS, smem, h->stream>>>(h->n, h->rowptr, h->rowperm, h->colidx, Vval, h->W,
                                                               h->T);
 }
 template <typename TW, int R>
@@ -636,7 +650,7 @@ static void launch_spmm_lp(sdp_problem* h, const double* Vval, const TW* W) {
   const size_t smem = (size_t)R * h->n * sizeof(float);
   allow_max_smem((const void*)k_spmm_wv_lp<TW, R>);
   count_launch();
-  k_spmm_wv_lp<TW, R><<<cdiv(h->n, R), 256, smem, h->stream>>>(h->n, h->rowptr, h->rowperm, h->colidx, Vval, W,
+  k_spmm_wv_lp<TW, R><<<cdiv(h->n, R), SPMM_COLS, smem, h->stream>>>(h->n, h->rowptr, h->rowperm, h->colidx, Vval, W,
                                                                  h->T32);
 }
 

@@ -450,6 +450,7 @@ static sdp_status precond_alloc(sdp_problem* h) {
   if (!h->eig_base) {
     SDP_TRY(h->alloc(&h->eig_base, eig_work_bytes(n, true)));
     eig_work_carve(&h->eig, h->eig_base, n, true);
+    eig_work_clear(h->stream, &h->eig);
     h->eig.spin_cycles = h->prm.wait_cycles;
   }
   return SDP_OK;

@@ -19,17 +19,65 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <unordered_map>
 
 using namespace sdpgb;
 
+namespace sdpgb {
+
+// One pool per device that keeps up to 32 GiB of freed memory: what a finished
+// problem frees stays with the pool and the next request reuses it without a
+// new mapping, and a free is ordered on the freeing stream -- cudaFree waits
+// for all work on the device, so one serving request's clean-up would stall
+// every other request's kernels.
+static cudaMemPool_t device_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = 32ull << 30;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  cudaMemPool_t pool = device_pool();
+  if (!pool) return cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+void pool_free(void* p, cudaStream_t st) {
+  if (!p) return;
+  if (device_pool()) cudaFreeAsync(p, st);
+  else cudaFree(p);
+}
+
+}  // namespace sdpgb
+
 sdp_status sdp_problem::alloc(void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = pool_malloc(p, bytes, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    last_error = std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e);
+    last_error = std::string("device allocation (") + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e);
     *p = nullptr;
     return SDP_ERR_OOM;
   }
@@ -43,7 +91,7 @@ void sdp_problem::release(void* p) {
   if (!p) return;
   for (size_t i = 0; i < owned.size(); ++i) {
     if (owned[i] != p) continue;
-    cudaFree(p);
+    pool_free(p, stream);
     device_bytes -= (int64_t)owned_bytes[i];
     owned[i] = owned.back();
     owned.pop_back();
@@ -105,7 +153,7 @@ extern "C" void sdp_destroy(sdp_problem* h) {
   if (h->pcg_exec) cudaGraphExecDestroy(h->pcg_exec);
   if (h->pcg_graph) cudaGraphDestroy(h->pcg_graph);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
-  for (void* p : h->owned) cudaFree(p);
+  for (void* p : h->owned) pool_free(p, h->stream);
   delete h;
 }
 
