@@ -16,6 +16,11 @@
  *  - "_dev" pointers are device pointers owned by the caller; they must be
  *    valid on the handle's stream and must not alias each other.
  *  - The handle owns all other device memory and frees it in sdp_destroy.
+ *    Handles and batches allocate from one stream-ordered memory pool per device
+ *    (allocation waits for the handle's stream; a free is ordered on it), which
+ *    keeps up to 32 GiB of freed memory for the next handle instead of returning
+ *    it to the driver.  Destroy a handle only when no batch still has work in
+ *    flight on it (sdp_batch_remove it first, or let the batch call return).
  *  - Every call returns an sdp_status; nothing is thrown across the ABI.  After
  *    any status the handle may still be destroyed; sdp_last_error() gives text.
  *  - One handle is used by one host thread at a time.  All work is issued on the

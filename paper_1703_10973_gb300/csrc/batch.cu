@@ -93,6 +93,7 @@ static void batch_offsets(sdp_batch* b) {
   b->off.assign((size_t)BK_COUNT * (N + 1), 0);
   b->nmax = 0;
   b->any_lp = false;
+  for (int i = 0; i < N; ++i) b->nmax = std::max(b->nmax, b->hs[i]->n);
   for (int i = 0; i < N; ++i) {
     sdp_problem* h = b->hs[i];
     const int k = std::min(h->kcap, h->n - 1), Rk = h->hs_nr * k;   // grids for the largest rank
@@ -102,10 +103,9 @@ static void batch_offsets(sdp_batch* b) {
                                batch_blocks_warp_rows(Rk),     batch_blocks_out_bwd(Rk, h->hs_np),
                                0,
                                batch_blocks_split_G(h->n),     batch_blocks_split_R(h->n),
-                               batch_blocks_split_Q(h->n, k),  batch_blocks_spmm_lp(h->n)};
+                               batch_blocks_split_Q(h->n, k),  batch_blocks_spmm_lp(h->n, b->nmax)};
     for (int kd = 0; kd < BK_COUNT; ++kd)
       b->off[(size_t)kd * (N + 1) + i + 1] = b->off[(size_t)kd * (N + 1) + i] + cnt[kd];
-    b->nmax = std::max(b->nmax, h->n);
     if (h->prm.prec == SDP_FP32 || h->prm.prec == SDP_BF16) b->any_lp = true;
   }
   for (int kd = 0; kd < BK_COUNT; ++kd) b->total[kd] = b->off[(size_t)kd * (N + 1) + N];

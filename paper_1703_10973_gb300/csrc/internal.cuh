@@ -504,7 +504,7 @@ int batch_blocks_out_bwd(int Rk, int np);
 int batch_blocks_split_G(int n);
 int batch_blocks_split_R(int n);
 int batch_blocks_split_Q(int n, int k);
-int batch_blocks_spmm_lp(int n);
+int batch_blocks_spmm_lp(int n, int nmax);   // rows per CTA chosen from the batch's largest order
 void batch_launch_matvec_lp(cudaStream_t st, const BDesc* desc, const int* off_g, const int* off_r,
                             const int* off_q, const int* off_spmm, const int* off_sddmm, int N, int nb_g, int nb_r,
                             int nb_q, int nb_spmm, int nb_sddmm, int nmax, bool with_sddmm = true);

@@ -25,16 +25,23 @@ enum { R_RP = 8, R_RD, R_CX, R_BY, R_XS, R_XDS, R_DXS, R_DXDS, R_LMIN, R_LZ /* 5
 // Step lengths use Lanczos from this order on (below it the full eigensolver is cheap).
 constexpr int LZ_MIN_N = 64;
 
+// Probe vectors of the NT-scaling check (declared here: ipm_alloc sizes the
+// scratch that holds them).
+constexpr int NT_PROBES = 4;
+
 sdp_status ipm_alloc(sdp_problem* h) {
   if (h->L) return SDP_OK;
   const int n = h->n, m = h->m;
   const size_t nn = (size_t)n * n;
+  // M1 also holds the check's four n x NT_PROBES products and Gt its probe
+  // vectors, which exceed n^2 for n < 16
+  const size_t nm1 = std::max(nn, (size_t)4 * NT_PROBES * n), ngt = std::max(nn, (size_t)NT_PROBES * n);
   SDP_TRY(h->allocT(&h->L, nn));
   SDP_TRY(h->allocT(&h->Rs, nn));
-  if (!h->M1) SDP_TRY(h->allocT(&h->M1, nn));
+  if (!h->M1) SDP_TRY(h->allocT(&h->M1, nm1));
   SDP_TRY(h->allocT(&h->M2, nn));
   SDP_TRY(h->allocT(&h->M3, nn));
-  SDP_TRY(h->allocT(&h->Gt, nn));
+  SDP_TRY(h->allocT(&h->Gt, ngt));
   SDP_TRY(h->allocT(&h->Sinv, nn));
   SDP_TRY(h->allocT(&h->Rd, nn));
   SDP_TRY(h->allocT(&h->Rc, nn));
@@ -272,7 +279,6 @@ static sdp_status db_inv_sqrt(sdp_problem* h, double* M, double* Zout) {
 }
 
 // Probe vectors for the NT check: entries from a splitmix64 hash of the index, in [-1, 1].
-constexpr int NT_PROBES = 4;
 __global__ void k_probe_fill(int count, double* Z) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;

@@ -132,19 +132,45 @@ __global__ void __launch_bounds__(256) k_spmm_wv_f64(int n, const int* __restric
   spmm_f64_body<R>(blockIdx.x, n, rowptr, perm, colidx, Vval, W, T, wsh);
 }
 
+// Floats per staged column of the reduced-precision SpMM (see spmm_lp_body).
+__host__ __device__ constexpr int spmm_lp_stride(int R) { return (R % 4 == 0) ? R + 4 : R; }
 template <typename TW, int R>
 __device__ __forceinline__ void spmm_lp_body(int blk, int n, const int* __restrict__ rowptr,
                                              const int* __restrict__ perm, const int* __restrict__ colidx,
                                              const double* __restrict__ Vval, const TW* __restrict__ W,
                                              float* __restrict__ T, float* fsh) {
   // no column chunks here: in FP32 the FMAs are cheap next to staging R rows
-  // of W, so every CTA walks all rows of V for its R rows of W
+  // of W, so every CTA walks all rows of V for its R rows of W.  The R rows are
+  // staged transposed with a row stride of RS = spmm_lp_stride(R) floats
+  // (fsh[c * RS + rr]): the R values one stored entry of V needs are
+  // contiguous (R / 4 vector loads), and the pad of 4 makes the stride an odd
+  // number of 16-byte groups so that the random columns of a warp's lanes do
+  // not all fall on the same banks (without it the kernel ran 1.4x slower;
+  // with it, as fast as R scattered scalar loads: the CSR loads bound it).
+  // Each acc[rr] sums in the same order as with any other layout.
+  constexpr int RS = spmm_lp_stride(R);
   const int r0 = blk * R;
   for (int e = threadIdx.x; e < R * n; e += blockDim.x) {
     const int rr = e / n, c = e % n;
-    fsh[e] = (r0 + rr < n) ? tof<TW>(W[(size_t)(r0 + rr) * n + c]) : 0.f;
+    fsh[c * RS + rr] = (r0 + rr < n) ? tof<TW>(W[(size_t)(r0 + rr) * n + c]) : 0.f;
   }
   __syncthreads();
+  auto fma_row = [&](float val, int col, float* acc) {
+    const float* w = fsh + col * RS;
+    if constexpr (R % 4 == 0) {
+#pragma unroll
+      for (int q = 0; q < R / 4; ++q) {
+        const float4 w4 = reinterpret_cast<const float4*>(w)[q];
+        acc[4 * q + 0] = fmaf(val, w4.x, acc[4 * q + 0]);
+        acc[4 * q + 1] = fmaf(val, w4.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(val, w4.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(val, w4.w, acc[4 * q + 3]);
+      }
+    } else {
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc[rr] = fmaf(val, w[rr], acc[rr]);
+    }
+  };
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     const int l = perm[t];
     float acc[R];
@@ -161,16 +187,9 @@ __device__ __forceinline__ void spmm_lp_body(int blk, int n, const int* __restri
         val[u] = (float)Vval[s + u];
       }
 #pragma unroll
-      for (int u = 0; u < SPMM_UNROLL; ++u)
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) acc[rr] = fmaf(val[u], fsh[rr * n + col[u]], acc[rr]);
+      for (int u = 0; u < SPMM_UNROLL; ++u) fma_row(val[u], col[u], acc);
     }
-    for (; s < s1; ++s) {
-      const float val = (float)Vval[s];
-      const int col = colidx[s];
-#pragma unroll
-      for (int rr = 0; rr < R; ++rr) acc[rr] = fmaf(val, fsh[rr * n + col], acc[rr]);
-    }
+    for (; s < s1; ++s) fma_row((float)Vval[s], colidx[s], acc);
 #pragma unroll
     for (int rr = 0; rr < R; ++rr)
       if (r0 + rr < n) T[(size_t)(r0 + rr) * n + l] = acc[rr];
@@ -488,10 +507,15 @@ __global__ void k_split_Ws(int n, int k, const double* __restrict__ W, const dou
 
 // Batched FP32 forms: the same bodies as the single-problem launches (problems
 // in an FP64 sweep return at once).  Each entry of T is one thread's sum in the
-// row's CSR order whatever the rows per CTA, so the batched SpMM takes 16 rows
-// of W per CTA (a quarter of the CSR re-reads of 4) and still matches a problem
-// alone bit for bit.
-constexpr int BATCH_SPMM_LP_R = 16;
+// row's CSR order whatever the rows per CTA, so the batched SpMM may take more
+// rows of W per CTA than a problem alone and still match it bit for bit: 16 (a
+// quarter of the CSR re-reads of 4) while the staged rows of the batch's
+// largest problem fit in 200 KB of shared memory, fewer for larger orders.
+int batch_spmm_lp_rows(int nmax) {
+  for (int r = 16; r > 1; r /= 2)
+    if ((size_t)spmm_lp_stride(r) * nmax * sizeof(float) <= 200 * 1024) return r;
+  return 1;
+}
 __global__ void __launch_bounds__(256) kb_split_G(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
@@ -514,16 +538,17 @@ __global__ void __launch_bounds__(256) kb_split_R_Q(const BDesc* __restrict__ de
   if (!D.active || !D.lp || D.ks == 0) return;
   split_R_Q_body(blockIdx.x - off[i], D.n, D.ks, D.mvPart, D.wtop, D.mvG, D.Etop, D.mvR, D.mvQ);
 }
+template <int R>
 __global__ void __launch_bounds__(256) kb_spmm_lp(const BDesc* __restrict__ desc, const int* __restrict__ off, int N) {
   extern __shared__ float fsh[];
   const int i = batch_find(off, N, blockIdx.x);
   const BDesc& D = desc[i];
   if (!D.active || !D.lp) return;
   if (D.bf)
-    spmm_lp_body<__nv_bfloat16, BATCH_SPMM_LP_R>(blockIdx.x - off[i], D.n, D.rowptr, D.rowperm, D.colidx, D.Vval,
+    spmm_lp_body<__nv_bfloat16, R>(blockIdx.x - off[i], D.n, D.rowptr, D.rowperm, D.colidx, D.Vval,
                                                  D.W16, D.T32, fsh);
   else
-    spmm_lp_body<float, BATCH_SPMM_LP_R>(blockIdx.x - off[i], D.n, D.rowptr, D.rowperm, D.colidx, D.Vval, D.W32,
+    spmm_lp_body<float, R>(blockIdx.x - off[i], D.n, D.rowptr, D.rowperm, D.colidx, D.Vval, D.W32,
                                          D.T32, fsh);
 }
 __global__ void __launch_bounds__(256) kb_sddmm_lp(const BDesc* __restrict__ desc, const int* __restrict__ off,
@@ -543,7 +568,7 @@ __global__ void __launch_bounds__(256) kb_sddmm_lp(const BDesc* __restrict__ des
 int batch_blocks_split_G(int n) { return (int)cdiv((size_t)n * 32, 256); }
 int batch_blocks_split_R(int n) { return (int)cdiv(n, 128) * SPLIT_CHUNKS; }
 int batch_blocks_split_Q(int n, int k) { return (int)cdiv(std::max((size_t)n * k, (size_t)k * k * 32), 256); }
-int batch_blocks_spmm_lp(int n) { return (int)cdiv(n, BATCH_SPMM_LP_R); }
+int batch_blocks_spmm_lp(int n, int nmax) { return (int)cdiv(n, batch_spmm_lp_rows(nmax)); }
 // Both gathers of a mixed batch in one launch: the two forms share the block
 // partition (and the reduction groups), so each problem runs the same code as
 // in its own launch.
@@ -571,13 +596,21 @@ void batch_launch_sddmm_mixed(cudaStream_t st, const BDesc* desc, const int* off
 void batch_launch_matvec_lp(cudaStream_t st, const BDesc* desc, const int* off_g, const int* off_r,
                             const int* off_q, const int* off_spmm, const int* off_sddmm, int N, int nb_g, int nb_r,
                             int nb_q, int nb_spmm, int nb_sddmm, int nmax, bool with_sddmm) {
-  const size_t smem = (size_t)BATCH_SPMM_LP_R * nmax * sizeof(float);
-  allow_max_smem((const void*)kb_spmm_lp);
+  const int R = batch_spmm_lp_rows(nmax);
+  const size_t smem = (size_t)spmm_lp_stride(R) * nmax * sizeof(float);
   count_launch(with_sddmm ? 5 : 4);
   if (nb_g > 0) kb_split_G<<<nb_g, 256, 0, st>>>(desc, off_g, N);
   if (nb_r > 0) kb_split_R_part<<<nb_r, 128, 0, st>>>(desc, off_r, N);
   if (nb_q > 0) kb_split_R_Q<<<nb_q, 256, 0, st>>>(desc, off_q, N);
-  if (nb_spmm > 0) kb_spmm_lp<<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N);
+  if (nb_spmm > 0) {
+    switch (R) {
+      case 16: allow_max_smem((const void*)kb_spmm_lp<16>); kb_spmm_lp<16><<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N); break;
+      case 8: allow_max_smem((const void*)kb_spmm_lp<8>); kb_spmm_lp<8><<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N); break;
+      case 4: allow_max_smem((const void*)kb_spmm_lp<4>); kb_spmm_lp<4><<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N); break;
+      case 2: allow_max_smem((const void*)kb_spmm_lp<2>); kb_spmm_lp<2><<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N); break;
+      default: allow_max_smem((const void*)kb_spmm_lp<1>); kb_spmm_lp<1><<<nb_spmm, 256, smem, st>>>(desc, off_spmm, N); break;
+    }
+  }
   if (with_sddmm && nb_sddmm > 0) kb_sddmm_lp<<<nb_sddmm, 256, 0, st>>>(desc, off_sddmm, N);
 }
 
@@ -647,7 +680,7 @@ static void launch_spmm_f64(sdp_problem* h, const double* Vval) {
 }
 template <typename TW, int R>
 static void launch_spmm_lp(sdp_problem* h, const double* Vval, const TW* W) {
-  const size_t smem = (size_t)R * h->n * sizeof(float);
+  const size_t smem = (size_t)spmm_lp_stride(R) * h->n * sizeof(float);
   allow_max_smem((const void*)k_spmm_wv_lp<TW, R>);
   count_launch();
   k_spmm_wv_lp<TW, R><<<cdiv(h->n, R), SPMM_COLS, smem, h->stream>>>(h->n, h->rowptr, h->rowperm, h->colidx, Vval, W,

@@ -446,7 +446,8 @@ static sdp_status precond_alloc(sdp_problem* h) {
     SDP_TRY(h->allocT(&h->work, wneed));
     h->work_doubles = wneed;
   }
-  if (!h->M1) SDP_TRY(h->allocT(&h->M1, (size_t)n * n));
+  // n x n scratch, also the NT-scaling check's 16 n doubles when n < 16
+  if (!h->M1) SDP_TRY(h->allocT(&h->M1, std::max((size_t)n * n, (size_t)16 * n)));
   if (!h->eig_base) {
     SDP_TRY(h->alloc(&h->eig_base, eig_work_bytes(n, true)));
     eig_work_carve(&h->eig, h->eig_base, n, true);
